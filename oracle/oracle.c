@@ -1,0 +1,1060 @@
+/*
+ * FP64 CPU oracle of the Monte Carlo proton dose engine of the 4D-dose
+ * calculator (Pepin et al., arXiv:1809.03927) and of its two companion
+ * stages: the delivery timeline and the energy/mass-transfer accumulation.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * legs of the benchmark (cpu_baseline and the reference arm) load this
+ * library.  The CUDA product path never links, loads or calls it.  This
+ * file includes no project header and shares no table, constant generator
+ * or helper with the CUDA path; both follow the same written model.
+ *
+ * The paper (Sec. 2.C) names the engine "class II condensed-history proton
+ * transport" and says the MC converts HU to density, but prints no physics.
+ * The model written out here is the project's: piecewise-linear HU
+ * calibration, Bethe water stopping power (I = 75 eV) with CSDA range,
+ * Highland multiple scattering in its cumulative-thickness form, Bohr
+ * straggling and non-elastic nuclear removal with a fixed local-deposit
+ * fraction.  Every function below says which passage or definition it
+ * follows and what pins it:
+ *
+ *   or_philox4x32_10   Salmon et al., SC'11 (the cuRAND generator named in
+ *                      Sec. 2.B, footnote b).  Pinned: published
+ *                      known-answer vectors.
+ *   or_rho, or_spr     Sec. 2.C (HU -> density).  Pinned: water (HU 0) is
+ *                      exactly 1, air (HU -1000) is 0.0012 g/cm^3.
+ *   or_bethe_sw        Bethe formula with full T_max.  Pinned: Bragg-Kleeman
+ *                      rule (Bortfeld 1997) within 2 %.
+ *   or_range, or_energy_from_range
+ *                      CSDA range = integral of 1/S.  Pinned: independent
+ *                      adaptive quadrature; R(E(R)) = R.
+ *   or_allocate        Sec. 1 / 2.A (spots carry weights).  Pinned: brute
+ *                      force on small cases, sum and bound invariants.
+ *   or_transport       Sec. 2.C.  Pinned: CSDA range, range scaling with
+ *                      SPR, R80, Fermi-Eyges lateral sigma, primary fluence,
+ *                      energy balance, one-step moment checks.
+ *   or_normalise       Sec. 2.C (dose and density outputs), Eq. 4 (E = M D).
+ *                      Pinned: hand-worked unit conversion.
+ *   or_timeline        Sec. 2.B, App. A.  Pinned: invariants (protons
+ *                      conserved, clock total), the one-phase test of
+ *                      Sec. 2.E, hand-worked examples.
+ *   or_emtm            Sec. 2.D.2, Eqs. 2, 4-6.  Pinned: identity-DVF test
+ *                      of Sec. 2.E, integer translation, mass conservation,
+ *                      brute force.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- physical constants (standard values; the paper gives none) -------- */
+#define OR_K        0.307075         /* MeV cm^2 / mol                       */
+#define OR_ME       0.51099895       /* electron rest energy, MeV            */
+#define OR_MP       938.27208816     /* proton rest energy, MeV              */
+#define OR_ZA       0.55509          /* water Z/A                            */
+#define OR_I        75.0e-6          /* water mean excitation energy, MeV    */
+#define OR_X0_MM    360.8            /* water radiation length 36.08 g/cm^2  */
+#define OR_MEV_J    1.602176634e-13  /* J per MeV                            */
+/* ---- transport model parameters (project choices) ---------------------- */
+#define OR_ECUT     0.5              /* MeV: below this, deposit and stop    */
+#define OR_FSTEP    0.25             /* step <= 0.25 x residual range        */
+#define OR_SMIN     0.01             /* mm: minimum physics step             */
+#define OR_SIG_INF  0.0123           /* 1/cm, nuclear Sigma_w at high energy */
+#define OR_E_TH     7.0              /* MeV, nuclear threshold               */
+#define OR_E_S      20.0             /* MeV, nuclear rise scale              */
+#define OR_FLOC     0.6              /* local-deposit fraction at removal    */
+#define OR_HL_A     13.6             /* Highland, MeV                        */
+#define OR_HL_B     0.038            /* Highland log coefficient             */
+
+#define OR_OK        0
+#define OR_EINVAL   -1
+#define OR_ENOMEM   -2
+#define OR_ESTEP    -5
+
+/* ======================================================================= */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).                      */
+/* Round: two 32x32->64 products of counter words 0 and 2 with the         */
+/* multipliers, outputs permuted and xor-ed with the key; the key gets a   */
+/* Weyl increment between rounds.                                          */
+/* ======================================================================= */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                      uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The random stream of history h (stream id st, 64-bit seed): block b is
+ * Philox4x32-10 of counter (b, h_lo, h_hi, st) under key (seed_lo, seed_hi).
+ * A block's 128 bits, read as one little-endian integer, give six 21-bit
+ * integers k_i = bits [21 i, 21 i + 21), i = 0..5, and the uniforms
+ * u_i = (k_i + 1/2) / 2^21, all in (0, 1) and exact in binary floating point.
+ * Block 0 is the history's birth block, block k + 1 serves step k.          */
+void or_block_uniforms(uint64_t seed, uint64_t h, uint32_t stream,
+                       uint32_t block, double u[6])
+{
+    uint32_t ctr[4] = { block, (uint32_t)h, (uint32_t)(h >> 32), stream };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t w[4];
+    or_philox4x32_10(ctr, key, w);
+    unsigned __int128 v = (unsigned __int128)w[0] | ((unsigned __int128)w[1] << 32) |
+                          ((unsigned __int128)w[2] << 64) | ((unsigned __int128)w[3] << 96);
+    for (int i = 0; i < 6; ++i) {
+        uint32_t k = (uint32_t)((v >> (21 * i)) & 0x1FFFFFu);
+        u[i] = ((double)k + 0.5) / 2097152.0;
+    }
+}
+
+/* Box-Muller: a pair of independent standard normals from two uniforms.    */
+static void or_box_muller(double ua, double ub, double *z0, double *z1)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double r = sqrt(-2.0 * log(ua));
+    *z0 = r * cos(two_pi * ub);
+    *z1 = r * sin(two_pi * ub);
+}
+
+/* ======================================================================= */
+/* HU -> mass density and stopping-power ratio (Sec. 2.C: the MC converts  */
+/* Hounsfield units to density).  Piecewise linear through the project's   */
+/* calibration points, HU clamped to [-1000, 3000].                        */
+/* ======================================================================= */
+static const double OR_CAL_HU[5]  = { -1000.0, 0.0, 100.0, 1200.0, 3000.0 };
+static const double OR_CAL_RHO[5] = { 0.0012, 1.000, 1.100, 1.727, 2.753 };
+static const double OR_CAL_SPR[5] = { 0.00107, 1.000, 1.085, 1.640, 2.500 };
+
+static double or_piecewise(double hu, const double *y)
+{
+    if (hu <= OR_CAL_HU[0]) return y[0];
+    if (hu >= OR_CAL_HU[4]) return y[4];
+    int k = 0;
+    while (!(hu >= OR_CAL_HU[k] && hu <= OR_CAL_HU[k + 1])) ++k;
+    double t = (hu - OR_CAL_HU[k]) / (OR_CAL_HU[k + 1] - OR_CAL_HU[k]);
+    return y[k] + t * (y[k + 1] - y[k]);
+}
+double or_rho(int hu) { return or_piecewise((double)hu, OR_CAL_RHO); }
+double or_spr(int hu) { return or_piecewise((double)hu, OR_CAL_SPR); }
+
+/* ======================================================================= */
+/* Bethe mass stopping power of water, MeV cm^2/g, with the full maximum   */
+/* energy transfer and no shell, density-effect or Barkas terms:           */
+/*   S = K (Z/A) / beta^2 [ 1/2 ln(2 me beta^2 gamma^2 Tmax / I^2) - beta^2 ] */
+/*   Tmax = 2 me beta^2 gamma^2 / (1 + 2 gamma me/mp + (me/mp)^2)          */
+/* ======================================================================= */
+double or_bethe_sw(double E)
+{
+    double gam = 1.0 + E / OR_MP;
+    double bg2 = gam * gam - 1.0;              /* beta^2 gamma^2 */
+    double b2 = bg2 / (gam * gam);
+    double r = OR_ME / OR_MP;
+    double tmax = 2.0 * OR_ME * bg2 / (1.0 + 2.0 * gam * r + r * r);
+    double arg = 2.0 * OR_ME * bg2 * tmax / (OR_I * OR_I);
+    return OR_K * OR_ZA / b2 * (0.5 * log(arg) - b2);
+}
+
+/* ---- CSDA range R(E) = integral_{Ecut}^{E} dE'/S(E') --------------------
+ * Cumulative integrals on nodes E_k = Ecut + k h (h = 0.01 MeV) with an
+ * n-point Gauss-Legendre rule per interval; R(E) between nodes adds the
+ * same rule over [E_k, E].  Ranges are returned in mm of water (1 g/cm^3). */
+#define OR_RH      0.01
+#define OR_RNODES  26001                 /* up to Ecut + 260 MeV */
+#define OR_GLN     4
+static double or_gl_x[OR_GLN], or_gl_w[OR_GLN];
+static double or_rcum[OR_RNODES];
+static int or_tables_ready = 0;
+
+/* Gauss-Legendre nodes/weights on [-1, 1] by Newton on P_n (three-term
+ * recurrence), the textbook construction.                                  */
+static void or_gauss_legendre(int n, double *x, double *w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = cos(pi * (i + 0.75) / (n + 0.5));
+        double pp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                double p3 = p2; p2 = p1;
+                p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1.0);
+            double z1 = z;
+            z = z1 - p1 / pp;
+            if (fabs(z - z1) < 1e-15) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+static double or_gl_inv_s(double a, double b)
+{
+    double c = 0.5 * (a + b), hw = 0.5 * (b - a), s = 0.0;
+    for (int i = 0; i < OR_GLN; ++i) s += or_gl_w[i] / or_bethe_sw(c + hw * or_gl_x[i]);
+    return s * hw;                       /* g/cm^2 */
+}
+
+void or_init_tables(void)
+{
+    if (or_tables_ready) return;
+    or_gauss_legendre(OR_GLN, or_gl_x, or_gl_w);
+    or_rcum[0] = 0.0;
+    for (int k = 1; k < OR_RNODES; ++k) {
+        double a = OR_ECUT + (k - 1) * OR_RH, b = OR_ECUT + k * OR_RH;
+        or_rcum[k] = or_rcum[k - 1] + 10.0 * or_gl_inv_s(a, b);   /* mm */
+    }
+    or_tables_ready = 1;
+}
+
+double or_range(double E)
+{
+    if (E <= OR_ECUT) return 0.0;
+    double x = (E - OR_ECUT) / OR_RH;
+    int k = (int)floor(x);
+    if (k >= OR_RNODES - 1) k = OR_RNODES - 2;
+    double Ek = OR_ECUT + k * OR_RH;
+    return or_rcum[k] + 10.0 * or_gl_inv_s(Ek, E);
+}
+
+/* Inverse of the range: bisection over the node table, then safeguarded
+ * Newton (dR/dE = 1/S) to full double precision.                          */
+double or_energy_from_range(double R)
+{
+    if (R <= 0.0) return OR_ECUT;
+    int lo = 0, hi = OR_RNODES - 1;
+    if (R >= or_rcum[hi]) return OR_ECUT + hi * OR_RH;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (or_rcum[mid] <= R) lo = mid; else hi = mid;
+    }
+    double a = OR_ECUT + lo * OR_RH, b = OR_ECUT + hi * OR_RH;
+    double E = a + (R - or_rcum[lo]) / (or_rcum[hi] - or_rcum[lo]) * (b - a);
+    for (int it = 0; it < 60; ++it) {
+        double f = or_range(E) - R;
+        if (f > 0.0) b = E; else a = E;
+        double En = E - f * or_bethe_sw(E) / 10.0;
+        if (fabs(En - E) <= 1e-13 * E) { E = En; break; }
+        if (!(En >= a && En <= b)) En = 0.5 * (a + b);
+        E = En;
+    }
+    return E;
+}
+
+/* Nuclear removal cross-section per water-equivalent length, 1/cm.         */
+double or_sigma_nuc(double E)
+{
+    if (E <= OR_E_TH) return 0.0;
+    return OR_SIG_INF * (1.0 - exp(-(E - OR_E_TH) / OR_E_S));
+}
+
+/* Highland cumulative function g(u) = u (1 + 0.038 ln u)^2, g(0) = 0.       */
+static double or_highland_g(double u)
+{
+    if (u <= 0.0) return 0.0;
+    double t = 1.0 + OR_HL_B * log(u);
+    return u * t * t;
+}
+
+/* p v (MeV) of a proton of kinetic energy E: E (E + 2 mp) / (E + mp).     */
+double or_pv(double E) { return E * (E + 2.0 * OR_MP) / (E + OR_MP); }
+
+/* ---- pieces of one condensed-history step, shared by the transport and by
+ * the single-step functions exposed for the pins ------------------------ */
+
+/* CSDA over a water-equivalent path sw (mm) from energy E with residual
+ * range R0: end energy E(R0 - sw) and the step-mean energy (E + E1)/2.     */
+static void or_csda(double E, double R0, double sw, double *E1c, double *Emean)
+{
+    *E1c = or_energy_from_range(R0 - sw);
+    *Emean = 0.5 * (E + *E1c);
+}
+
+/* Bohr straggling variance (MeV^2) over a water-equivalent path sw (mm):
+ * K me (Z/A) sw[cm] (1 - beta^2/2)/(1 - beta^2), beta at the step start;
+ * (1 - beta^2/2)/(1 - beta^2) = (gamma^2 + 1)/2.                          */
+double or_bohr_var(double E, double sw_mm)
+{
+    double gam = 1.0 + E / OR_MP;
+    return OR_K * OR_ME * OR_ZA * (sw_mm / 10.0) * 0.5 * (gam * gam + 1.0);
+}
+
+/* Highland variance of the projected angle over radiation thickness
+ * [u0, u0 + du]: (13.6 / pv)^2 (g(u0 + du) - g(u0)), pv at energy E.      */
+double or_highland_theta2(double E, double u0, double du)
+{
+    double k = OR_HL_A / or_pv(E);
+    return k * k * (or_highland_g(u0 + du) - or_highland_g(u0));
+}
+
+/* Correlated lateral displacement and angle in one transverse plane over a
+ * step s: y = s theta0 (z1/sqrt(12) + z2/2), theta = theta0 z2 (the PDG
+ * Passage-of-particles form).                                             */
+static void or_mcs_plane(double s, double th0, double z1, double z2, double *y, double *t)
+{
+    *y = s * th0 * (z1 / sqrt(12.0) + 0.5 * z2);
+    *t = th0 * z2;
+}
+
+/* ======================================================================= */
+/* Histories per spot: proportional to the spot's protons, floor plus      */
+/* largest remainder; equal remainders go to the lower spot index.         */
+/* ======================================================================= */
+typedef struct { uint64_t rem; int64_t idx; } or_rem_t;
+
+static int or_rem_cmp(const void *a, const void *b)
+{
+    const or_rem_t *x = (const or_rem_t *)a, *y = (const or_rem_t *)b;
+    if (x->rem != y->rem) return x->rem > y->rem ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx ? 1 : 0);
+}
+
+int or_allocate(int64_t n_spots, const uint64_t *protons, uint64_t n_hist,
+                uint64_t *n_out)
+{
+    if (n_spots <= 0) return OR_EINVAL;
+    unsigned __int128 W = 0;
+    for (int64_t s = 0; s < n_spots; ++s) W += protons[s];
+    if (W == 0 || W > (unsigned __int128)UINT64_MAX) return OR_EINVAL;
+    or_rem_t *r = (or_rem_t *)malloc(sizeof(or_rem_t) * (size_t)n_spots);
+    if (!r) return OR_ENOMEM;
+    uint64_t assigned = 0;
+    for (int64_t s = 0; s < n_spots; ++s) {
+        unsigned __int128 q = (unsigned __int128)n_hist * protons[s];
+        n_out[s] = (uint64_t)(q / W);
+        r[s].rem = (uint64_t)(q % W);
+        r[s].idx = s;
+        assigned += n_out[s];
+    }
+    uint64_t left = n_hist - assigned;
+    qsort(r, (size_t)n_spots, sizeof(or_rem_t), or_rem_cmp);
+    for (uint64_t i = 0; i < left; ++i) n_out[r[i].idx] += 1;
+    free(r);
+    return OR_OK;
+}
+
+/* ======================================================================= */
+/* Transport (Sec. 2.C: class II condensed history).                       */
+/* ======================================================================= */
+typedef struct {
+    /* grid: voxel (i,j,k) covers [i dx, (i+1) dx) x ... in grid mm; x fastest */
+    int32_t n[3];
+    double d[3];
+    double origin[3];            /* patient-frame mm of the grid corner */
+    const int16_t *hu;
+    int32_t beam_axis;           /* 0, 1, 2 */
+    int32_t beam_sign;           /* +1 or -1 */
+    /* plan: spot lateral coordinates are the patient-frame coordinates on
+       the two non-beam axes, lower axis first */
+    int64_t n_spots;
+    const double *spot_x, *spot_y, *spot_e, *spot_sigma;
+    const uint64_t *spot_protons;
+    /* run */
+    uint64_t n_hist;             /* histories of the whole run */
+    uint64_t hist_begin, hist_end;
+    uint64_t seed;
+    uint32_t stream;
+    uint32_t physics;            /* bit0 straggling, bit1 MCS, bit2 nuclear */
+    double spr_scale;
+    double shift[3];             /* patient displacement, mm */
+    int64_t max_steps;
+    int32_t nthreads;
+    /* diagnostics, depth measured from the upstream face along the beam */
+    int32_t n_depth_bins;
+    double depth_bin_mm;
+    int32_t n_planes;
+    double plane_mm;             /* plane k at depth (k + 1) plane_mm */
+} or_run_params;
+
+typedef struct {
+    double *edep;                /* nvox, MeV x history weight */
+    double *depth_dose;          /* n_depth_bins or NULL */
+    double *plane_w;             /* n_planes: weight of primaries crossing */
+    double *plane_m1;            /* 2 x n_planes: sum w x (lateral axes) */
+    double *plane_m2;            /* 2 x n_planes: sum w x^2 */
+    double ledger[4];            /* deposited, escaped, removed, incident */
+    uint64_t steps;
+    uint64_t histories;
+    int32_t status;
+    double end_depth[2];         /* sum w z_end, sum w over histories that
+                                    stop by running out of energy */
+} or_run_out;
+
+#define OR_PHYS_STRAG 1u
+#define OR_PHYS_MCS   2u
+#define OR_PHYS_NUC   4u
+
+typedef struct {
+    double *edep, *depth, *pw, *pm1, *pm2;
+    double ledger[4];
+    uint64_t steps;
+    int32_t status;
+    double end_depth[2];
+} or_acc;
+
+static void or_depth_spread(const or_run_params *P, or_acc *A, double z0,
+                            double z1, double e)
+{
+    if (!A->depth || e == 0.0) return;
+    double a = z0 < z1 ? z0 : z1, b = z0 < z1 ? z1 : z0;
+    double w = P->depth_bin_mm;
+    if (b - a < 1e-12) {
+        int k = (int)floor(a / w);
+        if (k >= 0 && k < P->n_depth_bins) A->depth[k] += e;
+        return;
+    }
+    int ka = (int)floor(a / w), kb = (int)floor(b / w);
+    for (int k = ka; k <= kb; ++k) {
+        double lo = k * w > a ? k * w : a;
+        double hi = (k + 1) * w < b ? (k + 1) * w : b;
+        if (hi > lo && k >= 0 && k < P->n_depth_bins)
+            A->depth[k] += e * (hi - lo) / (b - a);
+    }
+}
+
+static double or_depth_of(const or_run_params *P, const double *p)
+{
+    int a = P->beam_axis;
+    return P->beam_sign > 0 ? p[a] : P->n[a] * P->d[a] - p[a];
+}
+
+static void or_planes(const or_run_params *P, or_acc *A, const double *p0,
+                      const double *p1, double w)
+{
+    if (!A->pw) return;
+    int a = P->beam_axis, b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+    double z0 = or_depth_of(P, p0), z1 = or_depth_of(P, p1);
+    if (z1 <= z0) return;
+    int k0 = (int)floor(z0 / P->plane_mm);          /* planes with z0 < zk <= z1 */
+    for (int k = k0; k < P->n_planes; ++k) {
+        double zk = (k + 1) * P->plane_mm;
+        if (zk <= z0) continue;
+        if (zk > z1) break;
+        double t = (zk - z0) / (z1 - z0);
+        double xb = p0[b] + t * (p1[b] - p0[b]);
+        double xc = p0[c] + t * (p1[c] - p0[c]);
+        A->pw[k] += w;
+        A->pm1[k] += w * xb;  A->pm1[P->n_planes + k] += w * xc;
+        A->pm2[k] += w * xb * xb;  A->pm2[P->n_planes + k] += w * xc * xc;
+    }
+}
+
+/* Orthonormal frame (e1, e2) perpendicular to unit vector d: the branch-free
+ * construction of Duff et al., "Building an Orthonormal Basis, Revisited",
+ * JCGT 6(1), 2017.                                                          */
+void or_frame(const double *d, double *e1, double *e2)
+{
+    double sg = d[2] >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + d[2]);
+    double b = d[0] * d[1] * a;
+    e1[0] = 1.0 + sg * d[0] * d[0] * a; e1[1] = sg * b; e1[2] = -sg * d[0];
+    e2[0] = b; e2[1] = sg + d[1] * d[1] * a; e2[2] = -d[1];
+}
+
+/* One history.  Returns 0, or OR_ESTEP if the step limit was hit.           */
+static void or_history(const or_run_params *P, const uint64_t *prefix,
+                       const double *wts, uint64_t h, or_acc *A)
+{
+    /* spot of history h: prefix[s] <= h < prefix[s+1] */
+    int64_t lo = 0, hi = P->n_spots;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) / 2;
+        if (prefix[mid] <= h) lo = mid; else hi = mid;
+    }
+    int64_t s = lo;
+    double w = wts[s];
+    int ax = P->beam_axis, bx = (ax == 0) ? 1 : 0, cx = (ax == 2) ? 1 : 2;
+    const int32_t *n = P->n;
+    const double *dd = P->d;
+
+    double u[6];
+    or_block_uniforms(P->seed, h, P->stream, 0u, u);
+    double zx, zy;
+    or_box_muller(u[0], u[1], &zx, &zy);
+    double eta = -log(u[2]);
+
+    double E = P->spot_e[s];
+    A->ledger[3] += E * w;
+
+    double p[3], dir[3] = { 0.0, 0.0, 0.0 };
+    p[bx] = P->spot_x[s] - P->origin[bx] - P->shift[bx] + P->spot_sigma[s] * zx;
+    p[cx] = P->spot_y[s] - P->origin[cx] - P->shift[cx] + P->spot_sigma[s] * zy;
+    p[ax] = P->beam_sign > 0 ? 0.0 : n[ax] * dd[ax];
+    dir[ax] = (double)P->beam_sign;
+    if (!(p[bx] >= 0.0 && p[bx] < n[bx] * dd[bx] &&
+          p[cx] >= 0.0 && p[cx] < n[cx] * dd[cx])) {
+        A->ledger[1] += E * w;                 /* never enters the grid */
+        return;
+    }
+    int32_t iv[3];
+    iv[bx] = (int32_t)floor(p[bx] / dd[bx]);
+    iv[cx] = (int32_t)floor(p[cx] / dd[cx]);
+    iv[ax] = P->beam_sign > 0 ? 0 : n[ax] - 1;
+
+    double uthick = 0.0;                       /* radiation lengths so far */
+    const double scap = fmin(dd[0], fmin(dd[1], dd[2]));
+    for (int64_t step = 0;; ++step) {
+        if (step >= P->max_steps) {
+            A->ledger[1] += E * w;
+            A->status = OR_ESTEP;
+            return;
+        }
+        A->steps += 1;
+        size_t vox = ((size_t)iv[2] * n[1] + iv[1]) * n[0] + iv[0];
+        int hu = P->hu[vox];
+        double rho = or_rho(hu);
+        double spr = or_spr(hu) * P->spr_scale;
+        double R0 = or_range(E);
+        double z_start = or_depth_of(P, p);
+        if (R0 / spr <= OR_SMIN) {             /* residual range below s_min */
+            A->edep[vox] += E * w;
+            A->ledger[0] += E * w;
+            or_depth_spread(P, A, z_start, z_start, E * w);
+            A->end_depth[0] += w * z_start;
+            A->end_depth[1] += w;
+            return;
+        }
+        /* distance to the faces of the current voxel */
+        double dbound = INFINITY;
+        int across = -1;
+        for (int k = 0; k < 3; ++k) {
+            double t;
+            if (dir[k] > 0.0) t = ((iv[k] + 1) * dd[k] - p[k]) / dir[k];
+            else if (dir[k] < 0.0) t = (iv[k] * dd[k] - p[k]) / dir[k];
+            else continue;
+            if (t < 0.0) t = 0.0;
+            if (t < dbound) { dbound = t; across = k; }
+        }
+        double sphys = fmax(OR_FSTEP * R0 / spr, OR_SMIN);
+        double s = fmin(scap, sphys);
+        int geom = 0;
+        if (dbound <= s) { s = dbound; geom = 1; }
+
+        double sw = s * spr;                   /* water-equivalent mm */
+        double E1c, Emean;
+        or_csda(E, R0, sw, &E1c, &Emean);
+        int nuclear = 0;
+        if (P->physics & OR_PHYS_NUC) {
+            double sig = or_sigma_nuc(Emean);  /* 1/cm */
+            double tau = sig * sw / 10.0;
+            if (sig > 0.0 && tau >= eta) {
+                nuclear = 1;
+                sw = eta * 10.0 / sig;
+                s = sw / spr;
+                geom = 0;
+                or_csda(E, R0, sw, &E1c, &Emean);
+            } else {
+                eta -= tau;
+            }
+        }
+        or_block_uniforms(P->seed, h, P->stream, (uint32_t)(step + 1), u);
+        double zA0, zA1, z1u, z2u, z1v, z2v;
+        or_box_muller(u[0], u[1], &zA0, &zA1);
+        or_box_muller(u[2], u[3], &z1u, &z2u);
+        or_box_muller(u[4], u[5], &z1v, &z2v);
+
+        double dE = E - E1c;
+        if (P->physics & OR_PHYS_STRAG) {
+            dE += sqrt(or_bohr_var(E, sw)) * zA0;
+            if (dE < 0.0) dE = 0.0;
+            if (dE > E) dE = E;
+        }
+        double E1 = E - dE;
+
+        if (nuclear) {
+            double loc = OR_FLOC * E1;
+            A->edep[vox] += (dE + loc) * w;
+            A->ledger[0] += (dE + loc) * w;
+            A->ledger[2] += (E1 - loc) * w;
+            double zend = z_start + s * dir[ax] * P->beam_sign;
+            or_depth_spread(P, A, z_start, zend, dE * w);
+            or_depth_spread(P, A, zend, zend, loc * w);
+            return;
+        }
+        if (E1 <= OR_ECUT) {
+            A->edep[vox] += E * w;             /* dE + E1 */
+            A->ledger[0] += E * w;
+            double zend = z_start + s * dir[ax] * P->beam_sign;
+            or_depth_spread(P, A, z_start, zend, dE * w);
+            or_depth_spread(P, A, zend, zend, E1 * w);
+            A->end_depth[0] += w * zend;
+            A->end_depth[1] += w;
+            return;
+        }
+        A->edep[vox] += dE * w;
+        A->ledger[0] += dE * w;
+
+        /* multiple Coulomb scattering over the step */
+        double y1 = 0.0, y2 = 0.0, t1 = 0.0, t2 = 0.0;
+        if (P->physics & OR_PHYS_MCS) {
+            double du = s * rho / OR_X0_MM;
+            double th2 = or_highland_theta2(Emean, uthick, du);
+            uthick += du;
+            double th0 = th2 > 0.0 ? sqrt(th2) : 0.0;
+            or_mcs_plane(s, th0, z1u, z2u, &y1, &t1);
+            or_mcs_plane(s, th0, z1v, z2v, &y2, &t2);
+        }
+        double e1[3], e2[3];
+        or_frame(dir, e1, e2);
+        double p0[3] = { p[0], p[1], p[2] };
+        double dir0[3] = { dir[0], dir[1], dir[2] };
+        for (int k = 0; k < 3; ++k) {
+            p[k] = p[k] + s * dir[k] + y1 * e1[k] + y2 * e2[k];
+            dir[k] = dir[k] + t1 * e1[k] + t2 * e2[k];
+        }
+        double nrm = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        for (int k = 0; k < 3; ++k) dir[k] /= nrm;
+        E = E1;
+        or_depth_spread(P, A, z_start, or_depth_of(P, p), dE * w);
+
+        /* voxel update: the crossed axis advances by one and its coordinate
+           is put on the crossed face; every other axis takes floor(p/d)    */
+        for (int k = 0; k < 3; ++k) {
+            if (geom && k == across) {
+                if (dir0[k] > 0.0) { iv[k] += 1; p[k] = iv[k] * dd[k]; }
+                else { p[k] = iv[k] * dd[k]; iv[k] -= 1; }
+            } else {
+                iv[k] = (int32_t)floor(p[k] / dd[k]);
+            }
+        }
+        or_planes(P, A, p0, p, w);
+        if (iv[0] < 0 || iv[0] >= n[0] || iv[1] < 0 || iv[1] >= n[1] ||
+            iv[2] < 0 || iv[2] >= n[2]) {
+            A->ledger[1] += E * w;
+            return;
+        }
+    }
+}
+
+int or_transport(const or_run_params *P, or_run_out *O)
+{
+    or_init_tables();
+    if (P->n_spots <= 0 || P->n_hist == 0 || P->hist_end > P->n_hist ||
+        P->hist_begin > P->hist_end || P->beam_axis < 0 || P->beam_axis > 2 ||
+        (P->beam_sign != 1 && P->beam_sign != -1))
+        return OR_EINVAL;
+    for (int64_t s = 0; s < P->n_spots; ++s)
+        if (!(P->spot_e[s] >= 1.0 && P->spot_e[s] <= 250.0)) return OR_EINVAL;
+    size_t nvox = (size_t)P->n[0] * P->n[1] * P->n[2];
+    uint64_t *ns = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)P->n_spots);
+    uint64_t *prefix = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(P->n_spots + 1));
+    double *wts = (double *)malloc(sizeof(double) * (size_t)P->n_spots);
+    if (!ns || !prefix || !wts) { free(ns); free(prefix); free(wts); return OR_ENOMEM; }
+    int rc = or_allocate(P->n_spots, P->spot_protons, P->n_hist, ns);
+    if (rc) { free(ns); free(prefix); free(wts); return rc; }
+    double W = 0.0;
+    for (int64_t s = 0; s < P->n_spots; ++s) W += (double)P->spot_protons[s];
+    prefix[0] = 0;
+    for (int64_t s = 0; s < P->n_spots; ++s) {
+        prefix[s + 1] = prefix[s] + ns[s];
+        /* history weight relative to the mean protons per history W/N */
+        wts[s] = ns[s] ? (double)P->spot_protons[s] * (double)P->n_hist / ((double)ns[s] * W) : 0.0;
+    }
+
+    int nt = P->nthreads > 0 ? P->nthreads : 1;
+    uint64_t count = P->hist_end - P->hist_begin;
+    if ((uint64_t)nt > count && count > 0) nt = (int)count;
+    if (nt < 1) nt = 1;
+    or_acc *acc = (or_acc *)calloc((size_t)nt, sizeof(or_acc));
+    int np = P->n_planes;
+    int ok = acc != NULL;
+    for (int t = 0; ok && t < nt; ++t) {
+        acc[t].edep = (double *)calloc(nvox, sizeof(double));
+        ok &= acc[t].edep != NULL;
+        if (O->depth_dose) { acc[t].depth = (double *)calloc((size_t)P->n_depth_bins, sizeof(double)); ok &= acc[t].depth != NULL; }
+        if (O->plane_w) {
+            acc[t].pw = (double *)calloc((size_t)np, sizeof(double));
+            acc[t].pm1 = (double *)calloc((size_t)(2 * np), sizeof(double));
+            acc[t].pm2 = (double *)calloc((size_t)(2 * np), sizeof(double));
+            ok &= acc[t].pw && acc[t].pm1 && acc[t].pm2;
+        }
+    }
+    if (ok) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(static)
+#endif
+        for (int t = 0; t < nt; ++t) {
+            uint64_t b = P->hist_begin + count * (uint64_t)t / (uint64_t)nt;
+            uint64_t e = P->hist_begin + count * (uint64_t)(t + 1) / (uint64_t)nt;
+            for (uint64_t h = b; h < e; ++h) or_history(P, prefix, wts, h, &acc[t]);
+        }
+        /* fixed-order reduction */
+        memset(O->ledger, 0, sizeof(O->ledger));
+        O->end_depth[0] = O->end_depth[1] = 0.0;
+        O->steps = 0;
+        O->status = OR_OK;
+        for (int t = 0; t < nt; ++t) {
+            for (size_t i = 0; i < nvox; ++i) O->edep[i] += acc[t].edep[i];
+            if (O->depth_dose)
+                for (int k = 0; k < P->n_depth_bins; ++k) O->depth_dose[k] += acc[t].depth[k];
+            if (O->plane_w)
+                for (int k = 0; k < np; ++k) {
+                    O->plane_w[k] += acc[t].pw[k];
+                    O->plane_m1[k] += acc[t].pm1[k]; O->plane_m1[np + k] += acc[t].pm1[np + k];
+                    O->plane_m2[k] += acc[t].pm2[k]; O->plane_m2[np + k] += acc[t].pm2[np + k];
+                }
+            for (int k = 0; k < 4; ++k) O->ledger[k] += acc[t].ledger[k];
+            O->end_depth[0] += acc[t].end_depth[0];
+            O->end_depth[1] += acc[t].end_depth[1];
+            O->steps += acc[t].steps;
+            if (acc[t].status) O->status = acc[t].status;
+        }
+        O->histories = count;
+    }
+    for (int t = 0; acc && t < nt; ++t) {
+        free(acc[t].edep); free(acc[t].depth); free(acc[t].pw); free(acc[t].pm1); free(acc[t].pm2);
+    }
+    free(acc); free(ns); free(prefix); free(wts);
+    return ok ? O->status : OR_ENOMEM;
+}
+
+/* One condensed-history step of a proton in an infinite uniform medium of
+ * the given HU with energy E and cumulative radiation thickness u0, over a
+ * step of s mm, drawn from the step-(step_index) uniforms of history h,
+ * with the same pieces the transport uses.  Exposed so that the single-step
+ * distributions (straggling variance, the correlated angle/displacement
+ * moments) can be pinned.
+ * out: [0] dE, [1] theta_1, [2] y_1, [3] theta_2, [4] y_2, [5] s (mm).     */
+void or_single_step(int hu, double E, double u0, double s, uint64_t seed,
+                    uint64_t h, uint32_t stream, uint32_t step_index,
+                    double *out)
+{
+    or_init_tables();
+    double rho = or_rho(hu), spr = or_spr(hu);
+    double R0 = or_range(E);
+    double sw = s * spr;
+    double E1c, Emean;
+    or_csda(E, R0, sw, &E1c, &Emean);
+    double u[6];
+    or_block_uniforms(seed, h, stream, step_index + 1, u);
+    double zA0, zA1, z1u, z2u, z1v, z2v;
+    or_box_muller(u[0], u[1], &zA0, &zA1);
+    or_box_muller(u[2], u[3], &z1u, &z2u);
+    or_box_muller(u[4], u[5], &z1v, &z2v);
+    double dE = E - E1c + sqrt(or_bohr_var(E, sw)) * zA0;
+    if (dE < 0.0) dE = 0.0;
+    if (dE > E) dE = E;
+    double th2 = or_highland_theta2(Emean, u0, s * rho / OR_X0_MM);
+    double th0 = th2 > 0.0 ? sqrt(th2) : 0.0;
+    out[0] = dE;
+    or_mcs_plane(s, th0, z1u, z2u, &out[2], &out[1]);
+    or_mcs_plane(s, th0, z1v, z2v, &out[4], &out[3]);
+    out[5] = s;
+}
+
+/* theta0^2 and nuclear optical depth of one step of s mm from energy E in a
+ * uniform medium, both taken at the step-mean energy as in the transport. */
+double or_step_theta2(int hu, double E, double u0, double s)
+{
+    or_init_tables();
+    double E1c, Emean;
+    or_csda(E, or_range(E), s * or_spr(hu), &E1c, &Emean);
+    return or_highland_theta2(Emean, u0, s * or_rho(hu) / OR_X0_MM);
+}
+
+double or_step_tau(int hu, double E, double s)
+{
+    or_init_tables();
+    double sw = s * or_spr(hu);
+    double E1c, Emean;
+    or_csda(E, or_range(E), sw, &E1c, &Emean);
+    return or_sigma_nuc(Emean) * sw / 10.0;
+}
+
+/* ======================================================================= */
+/* Dose from deposited energy (Sec. 2.C: dose and density per CT voxel):   */
+/*   D_i [Gy] = E_i [MeV] x W/N x 1.602176634e-13 J/MeV / (rho_i V_i 1e-3 kg) */
+/* where E_i is the history-weighted deposit and W/N the mean protons per   */
+/* history.                                                                 */
+/* ======================================================================= */
+void or_normalise(int64_t nvox, const double *edep, const double *rho,
+                  double w_bar, double voxel_cm3, double *dose)
+{
+    for (int64_t i = 0; i < nvox; ++i)
+        dose[i] = edep[i] * w_bar * OR_MEV_J / (rho[i] * voxel_cm3 * 1.0e-3);
+}
+
+/* ======================================================================= */
+/* Delivery timeline (Sec. 2.B, App. A): integer-ns breathing and spot     */
+/* clocks; each spot (or portion of a spot) is assigned to the breathing   */
+/* phase during which it is delivered.                                     */
+/* ======================================================================= */
+typedef struct {
+    int32_t n_phases, start_phase, gated, gate_first, gate_last, repaints;
+    int64_t period_ns, period_sigma_ns, spot_switch_ns, layer_switch_ns, discard_ns;
+    uint64_t rate_protons_per_s, seed;
+} or_delivery;
+
+typedef struct {
+    const or_delivery *D;
+    int64_t tph;
+    uint32_t p0;
+} or_clock;
+
+static uint32_t or_phase_at(const or_clock *C, int64_t t)
+{
+    return (uint32_t)((C->p0 + (uint64_t)(t / C->tph)) % (uint64_t)C->D->n_phases);
+}
+
+static int or_gate_on(const or_clock *C, uint32_t ph)
+{
+    return !C->D->gated || ((int32_t)ph >= C->D->gate_first && (int32_t)ph <= C->D->gate_last);
+}
+
+/* Advance t to the start of the next slot whose phase is the first gate-on
+ * phase, then add the beam-discard time; repeat while the gate is off.    */
+static int64_t or_wait_gate(const or_clock *C, int64_t t)
+{
+    while (!or_gate_on(C, or_phase_at(C, t))) {
+        int64_t slot = t / C->tph;
+        int64_t N = C->D->n_phases;
+        int64_t next = slot + 1;
+        int64_t ph_next = (int64_t)((C->p0 + (uint64_t)next) % (uint64_t)N);
+        int64_t delta = ((int64_t)C->D->gate_first - ph_next) % N;
+        if (delta < 0) delta += N;
+        t = (next + delta) * C->tph + C->D->discard_ns;
+    }
+    return t;
+}
+
+int or_timeline(int64_t n_spots, const uint64_t *protons, const int32_t *layer,
+                const int32_t *field, const or_delivery *D, uint64_t *pp,
+                int64_t *field_end_ns, int32_t *start_phase_out, int32_t n_fields)
+{
+    if (n_spots <= 0 || D->n_phases <= 0 || D->repaints <= 0 || D->period_ns <= 0 ||
+        D->rate_protons_per_s == 0 || D->period_sigma_ns != 0 || n_fields <= 0 ||
+        D->spot_switch_ns < 0 || D->layer_switch_ns < 0)
+        return OR_EINVAL;
+    int64_t tph = D->period_ns / D->n_phases;
+    if (tph <= 0) return OR_EINVAL;
+    if (D->gated) {
+        if (D->gate_first < 0 || D->gate_last >= D->n_phases || D->gate_first > D->gate_last)
+            return OR_EINVAL;
+        if (D->discard_ns < 0 || D->discard_ns >= (int64_t)(D->gate_last - D->gate_first + 1) * tph)
+            return OR_EINVAL;
+    }
+    if (D->start_phase >= D->n_phases) return OR_EINVAL;
+    for (int64_t s = 0; s < n_spots; ++s)
+        if (field[s] < 0 || field[s] >= n_fields) return OR_EINVAL;
+    memset(pp, 0, sizeof(uint64_t) * (size_t)(n_spots * D->n_phases));
+    size_t cap = 64;
+    int64_t *pd = (int64_t *)malloc(sizeof(int64_t) * cap);
+    uint32_t *pph = (uint32_t *)malloc(sizeof(uint32_t) * cap);
+    if (!pd || !pph) { free(pd); free(pph); return OR_ENOMEM; }
+    int rc = OR_OK;
+    for (int32_t f = 0; f < n_fields && rc == OR_OK; ++f) {
+        or_clock C = { D, tph, 0u };
+        if (D->start_phase >= 0) {
+            C.p0 = (uint32_t)D->start_phase;
+        } else {
+            /* random start phase: word 0 of Philox(counter (f,0,0,0), key seed) mod N */
+            uint32_t ctr[4] = { (uint32_t)f, 0u, 0u, 0u };
+            uint32_t key[2] = { (uint32_t)D->seed, (uint32_t)(D->seed >> 32) };
+            uint32_t w[4];
+            or_philox4x32_10(ctr, key, w);
+            C.p0 = w[0] % (uint32_t)D->n_phases;
+        }
+        start_phase_out[f] = (int32_t)C.p0;
+        int64_t t = 0;
+        int delivered_any = 0;
+        int64_t s = 0;
+        /* the field's spots in plan order; a layer is a maximal run of equal
+           layer ids among them and is painted `repaints` times in a row     */
+        while (s < n_spots && rc == OR_OK) {
+            if (field[s] != f) { ++s; continue; }
+            int64_t l0 = s, l1 = s;
+            for (int64_t k = s + 1; k < n_spots; ++k) {
+                if (field[k] != f) continue;
+                if (layer[k] != layer[l0]) break;
+                l1 = k;
+            }
+            s = l1 + 1;
+            int layer_started = 0;
+            for (int32_t r = 0; r < D->repaints && rc == OR_OK; ++r) {
+                for (int64_t q = l0; q <= l1; ++q) {
+                    if (field[q] != f) continue;
+                    uint64_t w = protons[q] / (uint64_t)D->repaints;
+                    if (r == D->repaints - 1) w += protons[q] % (uint64_t)D->repaints;
+                    if (w == 0) continue;
+                    if (delivered_any)
+                        t += layer_started ? D->spot_switch_ns : D->layer_switch_ns;
+                    delivered_any = 1;
+                    layer_started = 1;
+                    /* spill time of this portion, ns */
+                    int64_t dur = (int64_t)((unsigned __int128)w * 1000000000u / D->rate_protons_per_s);
+                    if (D->gated) t = or_wait_gate(&C, t);
+                    size_t np = 0;
+                    if (dur == 0) { pph[0] = or_phase_at(&C, t); pd[0] = 0; np = 1; }
+                    int64_t rem = dur;
+                    while (rem > 0) {
+                        if (D->gated) t = or_wait_gate(&C, t);
+                        int64_t slot = t / tph;
+                        int64_t seg = (slot + 1) * tph - t;
+                        int64_t d = rem < seg ? rem : seg;
+                        if (np == cap) {
+                            cap *= 2;
+                            int64_t *nd = (int64_t *)realloc(pd, sizeof(int64_t) * cap);
+                            if (nd) pd = nd;
+                            uint32_t *nph = (uint32_t *)realloc(pph, sizeof(uint32_t) * cap);
+                            if (nph) pph = nph;
+                            if (!nd || !nph) { rc = OR_ENOMEM; break; }
+                        }
+                        pph[np] = or_phase_at(&C, t); pd[np] = d; ++np;
+                        t += d;
+                        rem -= d;
+                    }
+                    if (rc) break;
+                    /* protons by time share: floor for every portion but the
+                       last, which takes the remainder                        */
+                    uint64_t given = 0;
+                    for (size_t j = 0; j < np; ++j) {
+                        uint64_t pj;
+                        if (j == np - 1) pj = w - given;
+                        else pj = (uint64_t)((unsigned __int128)w * (uint64_t)pd[j] / (uint64_t)dur);
+                        given += pj;
+                        pp[(size_t)pph[j] * (size_t)n_spots + (size_t)q] += pj;
+                    }
+                }
+            }
+        }
+        field_end_ns[f] = t;
+    }
+    free(pd); free(pph);
+    return rc;
+}
+
+/* ======================================================================= */
+/* Energy/mass-transfer accumulation (Sec. 2.D.2, Eqs. 4-6) and the phase  */
+/* sum of Eq. 2.                                                           */
+/*                                                                         */
+/* Each voxel j of every source phase S != R is split into nsub[0] x       */
+/* nsub[1] x nsub[2] subvoxels; subvoxel centre r_jk is moved by the DVF   */
+/* of S (trilinear between voxel centres, edge-clamped) and lands in the   */
+/* reference voxel i whose half-open cell contains it.  Subvoxel mass is   */
+/* M = rho_j v_k and energy E = M D_j (Eq. 4); D_i^S = sum E / sum M over  */
+/* the subvoxels landing in i (Eqs. 5, 6), 0 where none lands; D_i = D_i^R */
+/* + sum_S D_i^S (Eq. 2), zero outside the mask.                           */
+/*                                                                         */
+/* The target voxel is an integer decided by floating point; it is taken  */
+/* in single precision with the operation order written below, the same   */
+/* precision the GPU kernel decides it in.  Sums and ratios are FP64.      */
+/* ======================================================================= */
+static float or_f_lerp(float a, float b, float t)
+{
+    volatile float diff = b - a;
+    volatile float prod = t * diff;
+    volatile float r = a + prod;
+    return r;
+}
+
+static float or_f_sample(const float *comp, const int32_t *n, float qx, float qy, float qz)
+{
+    float q[3] = { qx, qy, qz };
+    int32_t i0[3], i1[3];
+    float f[3];
+    for (int a = 0; a < 3; ++a) {
+        float fl = floorf(q[a]);
+        volatile float fr = q[a] - fl;
+        f[a] = fr;
+        int32_t k = (int32_t)fl;
+        int32_t k1 = k + 1;
+        if (k < 0) k = 0;
+        if (k > n[a] - 1) k = n[a] - 1;
+        if (k1 < 0) k1 = 0;
+        if (k1 > n[a] - 1) k1 = n[a] - 1;
+        i0[a] = k; i1[a] = k1;
+    }
+#define OR_AT(x, y, z) comp[((size_t)(z) * n[1] + (y)) * n[0] + (x)]
+    float c00 = or_f_lerp(OR_AT(i0[0], i0[1], i0[2]), OR_AT(i1[0], i0[1], i0[2]), f[0]);
+    float c10 = or_f_lerp(OR_AT(i0[0], i1[1], i0[2]), OR_AT(i1[0], i1[1], i0[2]), f[0]);
+    float c01 = or_f_lerp(OR_AT(i0[0], i0[1], i1[2]), OR_AT(i1[0], i0[1], i1[2]), f[0]);
+    float c11 = or_f_lerp(OR_AT(i0[0], i1[1], i1[2]), OR_AT(i1[0], i1[1], i1[2]), f[0]);
+#undef OR_AT
+    float c0 = or_f_lerp(c00, c10, f[1]);
+    float c1 = or_f_lerp(c01, c11, f[1]);
+    return or_f_lerp(c0, c1, f[2]);
+}
+
+int or_emtm(const int32_t n[3], const float dmm[3], int32_t n_phases,
+            int32_t ref_phase, const int32_t nsub[3], const float *dose,
+            const float *rho, const float *dvf, const uint8_t *mask,
+            double *accum, double *e_sum, double *m_sum, uint64_t *dropped)
+{
+    if (n_phases <= 0 || ref_phase < 0 || ref_phase >= n_phases ||
+        nsub[0] <= 0 || nsub[1] <= 0 || nsub[2] <= 0)
+        return OR_EINVAL;
+    size_t nvox = (size_t)n[0] * n[1] * n[2];
+    double *E = (double *)calloc(nvox, sizeof(double));
+    double *M = (double *)calloc(nvox, sizeof(double));
+    if (!E || !M) { free(E); free(M); return OR_ENOMEM; }
+    for (size_t i = 0; i < nvox; ++i) accum[i] = (double)dose[(size_t)ref_phase * nvox + i];
+    uint64_t drop = 0;
+    for (int32_t S = 0; S < n_phases; ++S) {
+        if (S == ref_phase) continue;
+        memset(E, 0, nvox * sizeof(double));
+        memset(M, 0, nvox * sizeof(double));
+        const float *ds = dose + (size_t)S * nvox;
+        const float *rs = rho + (size_t)S * nvox;
+        for (int32_t jz = 0; jz < n[2]; ++jz)
+        for (int32_t jy = 0; jy < n[1]; ++jy)
+        for (int32_t jx = 0; jx < n[0]; ++jx) {
+            size_t j = ((size_t)jz * n[1] + jy) * n[0] + jx;
+            double m = (double)rs[j];
+            double e = (double)rs[j] * (double)ds[j];
+            for (int32_t kz = 0; kz < nsub[2]; ++kz)
+            for (int32_t ky = 0; ky < nsub[1]; ++ky)
+            for (int32_t kx = 0; kx < nsub[0]; ++kx) {
+                /* subvoxel centre in continuous voxel-centre index space:
+                   q = j + (k + 1/2)/nsub - 1/2 */
+                int32_t jj[3] = { jx, jy, jz }, kk[3] = { kx, ky, kz };
+                float q[3], t[3];
+                for (int a = 0; a < 3; ++a) {
+                    volatile float frac = ((float)kk[a] + 0.5f) / (float)nsub[a];
+                    volatile float s1 = (float)jj[a] + frac;
+                    volatile float s2 = s1 - 0.5f;
+                    q[a] = s2;
+                }
+                for (int a = 0; a < 3; ++a) {
+                    float disp = 0.0f;
+                    if (dvf) disp = or_f_sample(dvf + ((size_t)S * 3 + a) * nvox, n, q[0], q[1], q[2]);
+                    volatile float base = q[a] + 0.5f;
+                    volatile float off = disp / dmm[a];
+                    volatile float r = base + off;
+                    t[a] = r;
+                }
+                int32_t ix = (int32_t)floorf(t[0]), iy = (int32_t)floorf(t[1]), iz = (int32_t)floorf(t[2]);
+                if (ix < 0 || ix >= n[0] || iy < 0 || iy >= n[1] || iz < 0 || iz >= n[2]) { ++drop; continue; }
+                size_t i = ((size_t)iz * n[1] + iy) * n[0] + ix;
+                E[i] += e;
+                M[i] += m;
+            }
+        }
+        for (size_t i = 0; i < nvox; ++i) {
+            if (M[i] > 0.0) accum[i] += E[i] / M[i];
+            if (e_sum) e_sum[i] += E[i];
+            if (m_sum) m_sum[i] += M[i];
+        }
+    }
+    if (mask)
+        for (size_t i = 0; i < nvox; ++i) if (!mask[i]) accum[i] = 0.0;
+    if (dropped) *dropped = drop;
+    free(E); free(M);
+    return OR_OK;
+}

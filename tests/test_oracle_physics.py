@@ -1,0 +1,221 @@
+"""Pins of the oracle's random numbers, calibration and physics tables.
+
+Every check compares the oracle with something other than its own code:
+published known-answer vectors, physical facts, fundamental constants, an
+independent adaptive quadrature, or a closed-form property of a sampling
+scheme.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ Philox
+def _kat():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(v, 16) for v in line.split()]
+        rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answers(orc):
+    """Philox4x32-10 reproduces the published known-answer vectors (SC'11)."""
+    rows = _kat()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        got = orc.philox4x32_10(ctr, key)
+        assert [int(v) for v in got] == want
+
+
+def test_block_uniforms_distribution(orc):
+    """Six 21-bit uniforms per block: in (0,1), mean 1/2, variance 1/12,
+    uncorrelated with each other and with the next block."""
+    n = 20000
+    u = np.array([orc.block_uniforms(7, h, 3, 1) for h in range(n)])
+    v = np.array([orc.block_uniforms(7, h, 3, 2) for h in range(n)])
+    assert np.all(u > 0.0) and np.all(u < 1.0)
+    se = 1.0 / math.sqrt(12.0 * n)
+    assert np.all(np.abs(u.mean(axis=0) - 0.5) < 5 * se)
+    assert np.all(np.abs(u.var(axis=0) - 1.0 / 12.0) < 0.004)
+    c = np.corrcoef(np.hstack([u, v]).T)
+    off = c[~np.eye(12, dtype=bool)]
+    assert np.max(np.abs(off)) < 5.0 / math.sqrt(n)
+    # 2^21 grid: k + 1/2 over 2^21
+    k = u * 2 ** 21 - 0.5
+    assert np.all(np.abs(k - np.round(k)) < 1e-9)
+
+
+def test_streams_differ_by_history_stream_and_seed(orc):
+    a = orc.block_uniforms(1, 5, 0, 1)
+    assert not np.array_equal(a, orc.block_uniforms(1, 6, 0, 1))
+    assert not np.array_equal(a, orc.block_uniforms(1, 5, 1, 1))
+    assert not np.array_equal(a, orc.block_uniforms(2, 5, 0, 1))
+    assert not np.array_equal(a, orc.block_uniforms(1, 5 + (1 << 32), 0, 1))
+    assert np.array_equal(a, orc.block_uniforms(1, 5, 0, 1))
+
+
+# ------------------------------------------------------------ calibration
+def test_calibration_physical_anchors(orc):
+    """Water (HU 0) is the reference medium: density and SPR exactly 1.
+    Air (HU -1000) has the density of air at room conditions, 0.0012 g/cm^3."""
+    assert orc.rho(0) == 1.0 and orc.spr(0) == 1.0
+    assert abs(orc.rho(-1000) - 0.0012) < 1e-12
+    assert orc.spr(-1000) < 0.002
+    # monotone, clamped outside [-1000, 3000]
+    hu = np.arange(-1100, 3101, 7)
+    r = np.array([orc.rho(h) for h in hu])
+    s = np.array([orc.spr(h) for h in hu])
+    assert np.all(np.diff(r) >= 0) and np.all(np.diff(s) >= 0)
+    assert orc.rho(-2000) == orc.rho(-1000) and orc.rho(5000) == orc.rho(3000)
+
+
+# ------------------------------------------------------ stopping / range
+def test_constants_from_codata(orc):
+    """K = 4 pi N_A r_e^2 m_e c^2 = 0.307075 MeV cm^2/mol follows from CODATA
+    r_e, N_A and m_e c^2; the oracle's Bohr variance per cm of water at
+    non-relativistic speed must equal 4 pi N_A r_e^2 (m_e c^2)^2 Z/A."""
+    r_e = 2.8179403262e-13      # cm
+    n_a = 6.02214076e23         # 1/mol
+    me = 0.51099895000          # MeV
+    k = 4.0 * math.pi * n_a * r_e ** 2 * me
+    assert abs(k - 0.307075) < 2e-6
+    kb = 4.0 * math.pi * n_a * r_e ** 2 * me ** 2 * 0.55509
+    v = orc.bohr_var(1e-6, 10.0)                 # 1 cm of water, gamma -> 1
+    assert abs(v - kb) / kb < 1e-5
+    # relativistic factor (1 - beta^2/2)/(1 - beta^2) at 200 MeV
+    g = 1.0 + 200.0 / 938.27208816
+    b2 = 1.0 - 1.0 / (g * g)
+    assert abs(orc.bohr_var(200.0, 10.0) / v - (1 - b2 / 2) / (1 - b2)) < 1e-6
+
+
+def test_bragg_kleeman(orc):
+    """CSDA range of protons in water follows the Bragg-Kleeman rule
+    R = 0.0022 cm * E^1.77 (Bortfeld, Med. Phys. 24, 2024, 1997) to within
+    about 2 % over the therapeutic range."""
+    for e in (70.0, 100.0, 150.0, 200.0, 220.0):
+        bk = 10.0 * 0.0022 * e ** 1.77
+        assert abs(orc.range_mm(e) - bk) / bk < 0.02, e
+    # local exponent d ln R / d ln E close to 1.77
+    for e in (80.0, 150.0, 200.0):
+        g = (math.log(orc.range_mm(e * 1.01)) - math.log(orc.range_mm(e / 1.01))) / (2 * math.log(1.01))
+        assert abs(g - 1.77) < 0.06
+
+
+def test_range_against_adaptive_quadrature(orc):
+    """R(E) = integral of 1/S from E_cut: oracle's node table + Gauss-Legendre
+    against scipy's adaptive Gauss-Kronrod (QUADPACK)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    for e in (1.0, 5.3, 30.0, 70.0, 150.0, 199.99, 250.0):
+        ref, err = integrate.quad(lambda x: 1.0 / orc.bethe_sw(x), 0.5, e,
+                                  epsabs=1e-13, epsrel=1e-12, limit=200)
+        assert abs(orc.range_mm(e) - 10.0 * ref) < 1e-6 + 1e-9 * ref * 10.0, e
+
+
+def test_energy_from_range_inverts(orc):
+    for e in np.linspace(0.6, 249.0, 57):
+        assert abs(orc.energy_from_range(orc.range_mm(e)) - e) < 1e-9 * e
+    assert orc.energy_from_range(0.0) == 0.5
+    assert orc.energy_from_range(-1.0) == 0.5
+    rs = [orc.range_mm(e) for e in np.linspace(0.5, 250.0, 300)]
+    assert np.all(np.diff(rs) > 0)
+
+
+def test_nuclear_cross_section_shape(orc):
+    assert orc.sigma_nuc(5.0) == 0.0 and orc.sigma_nuc(7.0) == 0.0
+    assert abs(orc.sigma_nuc(1e4) - 0.0123) < 1e-12
+    s = [orc.sigma_nuc(e) for e in np.linspace(7.0, 250.0, 100)]
+    assert np.all(np.diff(s) > 0)
+
+
+def test_pv_relativistic_kinematics(orc):
+    """p v = p^2 c^2 / (E_tot): check against momentum from E^2 = p^2 + m^2."""
+    mp = 938.27208816
+    for t in (1.0, 70.0, 230.0):
+        et = t + mp
+        p2 = et * et - mp * mp
+        assert abs(orc.pv(t) - p2 / et) < 1e-9 * t
+
+
+# --------------------------------------------------- one-step sampling
+def test_single_step_moments(orc):
+    """Highland/PDG correlated sampling over one step of length s: for each
+    transverse plane Var(y) = s^2 theta0^2 / 3, Cov(y, theta) = s theta0^2 / 2,
+    i.e. Var(y)/Var(theta) = s^2/3 and Cov/Var(theta) = s/2; planes
+    independent; straggling variance linear in the water-equivalent step."""
+    n = 40000
+    s = 1.7
+    rows = np.array([orc.single_step(0, 120.0, 0.05, s, 11, h) for h in range(n)])
+    th1, y1, th2, y2 = rows[:, 1], rows[:, 2], rows[:, 3], rows[:, 4]
+    vth = th1.var()
+    assert abs(y1.var() / vth - s * s / 3.0) / (s * s / 3.0) < 0.03
+    assert abs(np.mean(y1 * th1) / vth - s / 2.0) / (s / 2.0) < 0.03
+    assert abs(th2.var() / vth - 1.0) < 0.03
+    assert abs(np.corrcoef(th1, th2)[0, 1]) < 0.03
+    assert abs(np.mean(th1)) < 5 * math.sqrt(vth / n)
+    # straggling: ratio of variances at two step lengths equals the ratio of
+    # lengths (the Bohr variance is proportional to the path)
+    a = np.array([orc.single_step(0, 120.0, 0.05, 0.5, 12, h)[0] for h in range(n)])
+    b = np.array([orc.single_step(0, 120.0, 0.05, 2.0, 12, h)[0] for h in range(n)])
+    assert abs(b.var() / a.var() - 4.0) / 4.0 < 0.05
+
+
+def test_highland_cumulative_form_telescopes(orc):
+    """theta0^2 over [u0, u0+a+b] equals the sum over [u0, u0+a] and
+    [u0+a, u0+a+b] (step-size independence of the cumulative form)."""
+    e = 150.0
+    whole = orc.highland_theta2(e, 0.02, 0.05)
+    parts = orc.highland_theta2(e, 0.02, 0.02) + orc.highland_theta2(e, 0.04, 0.03)
+    assert abs(whole - parts) < 1e-15
+    # g(0) = 0: theta0^2 from zero thickness grows from zero
+    assert orc.highland_theta2(e, 0.0, 0.0) == 0.0
+    assert orc.highland_theta2(e, 0.0, 1e-3) > 0.0
+
+
+def _substeps(orc, hu, e, u0, s, f, n=64):
+    """Sum of a per-step quantity over n equal sub-steps, each starting from
+    the CSDA energy and radiation thickness reached by the previous ones."""
+    x0_mm = 360.8                # water radiation length 36.08 g/cm^2 (PDG)
+    tot, u = 0.0, u0
+    ds = s / n
+    for _ in range(n):
+        tot += f(e, u, ds)
+        u += ds * orc.rho(hu) / x0_mm
+        e = orc.energy_from_range(orc.range_mm(e) - ds * orc.spr(hu))
+    return tot
+
+
+@pytest.mark.parametrize("hu", [0, 1200])
+def test_step_quantities_consistent_under_substepping(orc, hu):
+    """A step's scattering variance and nuclear optical depth are integrals
+    along the path; taking the integrand at the step-mean energy makes one
+    large step agree with many small ones to second order.  Checked near the
+    end of range where the energy changes most within a step."""
+    for e in (20.0, 60.0):
+        s = 0.25 * orc.range_mm(e) / orc.spr(hu)
+        one = orc.step_theta2(hu, e, 0.05, s)
+        many = _substeps(orc, hu, e, 0.05, s, lambda ee, uu, ds: orc.step_theta2(hu, ee, uu, ds))
+        assert abs(one - many) / many < 0.01, (e, one, many)
+        one = orc.step_tau(hu, e, s)
+        many = _substeps(orc, hu, e, 0.05, s, lambda ee, uu, ds: orc.step_tau(hu, ee, ds))
+        assert abs(one - many) / many < 0.01, (e, one, many)
+
+
+def test_transverse_frame_is_orthonormal(orc):
+    """(d, e1, e2) must be a right-handed orthonormal basis for every unit d,
+    including directions along and against each axis."""
+    rng = np.random.default_rng(8)
+    dirs = [np.array(v, float) for v in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                                         (0, 0, 1), (0, 0, -1))]
+    dirs += [v / np.linalg.norm(v) for v in rng.normal(size=(200, 3))]
+    for d in dirs:
+        e1, e2 = orc.frame(d)
+        m = np.stack([e1, e2, d])
+        np.testing.assert_allclose(m @ m.T, np.eye(3), atol=1e-12)
+        np.testing.assert_allclose(np.cross(e1, e2), d, atol=1e-12)
