@@ -1,0 +1,238 @@
+/*
+ * dose.h -- C ABI of the GB300 Monte Carlo proton dose engine (libdose).
+ *
+ * The engine is the hot path of the 4D-dose calculator of Pepin et al.
+ * (arXiv:1809.03927): per-phase Monte Carlo dose (Sec. 2.C) of the subplans
+ * that the delivery simulation (Sec. 2.B, App. A) assigns to the breathing
+ * phases of a 4DCT (Sec. 2.A), and the energy/mass-transfer accumulation of
+ * the phase doses onto a reference phase (Sec. 2.D.2, Eqs. 2, 4-6).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Return value   DOSE_OK (0) or a negative dose_status.  Nothing is thrown
+ *                across the ABI.  dose_last_error(ctx) describes the last
+ *                failure on that context (dose_last_error(NULL): the last
+ *                failure of a call that had no context yet, per thread).
+ * Pointers       plain host or device pointers; every `*_on_device` flag
+ *                says which (0: host memory, 1: device memory of the
+ *                context's GPU).  Inputs are borrowed for the duration of
+ *                the call only: the library copies what it keeps.
+ * Ownership      a dose_ctx owns every device buffer it creates (HU grids,
+ *                densities, plan, subplans, tallies, doses, accumulation
+ *                buffers) and frees them in dose_destroy.
+ * Streams        `stream` is a cudaStream_t passed as void* (NULL = the
+ *                legacy default stream).  Calls enqueue their work on it and
+ *                return without waiting, except dose_read into host memory,
+ *                which waits for the stream (bounded by DOSE_OPT_TIMEOUT_MS).
+ * Layout         3D grids are x fastest: index = (k * ny + j) * nx + i.  A
+ *                voxel (i, j, k) covers [i dx, (i+1) dx) x [j dy, (j+1) dy) x
+ *                [k dz, (k+1) dz) in grid millimetres; `origin_mm` is the
+ *                patient-frame position of the grid corner.  Multi-phase
+ *                arrays are phase-major: phase p starts at p * nvox.
+ * Threading      a context and the contexts viewing its grid must not be
+ *                used from two host threads or two streams at the same time.
+ * Determinism    every history draws from a counter-based Philox4x32-10
+ *                stream keyed by (seed, history index, phase); tallies are
+ *                64-bit integers, so results are bit-identical run to run,
+ *                for any launch shape and any batching of histories.
+ */
+#ifndef DOSE_H
+#define DOSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dose_ctx dose_ctx;              /* opaque, owned by the library */
+
+typedef enum dose_status {
+    DOSE_OK = 0,
+    DOSE_EINVAL = -1,       /* bad argument; nothing was enqueued          */
+    DOSE_ENOMEM = -2,       /* device or host allocation failed            */
+    DOSE_ECUDA = -3,        /* CUDA runtime error (no device, launch, ...) */
+    DOSE_ETIMEOUT = -4,     /* a wait exceeded DOSE_OPT_TIMEOUT_MS         */
+    DOSE_ESTEPLIMIT = -5,   /* a history hit the step cap (read back)      */
+    DOSE_ESTATE = -6        /* call out of order (e.g. run before spots)   */
+} dose_status;
+
+/* One plan spot (Sec. 1 and 2.A: position, energy and weight).  x_mm, y_mm
+ * are patient-frame coordinates on the two axes other than the beam axis,
+ * lower axis first (beam along z: x, y; along y: x, z; along x: y, z).
+ * sigma_mm is the Gaussian spot size on the entry plane.  Spots of one
+ * field are delivered in array order; a layer is a maximal run of equal
+ * `layer` values within the field's spots.  32 bytes.                     */
+typedef struct dose_spot {
+    float x_mm, y_mm, energy_MeV, sigma_mm;
+    uint64_t protons;
+    int32_t layer, field;
+} dose_spot;
+
+/* Delivery-clock inputs of the beam-delivery simulation (Sec. 2.B, App. A),
+ * integer nanoseconds.  start_phase < 0 draws the start phase of field f as
+ * word 0 of Philox4x32-10(counter (f,0,0,0), key seed) mod n_phases.  Gated
+ * delivery (gated != 0) beams only in phases gate_first..gate_last; at a
+ * gate-off the clock skips to the start of the next gate_first phase and
+ * adds discard_ns.  Each layer is painted `repaints` times, a spot giving
+ * floor(protons/repaints) per painting and the remainder in the last.
+ * A spot's spill time is protons * 1e9 / rate_protons_per_s ns; a spill
+ * that crosses a phase boundary is split by time share (floor per portion,
+ * remainder to the last).  Switch times precede every spill but the first
+ * of a field: layer_switch_ns before a layer's first spill, spot_switch_ns
+ * otherwise.  period_sigma_ns must be 0.                                  */
+typedef struct dose_delivery {
+    int32_t n_phases, start_phase, gated, gate_first, gate_last, repaints;
+    int64_t period_ns, period_sigma_ns, spot_switch_ns, layer_switch_ns, discard_ns;
+    uint64_t rate_protons_per_s, seed;
+} dose_delivery;
+
+/* dose_read selectors */
+enum {
+    DOSE_PHASE_DOSE = 0,     /* float32[nvox]  Gy, phase `phase`                    */
+    DOSE_DENSITY = 1,        /* float32[nvox]  g/cm^3 of phase `phase`              */
+    DOSE_ACCUM = 2,          /* float32[nvox]  Gy, accumulated on the ref phase     */
+    DOSE_TALLY_I64 = 3,      /* uint64[nvox]   energy in units of 2^-24 MeV x history
+                                weight (weight = spot protons / its histories / (W/N)) */
+    DOSE_SUBPLAN = 4,        /* uint64[n_phases * n_spots]  protons per phase, spot */
+    DOSE_ENERGY_LEDGER = 5,  /* uint64[8] of phase `phase`: deposited, escaped,
+                                removed, incident (2^-24 MeV units), steps,
+                                histories, status flags, W (protons of the phase) */
+    DOSE_STATUS = 6,         /* int32[1]: DOSE_OK or DOSE_ESTEPLIMIT for `phase`     */
+    DOSE_START_PHASE = 7,    /* int32[n_fields]  start phase of each field          */
+    DOSE_FIELD_END_NS = 8,   /* int64[n_fields]  delivery clock at each field's end */
+    DOSE_EMTM_STATS = 9,     /* uint64[4]: subvoxels pushed, dropped (mapped outside),
+                                atomic pairs issued, reserved                       */
+    DOSE_HIST_PREFIX = 10    /* uint64[n_spots + 1] of phase `phase`: first history of
+                                each spot (histories of spot s = p[s+1] - p[s])      */
+};
+
+/* Physics switches (dose_set_option DOSE_OPT_PHYSICS), all on by default. */
+enum { DOSE_PHYS_STRAGGLING = 1, DOSE_PHYS_MCS = 2, DOSE_PHYS_NUCLEAR = 4, DOSE_PHYS_ALL = 7 };
+
+/* Options (dose_set_option).  Launch shape options change speed only,
+ * never results.                                                           */
+enum {
+    DOSE_OPT_PHYSICS = 0,         /* bit mask of DOSE_PHYS_*                     */
+    DOSE_OPT_MAX_STEPS = 1,       /* step cap per history (default 20000)        */
+    DOSE_OPT_BLOCK = 2,           /* transport threads per block (64..1024)      */
+    DOSE_OPT_BLOCKS_PER_SM = 3,   /* transport blocks per SM (0 = occupancy max) */
+    DOSE_OPT_CHUNK = 4,           /* histories a warp takes per queue pull       */
+    DOSE_OPT_TIMEOUT_MS = 5,      /* host wait bound for dose_read (default 600000) */
+    DOSE_OPT_FAIL_ALLOC_AFTER = 6 /* test hook: the n-th later device allocation
+                                     of this context fails (-1 = off)            */
+};
+
+/* Create a context holding a voxel grid of `n_phases` HU volumes (Sec. 2.A:
+ * one CT per breathing phase; Sec. 2.C: the dose grid is the CT grid) and
+ * convert HU to mass density (Sec. 2.C) on the device.
+ * hu: int16[n_phases * nx * ny * nz], host or device.  beam_dir must be a
+ * unit axis vector (+-x, +-y, +-z): the beam enters through the upstream
+ * face of the grid.  On failure *out is NULL and dose_last_error(NULL)
+ * says why.                                                                 */
+int dose_create_grid(dose_ctx **out, int nx, int ny, int nz, float dx_mm, float dy_mm,
+                     float dz_mm, const float origin_mm[3], int n_phases, const int16_t *hu,
+                     int hu_on_device, const float beam_dir[3], void *stream);
+
+/* A new context that shares `base`'s grid and densities (read-only, kept
+ * alive by a reference count) with its own plan, tallies and doses, so that
+ * many dose requests over one resident 4DCT need one copy of the CT.        */
+int dose_create_view(dose_ctx *base, dose_ctx **out);
+
+/* Load the plan (host array of n spots) and run the delivery simulation on
+ * the device (Sec. 2.B): the per-phase subplans (protons per phase and
+ * spot).  delivery = NULL puts every spot wholly on phase 0 (a static, 3D
+ * delivery).  Replaces any previous plan and clears all phase results.     */
+int dose_add_spots(dose_ctx *c, const dose_spot *spots, int64_t n,
+                   const dose_delivery *delivery, void *stream);
+
+/* Monte Carlo dose of one phase's subplan (Sec. 2.C): allocate n_histories
+ * over the spots in proportion to their protons (floor + largest remainder,
+ * ties to the lower index), transport them through the phase's CT with
+ * Philox streams keyed by (seed, history, phase), tally energy in 64-bit
+ * fixed point and normalise to Gy.  spr_scale multiplies every stopping-
+ * power ratio (range-uncertainty scenario); shift_mm (NULL = none) is a
+ * patient setup displacement applied to the beam geometry.                 */
+int dose_run_phase(dose_ctx *c, int phase, uint64_t n_histories, uint64_t seed,
+                   float spr_scale, const float shift_mm[3], void *stream);
+
+/* A ragged batch of transport jobs in one persistent launch.  Each job
+ * runs histories [hist_begin, hist_end) of an n_histories-history run of
+ * (ctx, phase); DOSE_JOB_CLEAR zeroes the job's tally and allocates its
+ * histories first, DOSE_JOB_FINISH normalises the tally to dose after the
+ * launch.  Splitting a run into slices over several batches gives the same
+ * bits as one call.  All contexts must live on the same GPU.              */
+enum { DOSE_JOB_CLEAR = 1, DOSE_JOB_FINISH = 2 };
+typedef struct dose_job {
+    dose_ctx *ctx;
+    int32_t phase;
+    uint32_t flags;
+    uint64_t n_histories;
+    uint64_t hist_begin, hist_end;
+    uint64_t seed;
+    float spr_scale;
+    float shift_mm[3];
+} dose_job;
+int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream);
+
+/* Supply the dose of one phase from outside (float32[nvox] Gy), e.g. to
+ * accumulate doses computed elsewhere.                                     */
+int dose_set_phase_dose(dose_ctx *c, int phase, const float *dose, int dose_on_device,
+                        void *stream);
+
+/* Accumulate the phase doses onto ref_phase (Sec. 2.D.2).  method 0 is the
+ * energy/mass-transfer method of Eqs. 4-6: every voxel of each source phase
+ * S != ref_phase is split into nsub[0] x nsub[1] x nsub[2] subvoxels whose
+ * centres move by S's DVF (trilinear between voxel centres, clamped at the
+ * edges) into the reference voxel whose half-open cell holds them; subvoxel
+ * mass rho_j v_k and energy rho_j v_k D_j are summed per reference voxel in
+ * 64-bit fixed point, D_i^S = sum E / sum M (0 where nothing lands), and
+ * D_i = D_i^R + sum_S D_i^S (Eq. 2), zero where mask == 0.
+ * dvf: float32[n_phases * 3 * nvox] mm, the displacement carrying a point
+ * of phase S to the reference (component-major per phase); NULL = identity.
+ * mask: uint8[nvox] or NULL (all ones).  method 1 (DIM, Eq. 3) is not
+ * provided and returns DOSE_EINVAL.  Every phase must have a dose.         */
+int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], const float *dvf,
+                             int dvf_on_device, const uint8_t *mask, int mask_on_device,
+                             int method, void *stream);
+
+/* Copy a result (see the selectors) into dst (`bytes` must equal its size).
+ * Into host memory the call waits for `stream`; into device memory it only
+ * enqueues the copy.                                                       */
+int dose_read(dose_ctx *c, int what, int phase, void *dst, size_t bytes, int dst_on_device,
+              void *stream);
+
+/* Set an option (DOSE_OPT_*).                                              */
+int dose_set_option(dose_ctx *c, int option, int64_t value);
+
+/* Free the context (waits for its device work).  NULL is a no-op.          */
+void dose_destroy(dose_ctx *c);
+
+/* Text of the last failure on c (or of this thread's last context-less
+ * failure when c is NULL).  Valid until the next call on c.               */
+const char *dose_last_error(const dose_ctx *c);
+
+/* Library version, for the binding's load check.                           */
+int dose_version(void);
+
+/* Self-test of the device random-number generator: Philox4x32-10 (Salmon
+ * et al., SC'11; the generator of Sec. 2.B, footnote b) of n counters
+ * ctr[4 i..4 i+3] under keys key[2 i..2 i+1] into out[4 i..], and the six
+ * 21-bit uniforms (k + 1/2) 2^-21 the transport draws from each block into
+ * uniforms[6 i..] (NULL: skipped).  All pointers are host memory; the call
+ * runs on the current device and waits for it.                              */
+int dose_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n,
+                      float *uniforms);
+
+/* Self-test of the device lookup tables: for each of the n energies E[i]
+ * (host, MeV) writes out[5 i..5 i+4] = CSDA range R(E) in mm of water, the
+ * energy at that range E(R(E)), the Bohr variance per mm of water path, the
+ * Highland coefficient (13.6/pv)^2 and the nuclear Sigma per mm, each
+ * interpolated exactly as the transport does.  Host memory; waits.         */
+int dose_debug_tables(const float *E, int n, float *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOSE_H */

@@ -53,6 +53,7 @@ class RunParams(C.Structure):
         ("spr_scale", C.c_double), ("shift", C.c_double * 3), ("max_steps", C.c_int64),
         ("nthreads", C.c_int32), ("n_depth_bins", C.c_int32), ("depth_bin_mm", C.c_double),
         ("n_planes", C.c_int32), ("plane_mm", C.c_double),
+        ("batch_count", C.c_uint64), ("batch_index", C.c_uint64),
     ]
 
 
@@ -207,9 +208,11 @@ def allocate(protons, n_hist):
 
 
 def transport(phantom, plan, n_hist, seed, stream=0, phase=None, hist_range=None,
-              physics=PHYS_ALL, spr_scale=1.0, shift=(0.0, 0.0, 0.0), max_steps=1_000_000,
-              nthreads=None, depth_bin_mm=0.0, n_depth_bins=0, plane_mm=0.0, n_planes=0):
-    """Run histories ``hist_range`` (default all) of an ``n_hist``-history run.
+              physics=PHYS_ALL, spr_scale=1.0, shift=(0.0, 0.0, 0.0), max_steps=20_000,
+              nthreads=None, depth_bin_mm=0.0, n_depth_bins=0, plane_mm=0.0, n_planes=0,
+              batch=None):
+    """Run histories ``hist_range`` (default all) of an ``n_hist``-history run;
+    ``batch=(b, B)`` keeps only the histories h with h mod B == b.
 
     Returns a dict: ``edep`` (nz, ny, nx) MeV x history weight, ``ledger``
     (deposited, escaped, removed, incident), ``steps``, ``status`` and, if
@@ -241,6 +244,8 @@ def transport(phantom, plan, n_hist, seed, stream=0, phase=None, hist_range=None
     P.nthreads = int(nthreads or os.cpu_count() or 1)
     P.n_depth_bins, P.depth_bin_mm = int(n_depth_bins), float(depth_bin_mm)
     P.n_planes, P.plane_mm = int(n_planes), float(plane_mm)
+    if batch is not None:
+        P.batch_index, P.batch_count = int(batch[0]), int(batch[1])
     edep = np.zeros((nz, ny, nx), dtype=np.float64)
     dd = np.zeros(n_depth_bins, np.float64) if n_depth_bins else None
     pw = np.zeros(n_planes, np.float64) if n_planes else None

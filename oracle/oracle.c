@@ -296,6 +296,19 @@ double or_bohr_var(double E, double sw_mm)
     return OR_K * OR_ME * OR_ZA * (sw_mm / 10.0) * 0.5 * (gam * gam + 1.0);
 }
 
+/* Straggling fluctuation of a step whose mean (CSDA) loss is dE_mean: the
+ * Bohr Gaussian sigma z, truncated symmetrically to [-dE_mean, +dE_mean] so
+ * that the step's loss stays in [0, 2 dE_mean] and its expectation is the
+ * CSDA loss for any step length (a one-sided cut at zero would add a
+ * positive bias of about 0.4 sigma on thin steps, where sigma >> dE_mean). */
+static double or_straggle(double dE_mean, double var, double z)
+{
+    double f = sqrt(var) * z;
+    if (f > dE_mean) f = dE_mean;
+    if (f < -dE_mean) f = -dE_mean;
+    return f;
+}
+
 /* Highland variance of the projected angle over radiation thickness
  * [u0, u0 + du]: (13.6 / pv)^2 (g(u0 + du) - g(u0)), pv at energy E.      */
 double or_highland_theta2(double E, double u0, double du)
@@ -381,6 +394,9 @@ typedef struct {
     double depth_bin_mm;
     int32_t n_planes;
     double plane_mm;             /* plane k at depth (k + 1) plane_mm */
+    /* run only the histories h of [hist_begin, hist_end) with
+       h mod batch_count == batch_index (batch_count 0 or 1: all)          */
+    uint64_t batch_count, batch_index;
 } or_run_params;
 
 typedef struct {
@@ -509,7 +525,6 @@ static void or_history(const or_run_params *P, const uint64_t *prefix,
     iv[ax] = P->beam_sign > 0 ? 0 : n[ax] - 1;
 
     double uthick = 0.0;                       /* radiation lengths so far */
-    const double scap = fmin(dd[0], fmin(dd[1], dd[2]));
     for (int64_t step = 0;; ++step) {
         if (step >= P->max_steps) {
             A->ledger[1] += E * w;
@@ -542,8 +557,9 @@ static void or_history(const or_run_params *P, const uint64_t *prefix,
             if (t < 0.0) t = 0.0;
             if (t < dbound) { dbound = t; across = k; }
         }
-        double sphys = fmax(OR_FSTEP * R0 / spr, OR_SMIN);
-        double s = fmin(scap, sphys);
+        /* the step ends at the voxel boundary or after the physics length,
+           whichever comes first */
+        double s = fmax(OR_FSTEP * R0 / spr, OR_SMIN);
         int geom = 0;
         if (dbound <= s) { s = dbound; geom = 1; }
 
@@ -572,8 +588,7 @@ static void or_history(const or_run_params *P, const uint64_t *prefix,
 
         double dE = E - E1c;
         if (P->physics & OR_PHYS_STRAG) {
-            dE += sqrt(or_bohr_var(E, sw)) * zA0;
-            if (dE < 0.0) dE = 0.0;
+            dE += or_straggle(dE, or_bohr_var(E, sw), zA0);
             if (dE > E) dE = E;
         }
         double E1 = E - dE;
@@ -625,12 +640,16 @@ static void or_history(const or_run_params *P, const uint64_t *prefix,
         or_depth_spread(P, A, z_start, or_depth_of(P, p), dE * w);
 
         /* voxel update: the crossed axis advances by one and its coordinate
-           is put on the crossed face; every other axis takes floor(p/d)    */
+           is put on the crossed face; every other axis keeps its index while
+           the position stays inside the voxel's closed extent [i d, (i+1) d]
+           and takes floor(p/d) once the lateral displacement has carried it
+           outside (keeping the index on a face avoids handing a particle
+           that sits on an edge back and forth between two voxels)          */
         for (int k = 0; k < 3; ++k) {
             if (geom && k == across) {
                 if (dir0[k] > 0.0) { iv[k] += 1; p[k] = iv[k] * dd[k]; }
                 else { p[k] = iv[k] * dd[k]; iv[k] -= 1; }
-            } else {
+            } else if (p[k] < iv[k] * dd[k] || p[k] > (iv[k] + 1) * dd[k]) {
                 iv[k] = (int32_t)floor(p[k] / dd[k]);
             }
         }
@@ -669,7 +688,10 @@ int or_transport(const or_run_params *P, or_run_out *O)
     }
 
     int nt = P->nthreads > 0 ? P->nthreads : 1;
-    uint64_t count = P->hist_end - P->hist_begin;
+    const uint64_t bc = P->batch_count > 1 ? P->batch_count : 1;
+    const uint64_t bi = bc > 1 ? P->batch_index % bc : 0;
+    const uint64_t first = P->hist_begin + (bi + bc - P->hist_begin % bc) % bc;
+    const uint64_t count = first < P->hist_end ? (P->hist_end - first + bc - 1) / bc : 0;
     if ((uint64_t)nt > count && count > 0) nt = (int)count;
     if (nt < 1) nt = 1;
     or_acc *acc = (or_acc *)calloc((size_t)nt, sizeof(or_acc));
@@ -691,9 +713,9 @@ int or_transport(const or_run_params *P, or_run_out *O)
 #pragma omp parallel for num_threads(nt) schedule(static)
 #endif
         for (int t = 0; t < nt; ++t) {
-            uint64_t b = P->hist_begin + count * (uint64_t)t / (uint64_t)nt;
-            uint64_t e = P->hist_begin + count * (uint64_t)(t + 1) / (uint64_t)nt;
-            for (uint64_t h = b; h < e; ++h) or_history(P, prefix, wts, h, &acc[t]);
+            uint64_t b = count * (uint64_t)t / (uint64_t)nt;
+            uint64_t e = count * (uint64_t)(t + 1) / (uint64_t)nt;
+            for (uint64_t k = b; k < e; ++k) or_history(P, prefix, wts, first + k * bc, &acc[t]);
         }
         /* fixed-order reduction */
         memset(O->ledger, 0, sizeof(O->ledger));
@@ -748,8 +770,8 @@ void or_single_step(int hu, double E, double u0, double s, uint64_t seed,
     or_box_muller(u[0], u[1], &zA0, &zA1);
     or_box_muller(u[2], u[3], &z1u, &z2u);
     or_box_muller(u[4], u[5], &z1v, &z2v);
-    double dE = E - E1c + sqrt(or_bohr_var(E, sw)) * zA0;
-    if (dE < 0.0) dE = 0.0;
+    double dE = E - E1c;
+    dE += or_straggle(dE, or_bohr_var(E, sw), zA0);
     if (dE > E) dE = E;
     double th2 = or_highland_theta2(Emean, u0, s * rho / OR_X0_MM);
     double th0 = th2 > 0.0 ? sqrt(th2) : 0.0;

@@ -1,0 +1,838 @@
+// C ABI of the dose engine (include/dose.h): context management, argument
+// validation and the launches of the engine's kernels.  Every step of the
+// dose computation runs in the kernels; this file only checks arguments,
+// owns device memory and enqueues work.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dose.h"
+#include "engine.cuh"
+#include "kernels.h"
+
+using namespace dose;
+
+namespace {
+
+constexpr int kVersion = 1;
+constexpr int kMaxSpots = 16384;
+constexpr int kMaxFields = 64;
+constexpr int kMaxDevices = 64;
+
+thread_local std::string g_thread_err;
+
+struct DeviceTables {
+    Tables *dev = nullptr;
+    float inv_ds = 0.0f;
+};
+std::mutex g_tab_mutex;
+DeviceTables g_tab[kMaxDevices];
+Tables *g_host_tables = nullptr;
+float g_host_inv_ds = 0.0f;
+
+struct Grid {
+    int n[3] = {0, 0, 0};
+    float d[3] = {0, 0, 0};
+    float origin[3] = {0, 0, 0};
+    int n_phases = 0;
+    int beam_axis = 2, beam_sign = 1;
+    long long nvox = 0;
+    int device = 0;
+    int16_t *hu = nullptr;
+    float *rho = nullptr;
+    std::atomic<int> refs{1};
+};
+
+struct PhaseState {
+    unsigned long long *tally = nullptr;
+    float *dose = nullptr;
+    unsigned long long *ledger = nullptr;
+    unsigned long long *prefix = nullptr;
+    float *wh = nullptr;
+    unsigned long long *rem = nullptr;
+    uint64_t n_hist = 0;
+    bool allocated = false;     // histories allocated for n_hist
+    bool has_dose = false;
+};
+
+}  // namespace
+
+struct dose_ctx {
+    Grid *g = nullptr;
+    int n_spots = 0;
+    float4 *spot = nullptr;
+    unsigned long long *protons = nullptr;
+    int *layer = nullptr;
+    int *field = nullptr;
+    unsigned long long *pp = nullptr;
+    int n_fields = 0;
+    int *start_phase = nullptr;
+    long long *field_end = nullptr;
+    bool have_plan = false;
+    std::vector<PhaseState> ph;
+    unsigned long long *tally_all = nullptr; // n_phases x nvox
+    float *dose_all = nullptr;               // n_phases x nvox
+    unsigned long long *ledger_all = nullptr;// n_phases x LED_WORDS
+    unsigned long long *em = nullptr;        // E then M, n_phases x nvox each
+    float *dvf_buf = nullptr;                // staging for host DVFs
+    uint8_t *mask_buf = nullptr;             // staging for a host mask
+    unsigned *maxbits = nullptr;
+    unsigned long long *emtm_stats = nullptr;
+    float *accum = nullptr;
+    bool have_accum = false;
+    TJob *d_jobs = nullptr;
+    int cap_jobs = 0;
+    AllocJob *d_alloc = nullptr;
+    NormJob *d_norm = nullptr;
+    int cap_aux = 0;
+    unsigned long long *d_counter = nullptr;
+    unsigned physics = DOSE_PHYS_ALL;
+    unsigned max_steps = 20000;
+    int block = 256;
+    int blocks_per_sm = 0;
+    unsigned chunk = 64;
+    long long timeout_ms = 600000;
+    long long fail_alloc_after = -1;
+    std::vector<void *> owned;
+    std::string err;
+};
+
+namespace {
+
+int fail(dose_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_thread_err = buf;
+    return code;
+}
+
+#define CK(c, call)                                                                      \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail((c), DOSE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int dalloc(dose_ctx *c, void **p, size_t bytes)
+{
+    if (c->fail_alloc_after >= 0) {
+        if (c->fail_alloc_after == 0) {
+            *p = nullptr;
+            return fail(c, DOSE_ENOMEM, "device allocation of %zu bytes failed (injected)", bytes);
+        }
+        --c->fail_alloc_after;
+    }
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, DOSE_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->owned.push_back(*p);
+    return DOSE_OK;
+}
+
+void dfree(dose_ctx *c, void *p)
+{
+    if (!p) return;
+    auto it = std::find(c->owned.begin(), c->owned.end(), p);
+    if (it != c->owned.end()) c->owned.erase(it);
+    cudaFree(p);
+}
+
+template <class T>
+int dalloc_t(dose_ctx *c, T **p, size_t count)
+{
+    return dalloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+int device_tables(dose_ctx *c, int dev, DeviceTables *out)
+{
+    std::lock_guard<std::mutex> lock(g_tab_mutex);
+    if (dev < 0 || dev >= kMaxDevices) return fail(c, DOSE_ECUDA, "device %d out of range", dev);
+    if (!g_host_tables) {
+        g_host_tables = new Tables;
+        build_tables(g_host_tables, &g_host_inv_ds);
+    }
+    if (!g_tab[dev].dev) {
+        Tables *t = nullptr;
+        cudaError_t e = cudaMalloc(&t, sizeof(Tables));
+        if (e != cudaSuccess) return fail(c, DOSE_ENOMEM, "tables: %s", cudaGetErrorString(e));
+        e = cudaMemcpy(t, g_host_tables, sizeof(Tables), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(t); return fail(c, DOSE_ECUDA, "tables: %s", cudaGetErrorString(e)); }
+        g_tab[dev].dev = t;
+        g_tab[dev].inv_ds = g_host_inv_ds;
+    }
+    *out = g_tab[dev];
+    return DOSE_OK;
+}
+
+int use_device(dose_ctx *c)
+{
+    CK(c, cudaSetDevice(c->g->device));
+    return DOSE_OK;
+}
+
+// Tallies, doses and ledgers of all phases live in three contiguous arrays
+// (phase-major), allocated on first use.
+int ensure_results(dose_ctx *c, cudaStream_t st)
+{
+    if (c->tally_all) return DOSE_OK;
+    const size_t nvox = (size_t)c->g->nvox, P = (size_t)c->g->n_phases;
+    int rc;
+    if ((rc = dalloc_t(c, &c->tally_all, P * nvox)) || (rc = dalloc_t(c, &c->dose_all, P * nvox)) ||
+        (rc = dalloc_t(c, &c->ledger_all, P * LED_WORDS))) {
+        dfree(c, c->tally_all); dfree(c, c->dose_all); dfree(c, c->ledger_all);
+        c->tally_all = nullptr; c->dose_all = nullptr; c->ledger_all = nullptr;
+        return rc;
+    }
+    CK(c, cudaMemsetAsync(c->ledger_all, 0, P * LED_WORDS * sizeof(unsigned long long), st));
+    for (size_t p = 0; p < P; ++p) {
+        c->ph[p].tally = c->tally_all + p * nvox;
+        c->ph[p].dose = c->dose_all + p * nvox;
+        c->ph[p].ledger = c->ledger_all + p * LED_WORDS;
+    }
+    return DOSE_OK;
+}
+
+int ensure_phase(dose_ctx *c, int p, cudaStream_t st)
+{
+    int rc;
+    if ((rc = ensure_results(c, st))) return rc;
+    PhaseState &P = c->ph[p];
+    if (!P.prefix) {
+        const int S = std::max(c->n_spots, 1);
+        if ((rc = dalloc_t(c, &P.prefix, S + 1))) return rc;
+        if ((rc = dalloc_t(c, &P.wh, S))) return rc;
+        if ((rc = dalloc_t(c, &P.rem, S))) return rc;
+    }
+    return DOSE_OK;
+}
+
+int ensure_workspace(dose_ctx *c, int n_jobs)
+{
+    int rc;
+    if (!c->d_counter && (rc = dalloc_t(c, &c->d_counter, 2))) return rc;
+    if (n_jobs > c->cap_jobs) {
+        dfree(c, c->d_jobs); dfree(c, c->d_alloc); dfree(c, c->d_norm);
+        c->d_jobs = nullptr; c->d_alloc = nullptr; c->d_norm = nullptr;
+        const int cap = std::max(n_jobs, 16);
+        if ((rc = dalloc_t(c, &c->d_jobs, cap))) return rc;
+        if ((rc = dalloc_t(c, &c->d_alloc, cap))) return rc;
+        if ((rc = dalloc_t(c, &c->d_norm, cap))) return rc;
+        c->cap_jobs = c->cap_aux = cap;
+    }
+    return DOSE_OK;
+}
+
+void free_plan(dose_ctx *c)
+{
+    dfree(c, c->spot); dfree(c, c->protons); dfree(c, c->layer); dfree(c, c->field);
+    dfree(c, c->pp); dfree(c, c->start_phase); dfree(c, c->field_end);
+    c->spot = nullptr; c->protons = nullptr; c->layer = nullptr; c->field = nullptr;
+    c->pp = nullptr; c->start_phase = nullptr; c->field_end = nullptr;
+    for (auto &P : c->ph) {
+        dfree(c, P.prefix); dfree(c, P.wh); dfree(c, P.rem);
+        P.prefix = nullptr; P.wh = nullptr; P.rem = nullptr;
+        P.allocated = false; P.has_dose = false; P.n_hist = 0;
+    }
+    c->have_plan = false;
+    c->have_accum = false;
+    c->n_spots = 0;
+}
+
+// Wait for `ev` with a bound; DOSE_ETIMEOUT if it does not complete.
+int wait_event(dose_ctx *c, cudaEvent_t ev)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return DOSE_OK;
+        if (e != cudaErrorNotReady) return fail(c, DOSE_ECUDA, "wait: %s", cudaGetErrorString(e));
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+            std::chrono::steady_clock::now() - t0).count();
+        if (ms > c->timeout_ms) return fail(c, DOSE_ETIMEOUT, "device work did not finish within %lld ms", c->timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(ms < 10 ? 20 : 500));
+    }
+}
+
+int sync_stream(dose_ctx *c, cudaStream_t st)
+{
+    cudaEvent_t ev;
+    CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, st);
+    int rc = e == cudaSuccess ? wait_event(c, ev) : fail(c, DOSE_ECUDA, "record: %s", cudaGetErrorString(e));
+    cudaEventDestroy(ev);
+    return rc;
+}
+
+bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+}  // namespace
+
+// ======================================================================== ABI
+extern "C" {
+
+int dose_version(void) { return kVersion; }
+
+const char *dose_last_error(const dose_ctx *c)
+{
+    return c ? c->err.c_str() : g_thread_err.c_str();
+}
+
+int dose_create_grid(dose_ctx **out, int nx, int ny, int nz, float dx_mm, float dy_mm, float dz_mm,
+                     const float origin_mm[3], int n_phases, const int16_t *hu, int hu_on_device,
+                     const float beam_dir[3], void *stream)
+{
+    if (!out) return fail(nullptr, DOSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(nullptr, DOSE_EINVAL, "grid dimensions must be positive");
+    if ((long long)nx * ny * nz > (1ll << 31) - 1)
+        return fail(nullptr, DOSE_EINVAL, "grid of %lld voxels exceeds 2^31-1", (long long)nx * ny * nz);
+    if (!(dx_mm > 0 && dy_mm > 0 && dz_mm > 0) || !std::isfinite(dx_mm) || !std::isfinite(dy_mm) || !std::isfinite(dz_mm))
+        return fail(nullptr, DOSE_EINVAL, "voxel sizes must be positive and finite");
+    if (!origin_mm || !finite3(origin_mm)) return fail(nullptr, DOSE_EINVAL, "origin must be 3 finite values");
+    if (n_phases <= 0 || n_phases > 4096) return fail(nullptr, DOSE_EINVAL, "n_phases must be in 1..4096");
+    if (!hu) return fail(nullptr, DOSE_EINVAL, "hu is NULL");
+    if (!beam_dir) return fail(nullptr, DOSE_EINVAL, "beam_dir is NULL");
+    int axis = -1, sign = 0, nz_count = 0;
+    for (int k = 0; k < 3; ++k) {
+        if (beam_dir[k] == 1.0f || beam_dir[k] == -1.0f) { axis = k; sign = beam_dir[k] > 0 ? 1 : -1; ++nz_count; }
+        else if (beam_dir[k] != 0.0f) return fail(nullptr, DOSE_EINVAL, "beam_dir must be a unit axis vector");
+    }
+    if (nz_count != 1) return fail(nullptr, DOSE_EINVAL, "beam_dir must be a unit axis vector");
+
+    dose_ctx *c = new dose_ctx;
+    c->g = new Grid;
+    Grid &g = *c->g;
+    g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
+    g.d[0] = dx_mm; g.d[1] = dy_mm; g.d[2] = dz_mm;
+    for (int k = 0; k < 3; ++k) g.origin[k] = origin_mm[k];
+    g.n_phases = n_phases;
+    g.beam_axis = axis; g.beam_sign = sign;
+    g.nvox = (long long)nx * ny * nz;
+    c->ph.resize(n_phases);
+    int rc = DOSE_OK;
+    cudaError_t e = cudaGetDevice(&g.device);
+    if (e != cudaSuccess) {
+        rc = fail(nullptr, DOSE_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+        delete c->g; delete c;
+        return rc;
+    }
+    DeviceTables tab;
+    const size_t n_all = (size_t)g.nvox * n_phases;
+    if ((rc = device_tables(c, g.device, &tab))) {
+        g_thread_err = c->err;
+        dose_destroy(c);
+        return rc;
+    }
+    e = cudaMalloc(&g.hu, n_all * sizeof(int16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g.rho, n_all * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(nullptr, DOSE_ENOMEM, "grid allocation (%zu voxels): %s", n_all, cudaGetErrorString(e));
+        dose_destroy(c);
+        return rc;
+    }
+    e = cudaMemcpyAsync(g.hu, hu, n_all * sizeof(int16_t),
+                        hu_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S(stream));
+    if (e == cudaSuccess) {
+        k_density<<<1184, 256, 0, S(stream)>>>(g.hu, g.rho, (long long)n_all, tab.dev);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        rc = fail(nullptr, DOSE_ECUDA, "grid upload: %s", cudaGetErrorString(e));
+        dose_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return DOSE_OK;
+}
+
+int dose_create_view(dose_ctx *base, dose_ctx **out)
+{
+    if (!out) return fail(nullptr, DOSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!base) return fail(nullptr, DOSE_EINVAL, "base is NULL");
+    dose_ctx *c = new dose_ctx;
+    c->g = base->g;
+    c->g->refs.fetch_add(1);
+    c->ph.resize(c->g->n_phases);
+    c->physics = base->physics;
+    c->max_steps = base->max_steps;
+    c->block = base->block;
+    c->blocks_per_sm = base->blocks_per_sm;
+    c->chunk = base->chunk;
+    c->timeout_ms = base->timeout_ms;
+    *out = c;
+    return DOSE_OK;
+}
+
+int dose_set_option(dose_ctx *c, int option, int64_t value)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    switch (option) {
+    case DOSE_OPT_PHYSICS:
+        if (value < 0 || value > 7) return fail(c, DOSE_EINVAL, "physics mask must be in 0..7");
+        c->physics = (unsigned)value; return DOSE_OK;
+    case DOSE_OPT_MAX_STEPS:
+        if (value < 1 || value > 100000000) return fail(c, DOSE_EINVAL, "max steps must be in 1..1e8");
+        c->max_steps = (unsigned)value; return DOSE_OK;
+    case DOSE_OPT_BLOCK:
+        if (value < 64 || value > 1024 || value % 32) return fail(c, DOSE_EINVAL, "block must be a multiple of 32 in 64..1024");
+        c->block = (int)value; return DOSE_OK;
+    case DOSE_OPT_BLOCKS_PER_SM:
+        if (value < 0 || value > 32) return fail(c, DOSE_EINVAL, "blocks per SM must be in 0..32");
+        c->blocks_per_sm = (int)value; return DOSE_OK;
+    case DOSE_OPT_CHUNK:
+        if (value < 1 || value > (1 << 20)) return fail(c, DOSE_EINVAL, "chunk must be in 1..2^20");
+        c->chunk = (unsigned)value; return DOSE_OK;
+    case DOSE_OPT_TIMEOUT_MS:
+        if (value < 1) return fail(c, DOSE_EINVAL, "timeout must be positive");
+        c->timeout_ms = value; return DOSE_OK;
+    case DOSE_OPT_FAIL_ALLOC_AFTER:
+        c->fail_alloc_after = value < 0 ? -1 : value; return DOSE_OK;
+    default:
+        return fail(c, DOSE_EINVAL, "unknown option %d", option);
+    }
+}
+
+int dose_add_spots(dose_ctx *c, const dose_spot *spots, int64_t n, const dose_delivery *dl, void *stream)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (!spots) return fail(c, DOSE_EINVAL, "spots is NULL");
+    if (n <= 0 || n > kMaxSpots) return fail(c, DOSE_EINVAL, "number of spots must be in 1..%d", kMaxSpots);
+    const int P = c->g->n_phases;
+    int n_fields = 0;
+    unsigned long long max_p = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const dose_spot &q = spots[s];
+        if (!(q.energy_MeV >= 1.0f && q.energy_MeV <= 250.0f))
+            return fail(c, DOSE_EINVAL, "spot %lld: energy %g MeV outside 1..250", (long long)s, q.energy_MeV);
+        if (!(q.sigma_mm >= 0.0f) || !std::isfinite(q.sigma_mm) || !std::isfinite(q.x_mm) || !std::isfinite(q.y_mm))
+            return fail(c, DOSE_EINVAL, "spot %lld: position and sigma must be finite, sigma >= 0", (long long)s);
+        if (q.field < 0 || q.field >= kMaxFields)
+            return fail(c, DOSE_EINVAL, "spot %lld: field %d outside 0..%d", (long long)s, q.field, kMaxFields - 1);
+        n_fields = std::max(n_fields, q.field + 1);
+        max_p = std::max(max_p, (unsigned long long)q.protons);
+    }
+    unsigned long long total = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        if (total + spots[s].protons < total) return fail(c, DOSE_EINVAL, "total protons overflow 64 bits");
+        total += spots[s].protons;
+    }
+    if (dl) {
+        if (dl->n_phases != P) return fail(c, DOSE_EINVAL, "delivery n_phases %d != grid phases %d", dl->n_phases, P);
+        if (dl->repaints < 1) return fail(c, DOSE_EINVAL, "repaints must be >= 1");
+        if (dl->period_ns <= 0 || dl->period_ns / P <= 0) return fail(c, DOSE_EINVAL, "period too short");
+        if (dl->period_sigma_ns != 0) return fail(c, DOSE_EINVAL, "irregular breathing (period_sigma_ns != 0) is not supported");
+        if (dl->rate_protons_per_s == 0) return fail(c, DOSE_EINVAL, "rate must be positive");
+        if (dl->spot_switch_ns < 0 || dl->layer_switch_ns < 0) return fail(c, DOSE_EINVAL, "switch times must be >= 0");
+        if (dl->start_phase >= P) return fail(c, DOSE_EINVAL, "start phase %d >= n_phases", dl->start_phase);
+        if (dl->gated) {
+            if (dl->gate_first < 0 || dl->gate_last >= P || dl->gate_first > dl->gate_last)
+                return fail(c, DOSE_EINVAL, "gate window must satisfy 0 <= first <= last < n_phases");
+            const long long tph = dl->period_ns / P;
+            if (dl->discard_ns < 0 || dl->discard_ns >= (long long)(dl->gate_last - dl->gate_first + 1) * tph)
+                return fail(c, DOSE_EINVAL, "discard time must be shorter than the gate window");
+        }
+        // the clock must stay far from overflow: total spill + switches < 2^62 ns
+        const long double spill = (long double)total * 1e9L / (long double)dl->rate_protons_per_s;
+        const long double sw = (long double)n * dl->repaints * (long double)std::max(dl->spot_switch_ns, dl->layer_switch_ns);
+        const long double waits = (long double)n * dl->repaints * (long double)dl->period_ns;
+        if (spill + sw + waits > 4.0e18L) return fail(c, DOSE_EINVAL, "delivery clock would overflow");
+    }
+    int rc;
+    if ((rc = use_device(c))) return rc;
+    free_plan(c);
+    std::vector<float4> sp(n);
+    std::vector<unsigned long long> pr(n);
+    std::vector<int> la(n), fi(n);
+    for (int64_t s = 0; s < n; ++s) {
+        sp[s] = make_float4(spots[s].x_mm, spots[s].y_mm, spots[s].energy_MeV, spots[s].sigma_mm);
+        pr[s] = spots[s].protons;
+        la[s] = spots[s].layer;
+        fi[s] = spots[s].field;
+    }
+    c->n_spots = (int)n;
+    c->n_fields = n_fields;
+    if ((rc = dalloc_t(c, &c->spot, n)) || (rc = dalloc_t(c, &c->protons, n)) ||
+        (rc = dalloc_t(c, &c->layer, n)) || (rc = dalloc_t(c, &c->field, n)) ||
+        (rc = dalloc_t(c, &c->pp, (size_t)n * P)) || (rc = dalloc_t(c, &c->start_phase, n_fields)) ||
+        (rc = dalloc_t(c, &c->field_end, n_fields))) {
+        free_plan(c);
+        return rc;
+    }
+    cudaStream_t st = S(stream);
+    CK(c, cudaMemcpyAsync(c->spot, sp.data(), n * sizeof(float4), cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemcpyAsync(c->protons, pr.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemcpyAsync(c->layer, la.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemcpyAsync(c->field, fi.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemsetAsync(c->pp, 0, (size_t)n * P * sizeof(unsigned long long), st));
+    if (dl) {
+        TimelineArgs a;
+        a.protons = c->protons; a.layer = c->layer; a.field = c->field; a.n_spots = (int)n;
+        a.n_phases = P; a.start_phase = dl->start_phase; a.gated = dl->gated;
+        a.gate_first = dl->gate_first; a.gate_last = dl->gate_last; a.repaints = dl->repaints;
+        a.tph = dl->period_ns / P; a.spot_switch = dl->spot_switch_ns; a.layer_switch = dl->layer_switch_ns;
+        a.discard = dl->gated ? dl->discard_ns : 0; a.rate = dl->rate_protons_per_s; a.seed = dl->seed;
+        a.pp = c->pp; a.field_end = c->field_end; a.start_out = c->start_phase; a.n_fields = n_fields;
+        k_timeline<<<1, 64, 0, st>>>(a);
+        CK(c, cudaGetLastError());
+    } else {
+        CK(c, cudaMemcpyAsync(c->pp, c->protons, n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+        CK(c, cudaMemsetAsync(c->start_phase, 0, n_fields * sizeof(int), st));
+        CK(c, cudaMemsetAsync(c->field_end, 0, n_fields * sizeof(long long), st));
+    }
+    c->have_plan = true;
+    return DOSE_OK;
+}
+
+int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
+{
+    if (!jobs || n_jobs <= 0) return fail(nullptr, DOSE_EINVAL, "no jobs");
+    dose_ctx *c0 = jobs[0].ctx;
+    if (!c0) return fail(nullptr, DOSE_EINVAL, "job 0 has no context");
+    for (int j = 0; j < n_jobs; ++j) {
+        const dose_job &J = jobs[j];
+        dose_ctx *c = J.ctx;
+        if (!c) return fail(c0, DOSE_EINVAL, "job %d has no context", j);
+        if (c->g->device != c0->g->device) return fail(c0, DOSE_EINVAL, "job %d is on another GPU", j);
+        if (!c->have_plan) return fail(c0, DOSE_ESTATE, "job %d: no spots loaded", j);
+        if (J.phase < 0 || J.phase >= c->g->n_phases) return fail(c0, DOSE_EINVAL, "job %d: phase %d out of range", j, J.phase);
+        if (J.n_histories == 0) return fail(c0, DOSE_EINVAL, "job %d: n_histories is 0", j);
+        if (J.hist_begin > J.hist_end || J.hist_end > J.n_histories)
+            return fail(c0, DOSE_EINVAL, "job %d: history range [%llu, %llu) outside [0, %llu)", j,
+                        (unsigned long long)J.hist_begin, (unsigned long long)J.hist_end,
+                        (unsigned long long)J.n_histories);
+        if (!(J.spr_scale > 0.1f && J.spr_scale < 10.0f)) return fail(c0, DOSE_EINVAL, "job %d: spr_scale out of range", j);
+        if (!finite3(J.shift_mm)) return fail(c0, DOSE_EINVAL, "job %d: shift must be finite", j);
+        const PhaseState &P = c->ph[J.phase];
+        if (!(J.flags & DOSE_JOB_CLEAR) && (!P.allocated || P.n_hist != J.n_histories))
+            return fail(c0, DOSE_ESTATE, "job %d: phase not started with DOSE_JOB_CLEAR for %llu histories", j,
+                        (unsigned long long)J.n_histories);
+        for (int k = 0; k < j; ++k)
+            if (jobs[k].ctx == c && jobs[k].phase == J.phase && ((J.flags | jobs[k].flags) & DOSE_JOB_CLEAR))
+                return fail(c0, DOSE_EINVAL, "jobs %d and %d clear the same phase", k, j);
+    }
+    int rc;
+    if ((rc = use_device(c0))) return rc;
+    DeviceTables tab;
+    if ((rc = device_tables(c0, c0->g->device, &tab))) return rc;
+    if ((rc = ensure_workspace(c0, n_jobs))) return rc;
+    cudaStream_t st = S(stream);
+    std::vector<AllocJob> aj;
+    std::vector<TJob> tj;
+    std::vector<NormJob> nj;
+    unsigned long long work = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const dose_job &J = jobs[j];
+        dose_ctx *c = J.ctx;
+        if ((rc = ensure_phase(c, J.phase, st))) { if (c != c0) c0->err = c->err; return rc; }
+        PhaseState &P = c->ph[J.phase];
+        const Grid &g = *c->g;
+        if (J.flags & DOSE_JOB_CLEAR) {
+            CK(c0, cudaMemsetAsync(P.tally, 0, g.nvox * sizeof(unsigned long long), st));
+            CK(c0, cudaMemsetAsync(P.ledger, 0, LED_WORDS * sizeof(unsigned long long), st));
+            AllocJob a;
+            a.protons = c->pp + (size_t)J.phase * c->n_spots;
+            a.rem = P.rem; a.prefix = P.prefix; a.wh = P.wh; a.ledger = P.ledger;
+            a.n_spots = c->n_spots; a.n_hist = J.n_histories;
+            aj.push_back(a);
+            P.n_hist = J.n_histories;
+            P.allocated = true;
+            P.has_dose = false;
+            c->have_accum = false;
+        }
+        const unsigned long long cnt = J.hist_end - J.hist_begin;
+        if (cnt) {
+            TJob t;
+            t.hu = g.hu + (size_t)J.phase * g.nvox;
+            t.tally = P.tally; t.ledger = P.ledger;
+            t.spot = c->spot; t.wh = P.wh; t.prefix = P.prefix; t.n_spots = c->n_spots;
+            t.nx = g.n[0]; t.ny = g.n[1]; t.nz = g.n[2];
+            t.dx = g.d[0]; t.dy = g.d[1]; t.dz = g.d[2];
+            const int a = g.beam_axis, b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+            t.ob = g.origin[b] + J.shift_mm[b];
+            t.oc = g.origin[cc] + J.shift_mm[cc];
+            t.beam_axis = a; t.beam_sign = g.beam_sign;
+            t.spr_scale = J.spr_scale; t.physics = c->physics; t.max_steps = c->max_steps;
+            t.key0 = (unsigned)J.seed; t.key1 = (unsigned)(J.seed >> 32); t.stream = (unsigned)J.phase;
+            t.hist_begin = J.hist_begin; t.work_begin = work;
+            tj.push_back(t);
+            work += cnt;
+        }
+        if (J.flags & DOSE_JOB_FINISH) {
+            NormJob nm;
+            nm.tally = P.tally; nm.ledger = P.ledger; nm.rho = g.rho + (size_t)J.phase * g.nvox;
+            nm.dose = P.dose; nm.n_hist = J.n_histories;
+            nm.voxel_cm3 = (double)g.d[0] * g.d[1] * g.d[2] / 1000.0;
+            nm.nvox = g.nvox;
+            nj.push_back(nm);
+            P.has_dose = true;
+        }
+    }
+    if (!aj.empty()) {
+        CK(c0, cudaMemcpyAsync(c0->d_alloc, aj.data(), aj.size() * sizeof(AllocJob), cudaMemcpyHostToDevice, st));
+        k_alloc<<<(unsigned)aj.size(), 1024, 0, st>>>(c0->d_alloc);
+        CK(c0, cudaGetLastError());
+    }
+    if (work) {
+        CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
+        CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
+        const size_t smem = sizeof(Tables);
+        CK(c0, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int sms = 0;
+        CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->g->device));
+        int per_sm = c0->blocks_per_sm;
+        if (per_sm <= 0) {
+            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport, c0->block, smem));
+            if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
+        }
+        const unsigned long long warps = (unsigned long long)sms * per_sm * (c0->block / 32);
+        unsigned chunk = c0->chunk;
+        // keep at least ~4 pulls per warp so the tail stays short
+        while (chunk > 32 && (unsigned long long)chunk * warps * 4 > work) chunk >>= 1;
+        k_transport<<<sms * per_sm, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
+                                                           tab.dev, tab.inv_ds, chunk);
+        CK(c0, cudaGetLastError());
+    }
+    if (!nj.empty()) {
+        CK(c0, cudaMemcpyAsync(c0->d_norm, nj.data(), nj.size() * sizeof(NormJob), cudaMemcpyHostToDevice, st));
+        dim3 grid(256, (unsigned)nj.size());
+        k_normalise<<<grid, 256, 0, st>>>(c0->d_norm);
+        CK(c0, cudaGetLastError());
+    }
+    return DOSE_OK;
+}
+
+int dose_run_phase(dose_ctx *c, int phase, uint64_t n_histories, uint64_t seed, float spr_scale,
+                   const float shift_mm[3], void *stream)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    dose_job j;
+    j.ctx = c; j.phase = phase; j.flags = DOSE_JOB_CLEAR | DOSE_JOB_FINISH;
+    j.n_histories = n_histories; j.hist_begin = 0; j.hist_end = n_histories;
+    j.seed = seed; j.spr_scale = spr_scale;
+    for (int k = 0; k < 3; ++k) j.shift_mm[k] = shift_mm ? shift_mm[k] : 0.0f;
+    const int rc = dose_run_batch(&j, 1, stream);
+    if (rc && c->err.empty()) c->err = g_thread_err;
+    return rc;
+}
+
+int dose_set_phase_dose(dose_ctx *c, int phase, const float *dose, int on_device, void *stream)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (!dose) return fail(c, DOSE_EINVAL, "dose is NULL");
+    if (phase < 0 || phase >= c->g->n_phases) return fail(c, DOSE_EINVAL, "phase %d out of range", phase);
+    int rc;
+    if ((rc = use_device(c))) return rc;
+    if ((rc = ensure_results(c, S(stream)))) return rc;
+    PhaseState &P = c->ph[phase];
+    CK(c, cudaMemcpyAsync(P.dose, dose, c->g->nvox * sizeof(float),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S(stream)));
+    P.has_dose = true;
+    c->have_accum = false;
+    return DOSE_OK;
+}
+
+int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], const float *dvf,
+                             int dvf_on_device, const uint8_t *mask, int mask_on_device, int method,
+                             void *stream)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (method != 0) return fail(c, DOSE_EINVAL, "only method 0 (energy/mass transfer) is provided");
+    const Grid &g = *c->g;
+    if (ref_phase < 0 || ref_phase >= g.n_phases) return fail(c, DOSE_EINVAL, "ref_phase out of range");
+    if (!nsub || nsub[0] < 1 || nsub[1] < 1 || nsub[2] < 1 || nsub[0] > 64 || nsub[1] > 64 || nsub[2] > 64)
+        return fail(c, DOSE_EINVAL, "nsub must be 3 values in 1..64");
+    for (int p = 0; p < g.n_phases; ++p)
+        if (!c->ph[p].has_dose) return fail(c, DOSE_ESTATE, "phase %d has no dose", p);
+    int rc;
+    if ((rc = use_device(c))) return rc;
+    const size_t nvox = (size_t)g.nvox, P = (size_t)g.n_phases;
+    if (!c->em) {
+        if ((rc = dalloc_t(c, &c->em, 2 * P * nvox)) || (rc = dalloc_t(c, &c->maxbits, P)) ||
+            (rc = dalloc_t(c, &c->emtm_stats, 4)) || (rc = dalloc_t(c, &c->accum, nvox)))
+            return rc;
+    }
+    cudaStream_t st = S(stream);
+    const float *dvf_dev = dvf;
+    const uint8_t *mask_dev = mask;
+    if (dvf && !dvf_on_device) {
+        if (!c->dvf_buf && (rc = dalloc_t(c, &c->dvf_buf, P * 3 * nvox))) return rc;
+        CK(c, cudaMemcpyAsync(c->dvf_buf, dvf, P * 3 * nvox * sizeof(float), cudaMemcpyHostToDevice, st));
+        dvf_dev = c->dvf_buf;
+    }
+    if (mask && !mask_on_device) {
+        if (!c->mask_buf && (rc = dalloc_t(c, &c->mask_buf, nvox))) return rc;
+        CK(c, cudaMemcpyAsync(c->mask_buf, mask, nvox, cudaMemcpyHostToDevice, st));
+        mask_dev = c->mask_buf;
+    }
+    CK(c, cudaMemsetAsync(c->em, 0, 2 * P * nvox * sizeof(unsigned long long), st));
+    CK(c, cudaMemsetAsync(c->maxbits, 0, P * sizeof(unsigned), st));
+    CK(c, cudaMemsetAsync(c->emtm_stats, 0, 4 * sizeof(unsigned long long), st));
+    EmtmArgs a;
+    a.dose = c->dose_all; a.rho = g.rho; a.dvf = dvf_dev; a.mask = mask_dev;
+    a.E = c->em; a.M = c->em + P * nvox; a.maxbits = c->maxbits; a.stats = c->emtm_stats;
+    a.accum = c->accum;
+    a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
+    a.dx = g.d[0]; a.dy = g.d[1]; a.dz = g.d[2];
+    a.nsx = nsub[0]; a.nsy = nsub[1]; a.nsz = nsub[2];
+    a.ref = ref_phase; a.n_phases = (int)P;
+    k_emtm_max<<<dim3(304, (unsigned)P), 256, 0, st>>>(a);
+    CK(c, cudaGetLastError());
+    k_emtm<<<dim3((unsigned)((nvox + 255) / 256), (unsigned)P), 256, 0, st>>>(a);
+    CK(c, cudaGetLastError());
+    k_emtm_sum<<<1216, 256, 0, st>>>(a);
+    CK(c, cudaGetLastError());
+    c->have_accum = true;
+    return DOSE_OK;
+}
+
+int dose_read(dose_ctx *c, int what, int phase, void *dst, size_t bytes, int dst_on_device, void *stream)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (!dst) return fail(c, DOSE_EINVAL, "dst is NULL");
+    const Grid &g = *c->g;
+    const size_t nvox = (size_t)g.nvox;
+    const void *src = nullptr;
+    size_t need = 0;
+    auto phase_ok = [&] { return phase >= 0 && phase < g.n_phases; };
+    switch (what) {
+    case DOSE_PHASE_DOSE:
+        if (!phase_ok()) return fail(c, DOSE_EINVAL, "phase out of range");
+        if (!c->ph[phase].has_dose) return fail(c, DOSE_ESTATE, "phase %d has no dose", phase);
+        src = c->ph[phase].dose; need = nvox * sizeof(float); break;
+    case DOSE_DENSITY:
+        if (!phase_ok()) return fail(c, DOSE_EINVAL, "phase out of range");
+        src = g.rho + (size_t)phase * nvox; need = nvox * sizeof(float); break;
+    case DOSE_ACCUM:
+        if (!c->have_accum) return fail(c, DOSE_ESTATE, "no accumulated dose");
+        src = c->accum; need = nvox * sizeof(float); break;
+    case DOSE_TALLY_I64:
+        if (!phase_ok()) return fail(c, DOSE_EINVAL, "phase out of range");
+        if (!c->ph[phase].tally || !c->ph[phase].allocated) return fail(c, DOSE_ESTATE, "phase %d was not run", phase);
+        src = c->ph[phase].tally; need = nvox * sizeof(unsigned long long); break;
+    case DOSE_SUBPLAN:
+        if (!c->have_plan) return fail(c, DOSE_ESTATE, "no plan");
+        src = c->pp; need = (size_t)g.n_phases * c->n_spots * sizeof(unsigned long long); break;
+    case DOSE_ENERGY_LEDGER:
+    case DOSE_STATUS:
+        if (!phase_ok()) return fail(c, DOSE_EINVAL, "phase out of range");
+        if (!c->ph[phase].ledger || !c->ph[phase].allocated) return fail(c, DOSE_ESTATE, "phase %d was not run", phase);
+        src = c->ph[phase].ledger;
+        need = what == DOSE_STATUS ? sizeof(int32_t) : LED_WORDS * sizeof(unsigned long long);
+        break;
+    case DOSE_START_PHASE:
+        if (!c->have_plan) return fail(c, DOSE_ESTATE, "no plan");
+        src = c->start_phase; need = c->n_fields * sizeof(int32_t); break;
+    case DOSE_FIELD_END_NS:
+        if (!c->have_plan) return fail(c, DOSE_ESTATE, "no plan");
+        src = c->field_end; need = c->n_fields * sizeof(int64_t); break;
+    case DOSE_EMTM_STATS:
+        if (!c->have_accum) return fail(c, DOSE_ESTATE, "no accumulated dose");
+        src = c->emtm_stats; need = 4 * sizeof(unsigned long long); break;
+    case DOSE_HIST_PREFIX:
+        if (!phase_ok()) return fail(c, DOSE_EINVAL, "phase out of range");
+        if (!c->ph[phase].allocated || !c->ph[phase].prefix) return fail(c, DOSE_ESTATE, "phase %d was not run", phase);
+        src = c->ph[phase].prefix; need = ((size_t)c->n_spots + 1) * sizeof(unsigned long long); break;
+    default:
+        return fail(c, DOSE_EINVAL, "unknown selector %d", what);
+    }
+    if (bytes != need) return fail(c, DOSE_EINVAL, "selector %d needs %zu bytes, got %zu", what, need, bytes);
+    int rc;
+    if ((rc = use_device(c))) return rc;
+    cudaStream_t st = S(stream);
+    if (what == DOSE_STATUS) {
+        if (dst_on_device) return fail(c, DOSE_EINVAL, "DOSE_STATUS is read into host memory only");
+        unsigned long long led[LED_WORDS];
+        CK(c, cudaMemcpyAsync(led, src, sizeof led, cudaMemcpyDeviceToHost, st));
+        if ((rc = sync_stream(c, st))) return rc;
+        *(int32_t *)dst = (led[LED_FLAGS] & FLAG_STEPLIMIT) ? DOSE_ESTEPLIMIT : DOSE_OK;
+        return DOSE_OK;
+    }
+    CK(c, cudaMemcpyAsync(dst, src, need, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!dst_on_device) return sync_stream(c, st);
+    return DOSE_OK;
+}
+
+int dose_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int n, float *uniforms)
+{
+    if (!ctr || !key || !out || n <= 0 || n > (1 << 24)) return fail(nullptr, DOSE_EINVAL, "bad arguments");
+    uint4 *dc = nullptr, *dout = nullptr;
+    uint2 *dk = nullptr;
+    float *du = nullptr;
+    cudaError_t e = cudaMalloc(&dc, n * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMalloc(&dk, n * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, n * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMalloc(&du, n * 6 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, n * sizeof(uint4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, key, n * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_debug_philox<<<(n + 255) / 256, 256>>>(dc, dk, dout, du, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, n * sizeof(uint4), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && uniforms) e = cudaMemcpy(uniforms, du, n * 6 * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(dc); cudaFree(dk); cudaFree(dout); cudaFree(du);
+    if (e != cudaSuccess) return fail(nullptr, DOSE_ECUDA, "philox self-test: %s", cudaGetErrorString(e));
+    return DOSE_OK;
+}
+
+int dose_debug_tables(const float *E, int n, float *out, void *stream)
+{
+    if (!E || !out || n <= 0 || n > (1 << 24)) return fail(nullptr, DOSE_EINVAL, "bad arguments");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, DOSE_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    DeviceTables tab;
+    dose_ctx tmp;
+    int rc = device_tables(&tmp, dev, &tab);
+    if (rc) return fail(nullptr, rc, "%s", tmp.err.c_str());
+    float *de = nullptr, *dout = nullptr;
+    e = cudaMalloc(&de, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, n * 5 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(de, E, n * sizeof(float), cudaMemcpyHostToDevice, S(stream));
+    if (e == cudaSuccess) {
+        k_debug_tables<<<(n + 255) / 256, 256, 0, S(stream)>>>(tab.dev, tab.inv_ds, de, n, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, n * 5 * sizeof(float), cudaMemcpyDeviceToHost, S(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S(stream));
+    cudaFree(de); cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, DOSE_ECUDA, "table self-test: %s", cudaGetErrorString(e));
+    return DOSE_OK;
+}
+
+void dose_destroy(dose_ctx *c)
+{
+    if (!c) return;
+    if (c->g) cudaSetDevice(c->g->device);
+    cudaDeviceSynchronize();
+    for (void *p : c->owned) cudaFree(p);
+    c->owned.clear();
+    if (c->g && c->g->refs.fetch_sub(1) == 1) {
+        if (c->g->hu) cudaFree(c->g->hu);
+        if (c->g->rho) cudaFree(c->g->rho);
+        delete c->g;
+    }
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Energy/mass-transfer accumulation (Sec. 2.D.2, Eqs. 4-6 of Pepin et al.)
+// and the phase sum of Eq. 2.
+//
+//   k_emtm_max  largest rho_j D_j of each source phase (fixed-point scale)
+//   k_emtm      one thread per source voxel j: split j into nsx x nsy x nsz
+//               subvoxels, move each centre by the phase's DVF (trilinear
+//               between voxel centres, edge-clamped) and add the subvoxel's
+//               mass rho_j and energy rho_j D_j (both in units of the common
+//               subvoxel volume) to the reference voxel whose half-open cell
+//               holds it.  Consecutive subvoxels landing in the same voxel
+//               are summed in registers and pushed with one pair of 64-bit
+//               integer atomics, so the sums are exact and order-free.
+//   k_emtm_sum  D_i = D_i^R + sum_S E_i^S / M_i^S (0 where M = 0), masked.
+//
+// The target voxel is decided in single precision with the rounding order
+// written out below (no contraction), so it is reproducible bit for bit.
+#include <cuda_runtime.h>
+#include <cmath>
+#include "engine.cuh"
+#include "kernels.h"
+
+namespace dose {
+
+namespace {
+constexpr int kMassShift = 40;   // mass units: rho x 2^40
+constexpr int kEnergyBits = 40;  // energy units: rho D scaled so max(rho D) < 2^40
+
+__device__ __forceinline__ int energy_shift(unsigned maxbits)
+{
+    if (maxbits == 0) return 0;
+    int e;
+    frexpf(__uint_as_float(maxbits), &e);          // max < 2^e
+    return kEnergyBits - e;
+}
+
+__device__ __forceinline__ float lerp_rn(float a, float b, float t)
+{
+    return __fadd_rn(a, __fmul_rn(t, __fsub_rn(b, a)));
+}
+
+__device__ float sample(const float *__restrict__ c, int nx, int ny, int nz, float qx, float qy,
+                        float qz)
+{
+    const float fx0 = floorf(qx), fy0 = floorf(qy), fz0 = floorf(qz);
+    const float fx = __fsub_rn(qx, fx0), fy = __fsub_rn(qy, fy0), fz = __fsub_rn(qz, fz0);
+    const int kx = (int)fx0, ky = (int)fy0, kz = (int)fz0;
+    const int x0 = min(max(kx, 0), nx - 1), x1 = min(max(kx + 1, 0), nx - 1);
+    const int y0 = min(max(ky, 0), ny - 1), y1 = min(max(ky + 1, 0), ny - 1);
+    const int z0 = min(max(kz, 0), nz - 1), z1 = min(max(kz + 1, 0), nz - 1);
+    const size_t r00 = ((size_t)z0 * ny + y0) * nx, r10 = ((size_t)z0 * ny + y1) * nx;
+    const size_t r01 = ((size_t)z1 * ny + y0) * nx, r11 = ((size_t)z1 * ny + y1) * nx;
+    const float c00 = lerp_rn(__ldg(c + r00 + x0), __ldg(c + r00 + x1), fx);
+    const float c10 = lerp_rn(__ldg(c + r10 + x0), __ldg(c + r10 + x1), fx);
+    const float c01 = lerp_rn(__ldg(c + r01 + x0), __ldg(c + r01 + x1), fx);
+    const float c11 = lerp_rn(__ldg(c + r11 + x0), __ldg(c + r11 + x1), fx);
+    return lerp_rn(lerp_rn(c00, c10, fy), lerp_rn(c01, c11, fy), fz);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+}  // namespace
+
+__global__ void k_emtm_max(EmtmArgs a)
+{
+    const int p = blockIdx.y;
+    if (p == a.ref) return;
+    const long long nvox = (long long)a.nx * a.ny * a.nz;
+    const float *d = a.dose + (size_t)p * nvox;
+    const float *r = a.rho + (size_t)p * nvox;
+    float m = 0.0f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride)
+        m = fmaxf(m, fmaxf(r[i] * d[i], 0.0f));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(a.maxbits + p, __float_as_uint(m));
+}
+
+__global__ void k_emtm(EmtmArgs a)
+{
+    const int S = blockIdx.y;
+    if (S == a.ref) return;
+    const long long nvox = (long long)a.nx * a.ny * a.nz;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long pushed = 0, dropped = 0, pairs = 0;
+    if (j < nvox) {
+        const int jx = (int)(j % a.nx);
+        const int jy = (int)((j / a.nx) % a.ny);
+        const int jz = (int)(j / ((long long)a.nx * a.ny));
+        const float rho = a.rho[(size_t)S * nvox + j];
+        const float dj = a.dose[(size_t)S * nvox + j];
+        const int es = energy_shift(a.maxbits[S]);
+        const double prod = fmax((double)rho * (double)dj, 0.0);
+        const unsigned long long eu = __double2ull_rn(ldexp(prod, es));
+        const unsigned long long mu = __double2ull_rn(ldexp((double)rho, kMassShift));
+        const float *dvx = a.dvf ? a.dvf + ((size_t)S * 3 + 0) * nvox : nullptr;
+        const float *dvy = a.dvf ? a.dvf + ((size_t)S * 3 + 1) * nvox : nullptr;
+        const float *dvz = a.dvf ? a.dvf + ((size_t)S * 3 + 2) * nvox : nullptr;
+        unsigned long long *E = a.E + (size_t)S * nvox;
+        unsigned long long *M = a.M + (size_t)S * nvox;
+        long long cur = -1;
+        unsigned long long cnt = 0;
+        for (int kz = 0; kz < a.nsz; ++kz) {
+            const float qz = __fsub_rn(__fadd_rn((float)jz, __fdiv_rn(__fadd_rn((float)kz, 0.5f), (float)a.nsz)), 0.5f);
+            for (int ky = 0; ky < a.nsy; ++ky) {
+                const float qy = __fsub_rn(__fadd_rn((float)jy, __fdiv_rn(__fadd_rn((float)ky, 0.5f), (float)a.nsy)), 0.5f);
+                for (int kx = 0; kx < a.nsx; ++kx) {
+                    const float qx = __fsub_rn(__fadd_rn((float)jx, __fdiv_rn(__fadd_rn((float)kx, 0.5f), (float)a.nsx)), 0.5f);
+                    float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+                    if (a.dvf) {
+                        ox = sample(dvx, a.nx, a.ny, a.nz, qx, qy, qz);
+                        oy = sample(dvy, a.nx, a.ny, a.nz, qx, qy, qz);
+                        oz = sample(dvz, a.nx, a.ny, a.nz, qx, qy, qz);
+                    }
+                    const float tx = __fadd_rn(__fadd_rn(qx, 0.5f), __fdiv_rn(ox, a.dx));
+                    const float ty = __fadd_rn(__fadd_rn(qy, 0.5f), __fdiv_rn(oy, a.dy));
+                    const float tz = __fadd_rn(__fadd_rn(qz, 0.5f), __fdiv_rn(oz, a.dz));
+                    const int ix = (int)floorf(tx), iy = (int)floorf(ty), iz = (int)floorf(tz);
+                    ++pushed;
+                    if (ix < 0 || ix >= a.nx || iy < 0 || iy >= a.ny || iz < 0 || iz >= a.nz) {
+                        ++dropped;
+                        continue;
+                    }
+                    const long long i = ((long long)iz * a.ny + iy) * a.nx + ix;
+                    if (i != cur) {
+                        if (cnt) {
+                            atomicAdd(E + cur, cnt * eu);
+                            atomicAdd(M + cur, cnt * mu);
+                            ++pairs;
+                        }
+                        cur = i;
+                        cnt = 0;
+                    }
+                    ++cnt;
+                }
+            }
+        }
+        if (cnt) {
+            atomicAdd(E + cur, cnt * eu);
+            atomicAdd(M + cur, cnt * mu);
+            ++pairs;
+        }
+    }
+    pushed = warp_sum(pushed);
+    dropped = warp_sum(dropped);
+    pairs = warp_sum(pairs);
+    if ((threadIdx.x & 31) == 0 && pushed) {
+        atomicAdd(a.stats + 0, pushed);
+        atomicAdd(a.stats + 1, dropped);
+        atomicAdd(a.stats + 2, pairs);
+    }
+}
+
+__global__ void k_emtm_sum(EmtmArgs a)
+{
+    const long long nvox = (long long)a.nx * a.ny * a.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+        double acc = (double)a.dose[(size_t)a.ref * nvox + i];
+        for (int S = 0; S < a.n_phases; ++S) {
+            if (S == a.ref) continue;
+            const unsigned long long m = a.M[(size_t)S * nvox + i];
+            if (m == 0) continue;
+            const int es = energy_shift(a.maxbits[S]);
+            acc += ldexp((double)a.E[(size_t)S * nvox + i] / (double)m, kMassShift - es);
+        }
+        if (a.mask && !a.mask[i]) acc = 0.0;
+        a.accum[i] = (float)acc;
+    }
+}
+
+}  // namespace dose

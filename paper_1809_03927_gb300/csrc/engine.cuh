@@ -1,0 +1,161 @@
+// Internal definitions of the CUDA dose engine: model constants, lookup-
+// table layout, per-launch job descriptors and small device helpers.
+// Included by the engine's translation units only.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dose {
+
+// ---- transport model (project choices; the paper prints no physics) -----
+constexpr float kEcut = 0.5f;          // MeV: below this the rest is deposited
+constexpr float kFstep = 0.25f;        // step <= 0.25 x residual range in the medium
+constexpr float kSmin = 0.01f;         // mm, shortest physics step
+constexpr float kFloc = 0.6f;          // local fraction at nuclear removal
+constexpr float kInvX0 = 1.0f / 360.8f;// 1/(water radiation length, mm at 1 g/cm^3)
+constexpr float kHighlandB = 0.038f;
+constexpr float kInvSqrt12 = 0.28867513459481287f;
+constexpr float kQuantum = 16777216.0f;   // tally units per MeV (2^24)
+
+// ---- lookup tables (built in FP64 on the host, stored FP32) -------------
+// re, hs: uniform kinetic-energy grid E_i = i * kDE, i = 0..kNE.
+// er:     grid uniform in sqrt(range): R_i = (i * kDS)^2, i = 0..kNR.
+// mat:    HU -1000..3000 -> (rho g/cm^3, SPR).
+constexpr int kNE = 2048;
+constexpr float kEmax = 256.0f;
+constexpr float kDE = kEmax / kNE;
+constexpr float kInvDE = kNE / kEmax;
+constexpr int kNR = 2048;
+constexpr float kRmax = 420.0f;        // mm, above the range of 256 MeV
+constexpr int kHuMin = -1000, kHuMax = 3000, kNHU = kHuMax - kHuMin + 1;
+
+struct Tables {
+    float2 re[kNE + 2];   // (CSDA range in water, mm; Bohr variance per mm of water path, MeV^2/mm)
+    float2 hs[kNE + 2];   // (Highland coefficient (13.6/pv)^2, rad^2; nuclear Sigma per mm of water)
+    float er[kNR + 4];    // energy at range (i kDS)^2
+    float2 mat[kNHU + 3]; // (rho, SPR)
+};
+static_assert(sizeof(Tables) % 16 == 0, "tables are copied to shared memory as int4");
+
+// Host-side FP64 builder (lut.cpp).  inv_ds receives 1/kDS.
+void build_tables(Tables *t, float *inv_ds);
+
+// ---- ledger words per phase/job ------------------------------------------
+enum { LED_DEP = 0, LED_ESC = 1, LED_REM = 2, LED_INC = 3, LED_STEPS = 4, LED_HIST = 5,
+       LED_FLAGS = 6, LED_W = 7, LED_WORDS = 8 };
+enum { FLAG_STEPLIMIT = 1 };
+
+// ---- one transport job of a persistent launch ---------------------------
+struct TJob {
+    const int16_t *hu;                  // this phase's grid
+    unsigned long long *tally;          // nvox
+    unsigned long long *ledger;         // LED_WORDS
+    const float4 *spot;                 // (x, y, E, sigma) patient mm / MeV
+    const float *wh;                    // history weight per spot
+    const unsigned long long *prefix;   // n_spots + 1 (first history of each spot)
+    int n_spots;
+    int nx, ny, nz;
+    float dx, dy, dz;
+    float ob, oc;                       // lateral patient->grid offsets (origin + shift)
+    int beam_axis, beam_sign;
+    float spr_scale;
+    unsigned physics;
+    unsigned max_steps;
+    unsigned key0, key1, stream;
+    unsigned long long hist_begin;      // first history of this slice
+    unsigned long long work_begin;      // offset in the launch's work index
+};
+
+struct AllocJob {
+    const unsigned long long *protons;  // n_spots, this phase's subplan
+    unsigned long long *rem;            // scratch n_spots
+    unsigned long long *prefix;         // n_spots + 1
+    float *wh;                          // n_spots
+    unsigned long long *ledger;         // LED_W receives W
+    int n_spots;
+    unsigned long long n_hist;
+};
+
+struct NormJob {
+    const unsigned long long *tally;
+    const unsigned long long *ledger;   // LED_W
+    const float *rho;
+    float *dose;
+    unsigned long long n_hist;
+    double voxel_cm3;
+    long long nvox;
+};
+
+#if defined(__CUDACC__)
+// ---- Philox4x32-10 (Salmon et al., SC'11) -------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Six 21-bit uniforms (k + 1/2) 2^-21 from the 128 bits of a block, bits
+// [21 i, 21 i + 21) of the little-endian word concatenation.
+struct U6 { float u[6]; };
+__device__ __forceinline__ U6 uniforms6(uint4 w)
+{
+    const unsigned long long lo = (unsigned long long)w.x | ((unsigned long long)w.y << 32);
+    const unsigned long long hi = (unsigned long long)w.z | ((unsigned long long)w.w << 32);
+    const unsigned long long M = 0x1FFFFFull;
+    unsigned k[6];
+    k[0] = (unsigned)(lo & M);
+    k[1] = (unsigned)((lo >> 21) & M);
+    k[2] = (unsigned)((lo >> 42) & M);
+    k[3] = (unsigned)(((lo >> 63) | (hi << 1)) & M);
+    k[4] = (unsigned)((hi >> 20) & M);
+    k[5] = (unsigned)((hi >> 41) & M);
+    U6 r;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) r.u[i] = __fmaf_rn((float)k[i], 4.76837158203125e-7f, 2.384185791015625e-7f);
+    return r;
+}
+
+// Box-Muller pair: r = sqrt(-2 ln ua), (r cos 2 pi ub, r sin 2 pi ub).  The
+// angle is evaluated as 2 pi ub - pi in (-pi, pi), where the fast sine and
+// cosine are accurate; cos(x + pi) = -cos x and sin(x + pi) = -sin x.
+__device__ __forceinline__ float2 box_muller(float ua, float ub)
+{
+    const float r = sqrtf(-2.0f * __logf(ua));
+    const float a = __fmaf_rn(6.28318530717958647f, ub, -3.14159265358979324f);
+    float s, c;
+    __sincosf(a, &s, &c);
+    return make_float2(-r * c, -r * s);
+}
+
+__device__ __forceinline__ unsigned long long to_units(float e)
+{
+    return __float2ull_rn(e * kQuantum);
+}
+
+// Linear interpolation on the uniform energy grid.
+__device__ __forceinline__ float2 lerp_e(const float2 *t, float e)
+{
+    const float x = fminf(fmaxf(e * kInvDE, 0.0f), (float)kNE);
+    const int i = min((int)x, kNE - 1);
+    const float f = x - (float)i;
+    const float2 a = t[i], b = t[i + 1];
+    return make_float2(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y));
+}
+
+// Energy at a residual water range, linear on the sqrt(range) grid.
+__device__ __forceinline__ float energy_at_range(const float *er, float r, float inv_ds)
+{
+    const float x = fminf(sqrtf(fmaxf(r, 0.0f)) * inv_ds, (float)kNR);
+    const int i = min((int)x, kNR - 1);
+    const float f = x - (float)i;
+    return fmaf(f, er[i + 1] - er[i], er[i]);
+}
+#endif  // __CUDACC__
+
+}  // namespace dose

@@ -1,0 +1,51 @@
+// Kernel declarations shared between the engine's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "engine.cuh"
+
+namespace dose {
+
+__global__ void k_density(const int16_t *hu, float *rho, long long n, const Tables *tab);
+__global__ void k_alloc(const AllocJob *jobs);
+__global__ void k_transport(const TJob *jobs, int n_jobs, unsigned long long total,
+                            unsigned long long *counter, const Tables *gtab, float inv_ds,
+                            unsigned chunk);
+__global__ void k_normalise(const NormJob *jobs);
+__global__ void k_debug_philox(const uint4 *ctr, const uint2 *key, uint4 *out, float *uni, int n);
+__global__ void k_debug_tables(const Tables *tab, float inv_ds, const float *e, int n, float *out);
+
+struct TimelineArgs {
+    const unsigned long long *protons;
+    const int *layer;
+    const int *field;
+    int n_spots;
+    int n_phases, start_phase, gated, gate_first, gate_last, repaints;
+    long long tph, spot_switch, layer_switch, discard;
+    unsigned long long rate, seed;
+    unsigned long long *pp;          // n_phases x n_spots, zeroed by the caller
+    long long *field_end;            // n_fields
+    int *start_out;                  // n_fields
+    int n_fields;
+};
+__global__ void k_timeline(TimelineArgs a);
+
+struct EmtmArgs {
+    const float *dose;               // n_phases x nvox
+    const float *rho;                // n_phases x nvox
+    const float *dvf;                // n_phases x 3 x nvox, or null
+    const uint8_t *mask;             // nvox or null
+    unsigned long long *E, *M;       // n_phases x nvox each (slot of the reference unused)
+    unsigned *maxbits;               // n_phases: bits of max(rho D) per phase
+    unsigned long long *stats;       // 4: pushed, dropped, atomic pairs, reserved
+    float *accum;                    // nvox
+    int nx, ny, nz;
+    float dx, dy, dz;
+    int nsx, nsy, nsz;
+    int ref, n_phases;
+};
+__global__ void k_emtm_max(EmtmArgs a);
+__global__ void k_emtm(EmtmArgs a);
+__global__ void k_emtm_sum(EmtmArgs a);
+
+}  // namespace dose

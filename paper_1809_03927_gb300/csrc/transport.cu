@@ -1,0 +1,512 @@
+// Transport-side kernels of the dose engine (Sec. 2.C of Pepin et al.):
+//   k_density    HU -> mass density of every voxel
+//   k_alloc      histories per spot (floor + largest remainder), prefix sums,
+//                history weights and the phase's proton total W
+//   k_transport  persistent, warp-cooperative class II condensed-history
+//                transport with a 64-bit fixed-point energy tally
+//   k_normalise  tally -> dose in Gy
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "engine.cuh"
+#include "kernels.h"
+
+namespace dose {
+
+namespace {
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Block-wide sum; every thread gets the total.  blockDim.x % 32 == 0.
+__device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_u64(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+// Block-wide exclusive prefix sum of one value per thread.
+__device__ unsigned long long block_exclusive_u64(unsigned long long v, unsigned long long *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    unsigned long long base = 0;
+    for (int w = 0; w < warp && w < nw; ++w) base += red[w];
+    return base + incl - v;
+}
+
+// (a b) / w and (a b) mod w for 64-bit a, b, w with a b / w < 2^64.
+__device__ void mul_divmod(unsigned long long a, unsigned long long b, unsigned long long w,
+                           unsigned long long *q, unsigned long long *r)
+{
+    const unsigned long long lo = a * b, hi = __umul64hi(a, b);
+    unsigned long long rem = hi, quo = 0;
+    for (int i = 63; i >= 0; --i) {
+        const unsigned long long carry = rem >> 63;
+        rem = (rem << 1) | ((lo >> i) & 1ull);
+        quo <<= 1;
+        if (carry || rem >= w) { rem -= w; quo |= 1ull; }
+    }
+    *q = quo;
+    *r = rem;
+}
+}  // namespace
+
+// ------------------------------------------------------------------ density
+__global__ void k_density(const int16_t *__restrict__ hu, float *__restrict__ rho, long long n,
+                          const Tables *__restrict__ tab)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int h = min(max((int)hu[i], kHuMin), kHuMax);
+        rho[i] = tab->mat[h - kHuMin].x;
+    }
+}
+
+// --------------------------------------------------------------- allocation
+// One block per job.  n_s = floor(N p_s / W) for every spot, then the
+// N - sum n_s spots with the largest remainders (ties: lower index) get one
+// more; prefix[s] is the first history of spot s; wh[s] = p_s N / (n_s W).
+__global__ void __launch_bounds__(1024) k_alloc(const AllocJob *__restrict__ jobs)
+{
+    __shared__ unsigned long long red[32];
+    __shared__ unsigned long long tile[1024];
+    const AllocJob J = jobs[blockIdx.x];
+    const int S = J.n_spots, tid = threadIdx.x, bs = blockDim.x;
+    const unsigned long long N = J.n_hist;
+
+    unsigned long long w = 0;
+    for (int s = tid; s < S; s += bs) w += J.protons[s];
+    const unsigned long long W = block_sum_u64(w, red);
+    if (W == 0 || N == 0) {
+        for (int s = tid; s <= S; s += bs) J.prefix[s] = 0;
+        for (int s = tid; s < S; s += bs) J.wh[s] = 0.0f;
+        if (tid == 0) J.ledger[LED_W] = W;
+        return;
+    }
+    unsigned long long used = 0;
+    for (int s = tid; s < S; s += bs) {
+        unsigned long long q, r;
+        mul_divmod(N, J.protons[s], W, &q, &r);
+        J.prefix[s + 1] = q;       // n_s for now
+        J.rem[s] = r;
+        used += q;
+    }
+    const unsigned long long left = N - block_sum_u64(used, red);
+    __syncthreads();
+    for (int base = 0; base < S; base += bs) {
+        const int s = base + tid;
+        const unsigned long long rs = s < S ? J.rem[s] : 0ull;
+        unsigned long long rank = 0;
+        for (int t0 = 0; t0 < S; t0 += 1024) {
+            __syncthreads();
+            for (int k = tid; k < 1024 && t0 + k < S; k += bs) tile[k] = J.rem[t0 + k];
+            __syncthreads();
+            const int tn = min(1024, S - t0);
+            if (s < S)
+                for (int k = 0; k < tn; ++k) {
+                    const unsigned long long rt = tile[k];
+                    rank += (rt > rs) | ((rt == rs) & (t0 + k < s));
+                }
+        }
+        if (s < S && rank < left) J.prefix[s + 1] += 1;
+    }
+    __syncthreads();
+    const int per = (S + bs - 1) / bs;
+    const int a = min(S, tid * per), b = min(S, a + per);
+    unsigned long long local = 0;
+    for (int k = a; k < b; ++k) local += J.prefix[k + 1];
+    unsigned long long run = block_exclusive_u64(local, red);
+    for (int k = a; k < b; ++k) {
+        const unsigned long long n = J.prefix[k + 1];
+        J.wh[k] = n ? (float)((double)J.protons[k] * (double)N / ((double)n * (double)W)) : 0.0f;
+        run += n;
+        J.prefix[k + 1] = run;
+    }
+    if (tid == 0) {
+        J.prefix[0] = 0;
+        J.ledger[LED_W] = W;
+    }
+}
+
+// ---------------------------------------------------------------- transport
+namespace {
+
+__device__ __forceinline__ float highland_g(float u)
+{
+    if (!(u > 0.0f)) return 0.0f;
+    const float t = fmaf(kHighlandB, __logf(u), 1.0f);
+    return u * t * t;
+}
+
+// Per-lane running totals for the job the lane currently serves.
+struct Ledger {
+    unsigned long long dep, esc, rem, inc;
+    unsigned steps, hist;
+};
+
+__device__ __forceinline__ void flush_ledger(unsigned long long *led, Ledger &L)
+{
+    if (L.dep) atomicAdd(led + LED_DEP, L.dep);
+    if (L.esc) atomicAdd(led + LED_ESC, L.esc);
+    if (L.rem) atomicAdd(led + LED_REM, L.rem);
+    if (L.inc) atomicAdd(led + LED_INC, L.inc);
+    if (L.steps) atomicAdd(led + LED_STEPS, (unsigned long long)L.steps);
+    if (L.hist) atomicAdd(led + LED_HIST, (unsigned long long)L.hist);
+    L.dep = L.esc = L.rem = L.inc = 0;
+    L.steps = L.hist = 0;
+}
+
+}  // namespace
+
+// Persistent kernel: every warp pulls `chunk` consecutive work items (one
+// history each) from a global counter and keeps its 32 lanes busy: when a
+// lane's history ends it takes the next unclaimed item of the warp's chunk
+// (ranked by ballot), so lanes are refilled as they die.  The loop ends when
+// the counter passes `total` and every lane of the warp is idle.  Every
+// history is a pure function of (seed, history index, stream), so results do
+// not depend on the launch shape, on the chunking or on the batching.
+__global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
+                            unsigned long long *__restrict__ counter,
+                            const Tables *__restrict__ gtab, float inv_ds, unsigned chunk)
+{
+    extern __shared__ int4 smem[];
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(gtab);
+        for (int i = threadIdx.x; i < (int)(sizeof(Tables) / 16); i += blockDim.x) smem[i] = src[i];
+    }
+    __syncthreads();
+    const Tables &T = *reinterpret_cast<const Tables *>(smem);
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    // per-lane history state
+    bool alive = false;
+    float px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0, E = 0, eta = 0, uth = 0, gth = 0, wh = 0;
+    int ix = 0, iy = 0, iz = 0;
+    unsigned step = 0;
+    unsigned long long h = 0;
+    int job = -1;
+    Ledger L = {0, 0, 0, 0, 0, 0};
+    unsigned long long *pend_tally = nullptr;
+    int pend_vox = -1;
+    unsigned long long pend_units = 0;
+
+    // job fields the step loop uses (refreshed when the lane changes job)
+    const int16_t *hu = nullptr;
+    unsigned long long *tally = nullptr;
+    int nx = 0, ny = 0, nz = 0;
+    float dx = 1, dy = 1, dz = 1, idx = 1, idy = 1, idz = 1, spr_scale = 1;
+    unsigned physics = 0, max_steps = 0, key0 = 0, key1 = 0, stream = 0;
+
+    // warp-uniform queue state
+    unsigned long long pool_next = 0, pool_end = 0;
+    bool queue_done = false;
+
+    for (;;) {
+        // ---------------- refill idle lanes from the warp's chunk
+        unsigned need = __ballot_sync(kFull, !alive);
+        while (need && !queue_done) {
+            if (pool_next >= pool_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(counter, (unsigned long long)chunk);
+                base = __shfl_sync(kFull, base, 0);
+                if (base >= total) { queue_done = true; break; }
+                pool_next = base;
+                pool_end = min(base + (unsigned long long)chunk, total);
+            }
+            const unsigned rank = __popc(need & lt_mask);
+            const unsigned long long avail = pool_end - pool_next;
+            if (!alive && rank < avail) {
+                const unsigned long long w = pool_next + rank;
+                int lo = 0, hi = n_jobs;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (jobs[mid].work_begin <= w) lo = mid; else hi = mid;
+                }
+                const TJob &J = jobs[lo];
+                if (lo != job) {
+                    if (job >= 0) flush_ledger(jobs[job].ledger, L);
+                    if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
+                    pend_units = 0;
+                    pend_vox = -1;
+                    job = lo;
+                    hu = J.hu; tally = J.tally;
+                    nx = J.nx; ny = J.ny; nz = J.nz;
+                    dx = J.dx; dy = J.dy; dz = J.dz;
+                    idx = 1.0f / dx; idy = 1.0f / dy; idz = 1.0f / dz;
+                    spr_scale = J.spr_scale;
+                    physics = J.physics; max_steps = J.max_steps;
+                    key0 = J.key0; key1 = J.key1; stream = J.stream;
+                    pend_tally = tally;
+                }
+                h = J.hist_begin + (w - J.work_begin);
+                const int S = J.n_spots;
+                if (h < J.prefix[S]) {
+                    int a = 0, b = S;
+                    while (b - a > 1) {
+                        const int m = (a + b) >> 1;
+                        if (J.prefix[m] <= h) a = m; else b = m;
+                    }
+                    const float4 sp = J.spot[a];
+                    wh = J.wh[a];
+                    E = sp.z;
+                    const U6 u = uniforms6(philox4x32_10(
+                        make_uint4(0u, (unsigned)h, (unsigned)(h >> 32), stream), key0, key1));
+                    const float2 z = box_muller(u.u[0], u.u[1]);
+                    eta = -__logf(u.u[2]);
+                    const unsigned long long e_units = to_units(E * wh);
+                    L.inc += e_units;
+                    L.hist += 1;
+                    const float lb = sp.x - J.ob + sp.w * z.x;
+                    const float lc = sp.y - J.oc + sp.w * z.y;
+                    const int ax = J.beam_axis, sg = J.beam_sign;
+                    bool inside;
+                    ux = uy = uz = 0.0f;
+                    if (ax == 2) {
+                        inside = lb >= 0.0f && lb < nx * dx && lc >= 0.0f && lc < ny * dy;
+                        px = lb; py = lc; pz = sg > 0 ? 0.0f : nz * dz; uz = (float)sg;
+                        ix = (int)floorf(px * idx); iy = (int)floorf(py * idy); iz = sg > 0 ? 0 : nz - 1;
+                    } else if (ax == 1) {
+                        inside = lb >= 0.0f && lb < nx * dx && lc >= 0.0f && lc < nz * dz;
+                        px = lb; pz = lc; py = sg > 0 ? 0.0f : ny * dy; uy = (float)sg;
+                        ix = (int)floorf(px * idx); iz = (int)floorf(pz * idz); iy = sg > 0 ? 0 : ny - 1;
+                    } else {
+                        inside = lb >= 0.0f && lb < ny * dy && lc >= 0.0f && lc < nz * dz;
+                        py = lb; pz = lc; px = sg > 0 ? 0.0f : nx * dx; ux = (float)sg;
+                        iy = (int)floorf(py * idy); iz = (int)floorf(pz * idz); ix = sg > 0 ? 0 : nx - 1;
+                    }
+                    // guard the floor against rounding at the far faces
+                    ix = min(max(ix, 0), nx - 1); iy = min(max(iy, 0), ny - 1); iz = min(max(iz, 0), nz - 1);
+                    if (inside) {
+                        uth = 0.0f; gth = 0.0f; step = 0;
+                        alive = true;
+                    } else {
+                        L.esc += e_units;
+                    }
+                }
+            }
+            pool_next += min((unsigned long long)__popc(need), avail);
+            need = __ballot_sync(kFull, !alive);
+        }
+        if (__ballot_sync(kFull, alive) == 0) break;
+        if (!alive) continue;
+
+        // ---------------- one condensed-history step
+        if (step >= max_steps) {
+            L.esc += to_units(E * wh);
+            atomicOr(jobs[job].ledger + LED_FLAGS, (unsigned long long)FLAG_STEPLIMIT);
+            alive = false;
+            continue;
+        }
+        L.steps += 1;
+        const int vox = (iz * ny + iy) * nx + ix;
+        const int hv = min(max((int)__ldg(hu + vox), kHuMin), kHuMax);
+        const float2 m = T.mat[hv - kHuMin];
+        const float rho = m.x;
+        const float spr = m.y * spr_scale;
+        const float inv_spr = __fdividef(1.0f, spr);
+        const float2 re0 = lerp_e(T.re, E);
+        const float R0 = re0.x;
+        if (R0 * inv_spr <= kSmin) {                   // residual range below s_min
+            const unsigned long long eu = to_units(E * wh);
+            L.dep += eu;
+            if (vox != pend_vox) {
+                if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
+                pend_vox = vox; pend_units = 0; pend_tally = tally;
+            }
+            pend_units += eu;
+            alive = false;
+            continue;
+        }
+        // distance to the faces of the current voxel (ties: lowest axis)
+        const float inf = __int_as_float(0x7f800000);
+        float tx = ux > 0.0f ? ((ix + 1) * dx - px) * __fdividef(1.0f, ux)
+                 : (ux < 0.0f ? (ix * dx - px) * __fdividef(1.0f, ux) : inf);
+        float ty = uy > 0.0f ? ((iy + 1) * dy - py) * __fdividef(1.0f, uy)
+                 : (uy < 0.0f ? (iy * dy - py) * __fdividef(1.0f, uy) : inf);
+        float tz = uz > 0.0f ? ((iz + 1) * dz - pz) * __fdividef(1.0f, uz)
+                 : (uz < 0.0f ? (iz * dz - pz) * __fdividef(1.0f, uz) : inf);
+        tx = fmaxf(tx, 0.0f); ty = fmaxf(ty, 0.0f); tz = fmaxf(tz, 0.0f);
+        int across = 0;
+        float dbound = tx;
+        if (ty < dbound) { dbound = ty; across = 1; }
+        if (tz < dbound) { dbound = tz; across = 2; }
+        // the step ends at the voxel boundary or after the physics length
+        float s = fmaxf(kFstep * R0 * inv_spr, kSmin);
+        bool geom = false;
+        if (dbound <= s) { s = dbound; geom = true; }
+
+        float sw = s * spr;                              // water-equivalent mm
+        float E1c = energy_at_range(T.er, R0 - sw, inv_ds);
+        float Emean = 0.5f * (E + E1c);
+        float2 hs = lerp_e(T.hs, Emean);
+        bool nuclear = false;
+        if (physics & 4u) {
+            const float tau = hs.y * sw;
+            if (hs.y > 0.0f && tau >= eta) {
+                nuclear = true;
+                sw = __fdividef(eta, hs.y);
+                s = sw * inv_spr;
+                geom = false;
+                E1c = energy_at_range(T.er, R0 - sw, inv_ds);
+            } else {
+                eta -= tau;
+            }
+        }
+        const U6 u = uniforms6(philox4x32_10(
+            make_uint4(step + 1u, (unsigned)h, (unsigned)(h >> 32), stream), key0, key1));
+        float dE = E - E1c;
+        if (physics & 1u) {
+            // Bohr fluctuation, truncated symmetrically at the mean loss so
+            // the step's expected loss is the CSDA loss for any length
+            const float zA = box_muller(u.u[0], u.u[1]).x;
+            const float f = sqrtf(re0.y * sw) * zA;
+            dE = fminf(dE + fminf(fmaxf(f, -dE), dE), E);
+        }
+        const float E1 = E - dE;
+        dE = E - E1;
+
+        if (nuclear || E1 <= kEcut) {
+            float local = E;                              // stop: dE + E1
+            if (nuclear) {
+                local = dE + kFloc * E1;
+                L.rem += to_units((E1 - kFloc * E1) * wh);
+            }
+            const unsigned long long eu = to_units(local * wh);
+            L.dep += eu;
+            if (vox != pend_vox) {
+                if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
+                pend_vox = vox; pend_units = 0; pend_tally = tally;
+            }
+            pend_units += eu;
+            alive = false;
+            continue;
+        }
+        {
+            const unsigned long long eu = to_units(dE * wh);
+            L.dep += eu;
+            if (vox != pend_vox) {
+                if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
+                pend_vox = vox; pend_units = 0; pend_tally = tally;
+            }
+            pend_units += eu;
+        }
+
+        // multiple Coulomb scattering over the step (cumulative Highland)
+        float y1 = 0.0f, y2 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+        if (physics & 2u) {
+            const float u1 = fmaf(s * rho, kInvX0, uth);
+            const float g1 = highland_g(u1);
+            const float th2 = hs.x * (g1 - gth);
+            uth = u1; gth = g1;
+            const float th0 = sqrtf(fmaxf(th2, 0.0f));
+            const float2 zu = box_muller(u.u[2], u.u[3]);
+            const float2 zv = box_muller(u.u[4], u.u[5]);
+            y1 = s * th0 * fmaf(zu.x, kInvSqrt12, 0.5f * zu.y);
+            t1 = th0 * zu.y;
+            y2 = s * th0 * fmaf(zv.x, kInvSqrt12, 0.5f * zv.y);
+            t2 = th0 * zv.y;
+        }
+        // transverse frame (Duff et al., JCGT 2017)
+        const float sgn = uz >= 0.0f ? 1.0f : -1.0f;
+        const float fa = __fdividef(-1.0f, sgn + uz);
+        const float fb = ux * uy * fa;
+        const float e1x = fmaf(sgn * ux * ux, fa, 1.0f), e1y = sgn * fb, e1z = -sgn * ux;
+        const float e2x = fb, e2y = fmaf(uy * uy, fa, sgn), e2z = -uy;
+        const float ux0 = ux, uy0 = uy, uz0 = uz;
+        px = fmaf(s, ux, fmaf(y1, e1x, fmaf(y2, e2x, px)));
+        py = fmaf(s, uy, fmaf(y1, e1y, fmaf(y2, e2y, py)));
+        pz = fmaf(s, uz, fmaf(y1, e1z, fmaf(y2, e2z, pz)));
+        ux = fmaf(t1, e1x, fmaf(t2, e2x, ux));
+        uy = fmaf(t1, e1y, fmaf(t2, e2y, uy));
+        uz = fmaf(t1, e1z, fmaf(t2, e2z, uz));
+        const float nrm = rsqrtf(ux * ux + uy * uy + uz * uz);
+        ux *= nrm; uy *= nrm; uz *= nrm;
+        E = E1;
+        ++step;
+
+        // voxel update: the crossed axis steps by one and its coordinate is
+        // put on the crossed face; every other axis keeps its index while the
+        // position stays inside the voxel's closed extent and takes
+        // floor(p / d) once the lateral displacement carried it outside
+        if (geom && across == 0) {
+            if (ux0 > 0.0f) { ix += 1; px = ix * dx; } else { px = ix * dx; ix -= 1; }
+        } else if (!(px >= ix * dx && px <= (ix + 1) * dx)) {
+            ix = (int)floorf(px * idx);
+        }
+        if (geom && across == 1) {
+            if (uy0 > 0.0f) { iy += 1; py = iy * dy; } else { py = iy * dy; iy -= 1; }
+        } else if (!(py >= iy * dy && py <= (iy + 1) * dy)) {
+            iy = (int)floorf(py * idy);
+        }
+        if (geom && across == 2) {
+            if (uz0 > 0.0f) { iz += 1; pz = iz * dz; } else { pz = iz * dz; iz -= 1; }
+        } else if (!(pz >= iz * dz && pz <= (iz + 1) * dz)) {
+            iz = (int)floorf(pz * idz);
+        }
+        if ((unsigned)ix >= (unsigned)nx || (unsigned)iy >= (unsigned)ny || (unsigned)iz >= (unsigned)nz) {
+            L.esc += to_units(E * wh);
+            alive = false;
+        }
+    }
+    if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
+    if (job >= 0) flush_ledger(jobs[job].ledger, L);
+}
+
+// ------------------------------------------------------------- self-tests
+__global__ void k_debug_philox(const uint4 *ctr, const uint2 *key, uint4 *out, float *uni, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 w = philox4x32_10(ctr[i], key[i].x, key[i].y);
+    out[i] = w;
+    const U6 u = uniforms6(w);
+    for (int k = 0; k < 6; ++k) uni[6 * i + k] = u.u[k];
+}
+
+__global__ void k_debug_tables(const Tables *tab, float inv_ds, const float *e, int n, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 re = lerp_e(tab->re, e[i]);
+    const float2 hs = lerp_e(tab->hs, e[i]);
+    out[5 * i + 0] = re.x;
+    out[5 * i + 1] = energy_at_range(tab->er, re.x, inv_ds);
+    out[5 * i + 2] = re.y;
+    out[5 * i + 3] = hs.x;
+    out[5 * i + 4] = hs.y;
+}
+
+// -------------------------------------------------------------- normalise
+// D_i = tally_i 2^-24 MeV x (W/N) x 1.602176634e-13 J/MeV / (rho_i V 1e-3 kg)
+__global__ void k_normalise(const NormJob *__restrict__ jobs)
+{
+    const NormJob J = jobs[blockIdx.y];
+    const unsigned long long W = J.ledger[LED_W];
+    const double factor = (W == 0 || J.n_hist == 0) ? 0.0
+        : (double)W / (double)J.n_hist * 1.602176634e-10 / (16777216.0 * J.voxel_cm3);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < J.nvox; i += stride)
+        J.dose[i] = (float)((double)J.tally[i] * factor / (double)J.rho[i]);
+}
+
+}  // namespace dose

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of ``libdose`` (``include/dose.h``).
+
+Argument marshalling only: every function below has the name of the C entry
+point it calls, converts arrays/tensors to pointers and raises ``DoseError``
+on a negative status.  All computation happens in the CUDA kernels of the
+library.  Importing this module fails loudly if ``libdose.so`` has not been
+built (``python -m paper_1809_03927_gb300.build``); there is no fallback.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or device);
+the ``*_on_device`` flags of the C ABI are derived from them.  ``stream``
+defaults to torch's current CUDA stream when torch has CUDA, else NULL.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libdose.so")
+
+DOSE_OK, DOSE_EINVAL, DOSE_ENOMEM, DOSE_ECUDA, DOSE_ETIMEOUT, DOSE_ESTEPLIMIT, DOSE_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6
+(DOSE_PHASE_DOSE, DOSE_DENSITY, DOSE_ACCUM, DOSE_TALLY_I64, DOSE_SUBPLAN, DOSE_ENERGY_LEDGER,
+ DOSE_STATUS, DOSE_START_PHASE, DOSE_FIELD_END_NS, DOSE_EMTM_STATS, DOSE_HIST_PREFIX) = range(11)
+DOSE_PHYS_STRAGGLING, DOSE_PHYS_MCS, DOSE_PHYS_NUCLEAR, DOSE_PHYS_ALL = 1, 2, 4, 7
+(DOSE_OPT_PHYSICS, DOSE_OPT_MAX_STEPS, DOSE_OPT_BLOCK, DOSE_OPT_BLOCKS_PER_SM, DOSE_OPT_CHUNK,
+ DOSE_OPT_TIMEOUT_MS, DOSE_OPT_FAIL_ALLOC_AFTER) = range(7)
+DOSE_JOB_CLEAR, DOSE_JOB_FINISH = 1, 2
+LEDGER = ("deposited", "escaped", "removed", "incident", "steps", "histories", "flags", "protons")
+
+
+class DoseError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdose error {code}: {msg}")
+        self.code = code
+
+
+class dose_spot(C.Structure):
+    _fields_ = [("x_mm", C.c_float), ("y_mm", C.c_float), ("energy_MeV", C.c_float),
+                ("sigma_mm", C.c_float), ("protons", C.c_uint64), ("layer", C.c_int32),
+                ("field", C.c_int32)]
+
+
+class dose_delivery(C.Structure):
+    _fields_ = [("n_phases", C.c_int32), ("start_phase", C.c_int32), ("gated", C.c_int32),
+                ("gate_first", C.c_int32), ("gate_last", C.c_int32), ("repaints", C.c_int32),
+                ("period_ns", C.c_int64), ("period_sigma_ns", C.c_int64),
+                ("spot_switch_ns", C.c_int64), ("layer_switch_ns", C.c_int64),
+                ("discard_ns", C.c_int64), ("rate_protons_per_s", C.c_uint64), ("seed", C.c_uint64)]
+
+
+class dose_job(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("phase", C.c_int32), ("flags", C.c_uint32),
+                ("n_histories", C.c_uint64), ("hist_begin", C.c_uint64), ("hist_end", C.c_uint64),
+                ("seed", C.c_uint64), ("spr_scale", C.c_float), ("shift_mm", C.c_float * 3)]
+
+
+assert C.sizeof(dose_spot) == 32 and C.sizeof(dose_job) == 64
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libdose.so is not built ({_LIB_PATH}); run "
+                          "`python -m paper_1809_03927_gb300.build` (needs nvcc)")
+    L = C.CDLL(_LIB_PATH)
+    P, I, U64, I64, F = C.c_void_p, C.c_int, C.c_uint64, C.c_int64, C.c_float
+    sig = {
+        "dose_create_grid": ([C.POINTER(P), I, I, I, F, F, F, P, I, P, I, P, P], I),
+        "dose_create_view": ([P, C.POINTER(P)], I),
+        "dose_add_spots": ([P, P, I64, P, P], I),
+        "dose_run_phase": ([P, I, U64, U64, F, P, P], I),
+        "dose_run_batch": ([P, I, P], I),
+        "dose_set_phase_dose": ([P, I, P, I, P], I),
+        "dose_accumulate_subvoxel": ([P, I, P, P, I, P, I, I, P], I),
+        "dose_read": ([P, I, I, P, C.c_size_t, I, P], I),
+        "dose_set_option": ([P, I, I64], I),
+        "dose_destroy": ([P], None),
+        "dose_last_error": ([P], C.c_char_p),
+        "dose_version": ([], I),
+        "dose_debug_philox": ([P, P, P, I, P], I),
+        "dose_debug_tables": ([P, I, P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+# ------------------------------------------------------------- marshalling
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), int(x.is_cuda)
+    if not (x.flags["C_CONTIGUOUS"]):
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data, 0
+
+
+def _nbytes(x):
+    if _is_torch(x):
+        return x.numel() * x.element_size()
+    return x.nbytes
+
+
+def default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _stream(s):
+    if s is None:
+        return default_stream()
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return s
+
+
+def _check(rc, ctx=None):
+    if rc != DOSE_OK:
+        msg = _lib.dose_last_error(ctx)
+        raise DoseError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _f3(v):
+    return (C.c_float * 3)(*[float(a) for a in v])
+
+
+# ------------------------------------------------------------------ API
+def dose_version():
+    return _lib.dose_version()
+
+
+def dose_last_error(ctx=None):
+    m = _lib.dose_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def dose_create_grid(nx, ny, nz, dx_mm, dy_mm, dz_mm, origin_mm, n_phases, hu, beam_dir,
+                     stream=None):
+    """HU must be int16 of n_phases*nz*ny*nx elements (x fastest)."""
+    if not _is_torch(hu):
+        hu = np.ascontiguousarray(hu, dtype=np.int16)
+    p, dev = _ptr(hu)
+    out = C.c_void_p()
+    rc = _lib.dose_create_grid(C.byref(out), int(nx), int(ny), int(nz), float(dx_mm), float(dy_mm),
+                               float(dz_mm), _f3(origin_mm), int(n_phases), p, dev, _f3(beam_dir),
+                               _stream(stream))
+    _check(rc, None)
+    return out.value
+
+
+def dose_create_view(base):
+    out = C.c_void_p()
+    _check(_lib.dose_create_view(base, C.byref(out)), None)
+    return out.value
+
+
+def dose_add_spots(ctx, spots, delivery=None, stream=None):
+    """``spots``: a ``dose_spot`` ctypes array; ``delivery``: ``dose_delivery`` or None."""
+    dl = C.byref(delivery) if delivery is not None else None
+    _check(_lib.dose_add_spots(ctx, C.cast(spots, C.c_void_p), len(spots), dl, _stream(stream)), ctx)
+
+
+def dose_run_phase(ctx, phase, n_histories, seed, spr_scale=1.0, shift_mm=None, stream=None):
+    sh = _f3(shift_mm) if shift_mm is not None else None
+    _check(_lib.dose_run_phase(ctx, int(phase), int(n_histories), int(seed), float(spr_scale), sh,
+                               _stream(stream)), ctx)
+
+
+def dose_run_batch(jobs, stream=None):
+    """``jobs``: a ``dose_job`` ctypes array (see ``make_jobs``)."""
+    rc = _lib.dose_run_batch(C.cast(jobs, C.c_void_p), len(jobs), _stream(stream))
+    _check(rc, jobs[0].ctx if len(jobs) else None)
+
+
+def dose_set_phase_dose(ctx, phase, dose, stream=None):
+    p, dev = _ptr(dose)
+    _check(_lib.dose_set_phase_dose(ctx, int(phase), p, dev, _stream(stream)), ctx)
+
+
+def dose_accumulate_subvoxel(ctx, ref_phase, nsub, dvf=None, mask=None, method=0, stream=None):
+    ns = (C.c_int * 3)(*[int(v) for v in nsub])
+    if dvf is not None and not _is_torch(dvf):
+        dvf = np.ascontiguousarray(dvf, dtype=np.float32)
+    if mask is not None and not _is_torch(mask):
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    dp, ddev = _ptr(dvf)
+    mp, mdev = _ptr(mask)
+    _check(_lib.dose_accumulate_subvoxel(ctx, int(ref_phase), ns, dp, ddev, mp, mdev, int(method),
+                                         _stream(stream)), ctx)
+
+
+def dose_read(ctx, what, phase, dst, stream=None):
+    p, dev = _ptr(dst)
+    _check(_lib.dose_read(ctx, int(what), int(phase), p, _nbytes(dst), dev, _stream(stream)), ctx)
+    return dst
+
+
+def dose_set_option(ctx, option, value):
+    _check(_lib.dose_set_option(ctx, int(option), int(value)), ctx)
+
+
+def dose_destroy(ctx):
+    _lib.dose_destroy(ctx)
+
+
+def dose_debug_philox(ctr, key, stream=None):
+    """Device Philox4x32-10 of n counters (n x 4 uint32) under keys (n x 2):
+    returns (words n x 4 uint32, uniforms n x 6 float32)."""
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, np.uint32).reshape(-1, 2)
+    n = c.shape[0]
+    w = np.zeros((n, 4), np.uint32)
+    u = np.zeros((n, 6), np.float32)
+    _check(_lib.dose_debug_philox(c.ctypes.data, k.ctypes.data, w.ctypes.data, n, u.ctypes.data))
+    return w, u
+
+
+def dose_debug_tables(energies):
+    """Device table lookups at the given energies: columns R(E), E(R(E)),
+    Bohr variance per mm, Highland coefficient, Sigma per mm (float32)."""
+    e = np.ascontiguousarray(energies, np.float32)
+    out = np.zeros((e.shape[0], 5), np.float32)
+    _check(_lib.dose_debug_tables(e.ctypes.data, e.shape[0], out.ctypes.data, None))
+    return out
+
+
+# ------------------------------------------------------- plan marshalling
+def spots_array(plan):
+    """``dose_spot`` array from a plan with x, y, energy, sigma, protons,
+    layer, field sequences."""
+    n = len(plan)
+    arr = (dose_spot * n)()
+    for i in range(n):
+        arr[i] = dose_spot(float(plan.x[i]), float(plan.y[i]), float(plan.energy[i]),
+                           float(plan.sigma[i]), int(plan.protons[i]), int(plan.layer[i]),
+                           int(plan.field[i]))
+    return arr
+
+
+def delivery_struct(d):
+    s = dose_delivery()
+    for name, _ in dose_delivery._fields_:
+        setattr(s, name, int(getattr(d, name)))
+    return s
+
+
+def make_jobs(specs):
+    """``dose_job`` array from dicts with keys ctx, phase, n_histories and
+    optionally flags, hist_begin, hist_end, seed, spr_scale, shift_mm."""
+    arr = (dose_job * len(specs))()
+    for i, s in enumerate(specs):
+        n = int(s["n_histories"])
+        arr[i] = dose_job(s["ctx"], int(s["phase"]), int(s.get("flags", DOSE_JOB_CLEAR | DOSE_JOB_FINISH)),
+                          n, int(s.get("hist_begin", 0)), int(s.get("hist_end", n)), int(s.get("seed", 1)),
+                          float(s.get("spr_scale", 1.0)), _f3(s.get("shift_mm", (0.0, 0.0, 0.0))))
+    return arr

@@ -21,3 +21,23 @@ def orc():
     oracle.build()
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def libdose():
+    """The CUDA engine's C-ABI library, built in-tree (nvcc cross-compiles
+    without a GPU) and loaded through the thin binding."""
+    from paper_1809_03927_gb300 import build
+    build.build()
+    from paper_1809_03927_gb300 import dose
+    return dose
+
+
+@pytest.fixture(scope="session")
+def gpu(libdose):
+    """Skip unless a CUDA device is usable; returns the binding."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    return libdose

@@ -1,0 +1,63 @@
+"""The C-ABI library without a GPU: it builds for sm_103a, loads, exports
+every entry point include/dose.h declares, and rejects bad arguments with
+DOSE_EINVAL and a message before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dose.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dose_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("dose_create_grid", "dose_add_spots", "dose_run_phase", "dose_accumulate_subvoxel",
+              "dose_read", "dose_run_batch", "dose_destroy", "dose_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libdose):
+    lib = C.CDLL(libdose._LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert libdose.dose_version() == 1
+
+
+def test_argument_validation_without_device(libdose):
+    D = libdose
+    hu = np.zeros(64, np.int16)
+    with pytest.raises(D.DoseError) as e:
+        D.dose_create_grid(0, 4, 4, 1, 1, 1, (0, 0, 0), 1, hu, (0, 0, 1))
+    assert e.value.code == D.DOSE_EINVAL and "positive" in str(e.value)
+    for bad in [dict(d=(0, 1, 1)), dict(d=(1, float("nan"), 1)), dict(beam=(0, 0.5, 0.5)),
+                dict(beam=(1, 1, 0)), dict(phases=0), dict(origin=(0, float("inf"), 0))]:
+        with pytest.raises(D.DoseError) as e:
+            D.dose_create_grid(4, 4, 4, *bad.get("d", (1, 1, 1)), bad.get("origin", (0, 0, 0)),
+                               bad.get("phases", 1), hu, bad.get("beam", (0, 0, 1)))
+        assert e.value.code == D.DOSE_EINVAL
+        assert D.dose_last_error(None)
+    lib = D.lib()
+    assert lib.dose_create_grid(None, 4, 4, 4, 1.0, 1.0, 1.0, None, 1, None, 0, None, None) == D.DOSE_EINVAL
+    assert lib.dose_run_batch(None, 0, None) == D.DOSE_EINVAL
+    assert lib.dose_read(None, 0, 0, None, 0, 0, None) == D.DOSE_EINVAL
+    assert lib.dose_set_option(None, 0, 0) == D.DOSE_EINVAL
+    assert lib.dose_add_spots(None, None, 0, None, None) == D.DOSE_EINVAL
+    assert lib.dose_accumulate_subvoxel(None, 0, None, None, 0, None, 0, 0, None) == D.DOSE_EINVAL
+    assert lib.dose_debug_philox(None, None, None, 0, None) == D.DOSE_EINVAL
+    lib.dose_destroy(None)
+
+
+def test_structs_match_the_header(libdose):
+    D = libdose
+    assert C.sizeof(D.dose_spot) == 32
+    assert C.sizeof(D.dose_delivery) == 6 * 4 + 5 * 8 + 2 * 8
+    assert C.sizeof(D.dose_job) == 64
+    assert D.dose_job.shift_mm.offset == 52

@@ -219,3 +219,16 @@ def test_transverse_frame_is_orthonormal(orc):
         m = np.stack([e1, e2, d])
         np.testing.assert_allclose(m @ m.T, np.eye(3), atol=1e-12)
         np.testing.assert_allclose(np.cross(e1, e2), d, atol=1e-12)
+
+
+@pytest.mark.parametrize("hu,e,s", [(-1000, 100.0, 2.0), (0, 150.0, 0.001), (-800, 70.0, 0.05)])
+def test_straggling_unbiased_on_thin_steps(orc, hu, e, s):
+    """The expected energy loss of a step is its CSDA loss E - E_w(R_w(E) -
+    s SPR) whatever the step length, including steps so thin that the Bohr
+    width exceeds the mean loss (air, sub-micron remainders)."""
+    n = 40000
+    de = np.array([orc.single_step(hu, e, 0.01, s, 3, h)[0] for h in range(n)])
+    csda = e - orc.energy_from_range(orc.range_mm(e) - s * orc.spr(hu))
+    assert np.all(de >= 0.0) and np.all(de <= 2.0 * csda + 1e-15)
+    assert abs(de.mean() - csda) <= 5.0 * de.std() / math.sqrt(n) + 1e-12
+    assert de.std() > 0.0
