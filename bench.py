@@ -186,6 +186,8 @@ def run_engine(args):
     D.dose_add_spots(ctx, spots, None, stream)
     seed = SEED + 1000 * rank
     n_hist = args.histories
+    # launch shape from the engine's autotuner (results do not depend on it)
+    tune = D.dose_autotune(ctx, 0, n_hist, min(n_hist, 2_000_000), seed, stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -283,6 +285,8 @@ def run_engine(args):
         "config": {"workload": WORKLOAD if n_hist == N_HIST else WORKLOAD.replace("1e7", f"{n_hist:.0e}"),
                    "histories_per_step": n_hist, "steps_per_history": round(steps_per_hist, 2),
                    "l2": "256 MB buffer written between timed steps, outside the step events",
+                   "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2],
+                              "autotune_sample_us": tune[3]},
                    "parallelism": f"{ws} independent replica(s), one per GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
                      "frac": achieved / peak_ops, "traffic": None,

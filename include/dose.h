@@ -120,8 +120,10 @@ enum {
     DOSE_OPT_BLOCKS_PER_SM = 3,   /* transport blocks per SM (0 = occupancy max) */
     DOSE_OPT_CHUNK = 4,           /* histories a warp takes per queue pull       */
     DOSE_OPT_TIMEOUT_MS = 5,      /* host wait bound for dose_read (default 600000) */
-    DOSE_OPT_FAIL_ALLOC_AFTER = 6 /* test hook: the n-th later device allocation
+    DOSE_OPT_FAIL_ALLOC_AFTER = 6,/* test hook: the n-th later device allocation
                                      of this context fails (-1 = off)            */
+    DOSE_OPT_REGISTERS = 7        /* transport register budget: 0 = up to 128 per
+                                     thread (blocks <= 512), 1 = 64 (blocks <= 1024) */
 };
 
 /* Create a context holding a voxel grid of `n_phases` HU volumes (Sec. 2.A:
@@ -203,6 +205,19 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
 int dose_read(dose_ctx *c, int what, int phase, void *dst, size_t bytes, int dst_on_device,
               void *stream);
 
+/* Autotuner: time the transport of histories [0, sample_histories) of an
+ * n_histories-history run of `phase` under each launch shape -- register
+ * budget (DOSE_OPT_REGISTERS 0 or 1) x threads per block in {128, 256, 512,
+ * 1024} (the shapes that fit) x histories a warp takes per queue pull in
+ * {32, 64, 128, 256} -- and keep the fastest on the context.  Launch shapes
+ * change speed only: the tallies are bit-identical for every shape.  The
+ * phase's tally and dose are overwritten.  best (host, may be NULL)
+ * receives {registers option, block, chunk, elapsed microseconds of the best
+ * shape}.  Waits for the stream.  The step-length rule is part of the
+ * physics model and is not tuned.                                          */
+int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_histories,
+                  uint64_t seed, void *stream, int64_t best[4]);
+
 /* Set an option (DOSE_OPT_*).                                              */
 int dose_set_option(dose_ctx *c, int option, int64_t value);
 
@@ -229,7 +244,7 @@ int dose_debug_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, i
  * (host, MeV) writes out[5 i..5 i+4] = CSDA range R(E) in mm of water, the
  * energy at that range E(R(E)), the Bohr variance per mm of water path, the
  * Highland coefficient (13.6/pv)^2 and the nuclear Sigma per mm, each
- * interpolated exactly as the transport does.  Host memory; waits.         */
+ * evaluated exactly as the transport does.  Host memory; waits.            */
 int dose_debug_tables(const float *E, int n, float *out, void *stream);
 
 #ifdef __cplusplus

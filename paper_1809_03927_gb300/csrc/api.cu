@@ -100,6 +100,7 @@ struct dose_ctx {
     int block = 256;
     int blocks_per_sm = 0;
     unsigned chunk = 64;
+    int regs = 0;
     long long timeout_ms = 600000;
     long long fail_alloc_after = -1;
     std::vector<void *> owned;
@@ -378,6 +379,7 @@ int dose_create_view(dose_ctx *base, dose_ctx **out)
     c->block = base->block;
     c->blocks_per_sm = base->blocks_per_sm;
     c->chunk = base->chunk;
+    c->regs = base->regs;
     c->timeout_ms = base->timeout_ms;
     *out = c;
     return DOSE_OK;
@@ -407,6 +409,9 @@ int dose_set_option(dose_ctx *c, int option, int64_t value)
         c->timeout_ms = value; return DOSE_OK;
     case DOSE_OPT_FAIL_ALLOC_AFTER:
         c->fail_alloc_after = value < 0 ? -1 : value; return DOSE_OK;
+    case DOSE_OPT_REGISTERS:
+        if (value != 0 && value != 1) return fail(c, DOSE_EINVAL, "register option must be 0 or 1");
+        c->regs = (int)value; return DOSE_OK;
     default:
         return fail(c, DOSE_EINVAL, "unknown option %d", option);
     }
@@ -551,6 +556,7 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
             CK(c0, cudaMemsetAsync(P.ledger, 0, LED_WORDS * sizeof(unsigned long long), st));
             AllocJob a;
             a.protons = c->pp + (size_t)J.phase * c->n_spots;
+            a.spot = c->spot;
             a.rem = P.rem; a.prefix = P.prefix; a.wh = P.wh; a.ledger = P.ledger;
             a.n_spots = c->n_spots; a.n_hist = J.n_histories;
             aj.push_back(a);
@@ -578,6 +584,8 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
             work += cnt;
         }
         if (J.flags & DOSE_JOB_FINISH) {
+            // the deposited total is re-taken from the tally at each finish
+            CK(c0, cudaMemsetAsync(P.ledger + LED_DEP, 0, sizeof(unsigned long long), st));
             NormJob nm;
             nm.tally = P.tally; nm.ledger = P.ledger; nm.rho = g.rho + (size_t)J.phase * g.nvox;
             nm.dose = P.dose; nm.n_hist = J.n_histories;
@@ -595,21 +603,24 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
     if (work) {
         CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
         CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
-        const size_t smem = sizeof(Tables);
-        CK(c0, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const size_t smem = kSmemTables;
+        auto kern = c0->regs ? k_transport_r64 : k_transport;
+        if (!c0->regs && c0->block > 512)
+            return fail(c0, DOSE_EINVAL, "block %d needs the 64-register variant (DOSE_OPT_REGISTERS 1)", c0->block);
+        CK(c0, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int sms = 0;
         CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->g->device));
         int per_sm = c0->blocks_per_sm;
         if (per_sm <= 0) {
-            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport, c0->block, smem));
+            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c0->block, smem));
             if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
         }
         const unsigned long long warps = (unsigned long long)sms * per_sm * (c0->block / 32);
         unsigned chunk = c0->chunk;
         // keep at least ~4 pulls per warp so the tail stays short
         while (chunk > 32 && (unsigned long long)chunk * warps * 4 > work) chunk >>= 1;
-        k_transport<<<sms * per_sm, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
-                                                           tab.dev, tab.inv_ds, chunk);
+        kern<<<sms * per_sm, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
+                                                    tab.dev, tab.inv_ds, chunk);
         CK(c0, cudaGetLastError());
     }
     if (!nj.empty()) {
@@ -632,6 +643,74 @@ int dose_run_phase(dose_ctx *c, int phase, uint64_t n_histories, uint64_t seed, 
     for (int k = 0; k < 3; ++k) j.shift_mm[k] = shift_mm ? shift_mm[k] : 0.0f;
     const int rc = dose_run_batch(&j, 1, stream);
     if (rc && c->err.empty()) c->err = g_thread_err;
+    return rc;
+}
+
+int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_histories, uint64_t seed,
+                  void *stream, int64_t best[4])
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (sample_histories == 0 || sample_histories > n_histories)
+        return fail(c, DOSE_EINVAL, "sample must be in 1..n_histories");
+    static const int blocks[] = {128, 256, 512, 1024};
+    static const unsigned chunks[] = {32, 64, 128, 256};
+    const int keep_block = c->block, keep_regs = c->regs, keep_per_sm = c->blocks_per_sm;
+    const unsigned keep_chunk = c->chunk;
+    cudaStream_t st = S(stream);
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    float best_ms = -1.0f;
+    int best_block = keep_block, best_regs = keep_regs;
+    unsigned best_chunk = keep_chunk;
+    int rc = DOSE_OK;
+    dose_job j;
+    j.ctx = c; j.phase = phase; j.n_histories = n_histories; j.seed = seed; j.spr_scale = 1.0f;
+    j.shift_mm[0] = j.shift_mm[1] = j.shift_mm[2] = 0.0f;
+    c->blocks_per_sm = 0;
+    // the occupancy query needs the kernels' dynamic shared-memory limit set
+    CK(c, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables));
+    CK(c, cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables));
+    // allocate the phase's histories once; each trial then only transports
+    j.flags = DOSE_JOB_CLEAR; j.hist_begin = 0; j.hist_end = 0;
+    if ((rc = dose_run_batch(&j, 1, stream))) goto done;
+    for (int regs = 0; regs < 2; ++regs) {
+        for (int b : blocks) {
+            if (!regs && b > 512) continue;
+            int fits = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, regs ? k_transport_r64 : k_transport, b,
+                                                              kSmemTables) != cudaSuccess || fits <= 0) {
+                cudaGetLastError();
+                continue;
+            }
+            for (unsigned ch : chunks) {
+                c->regs = regs;
+                c->block = b;
+                c->chunk = ch;
+                j.flags = 0; j.hist_begin = 0; j.hist_end = sample_histories;
+                cudaEventRecord(e0, st);
+                if ((rc = dose_run_batch(&j, 1, stream))) goto done;
+                cudaEventRecord(e1, st);
+                if ((rc = sync_stream(c, st))) goto done;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (best_ms < 0.0f || ms < best_ms) { best_ms = ms; best_block = b; best_chunk = ch; best_regs = regs; }
+            }
+        }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->block = rc ? keep_block : best_block;
+    c->chunk = rc ? keep_chunk : best_chunk;
+    c->regs = rc ? keep_regs : best_regs;
+    c->blocks_per_sm = keep_per_sm;
+    c->ph[phase].has_dose = false;
+    if (!rc && best_ms < 0.0f) rc = fail(c, DOSE_ECUDA, "autotune: no launch shape could be timed");
+    if (!rc && best) {
+        best[0] = best_regs; best[1] = best_block; best[2] = best_chunk;
+        best[3] = (int64_t)(best_ms * 1000.0f);
+    }
     return rc;
 }
 

@@ -2,6 +2,7 @@
 // table layout, per-launch job descriptors and small device helpers.
 // Included by the engine's translation units only.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -31,11 +32,15 @@ constexpr int kHuMin = -1000, kHuMax = 3000, kNHU = kHuMax - kHuMin + 1;
 
 struct Tables {
     float2 re[kNE + 2];   // (CSDA range in water, mm; Bohr variance per mm of water path, MeV^2/mm)
-    float2 hs[kNE + 2];   // (Highland coefficient (13.6/pv)^2, rad^2; nuclear Sigma per mm of water)
+    float2 hs[kNE + 2];   // (p v in MeV, for the Highland coefficient; nuclear Sigma per mm of water)
     float er[kNR + 4];    // energy at range (i kDS)^2
     float2 mat[kNHU + 3]; // (rho, SPR)
 };
 static_assert(sizeof(Tables) % 16 == 0, "tables are copied to shared memory as int4");
+// The transport stages the physics tables (re, hs, er) in shared memory and
+// reads the HU table through the L1 cache.
+constexpr size_t kSmemTables = offsetof(Tables, mat);
+static_assert(kSmemTables % 16 == 0, "staged part must be a multiple of 16 bytes");
 
 // Host-side FP64 builder (lut.cpp).  inv_ds receives 1/kDS.
 void build_tables(Tables *t, float *inv_ds);
@@ -68,6 +73,7 @@ struct TJob {
 
 struct AllocJob {
     const unsigned long long *protons;  // n_spots, this phase's subplan
+    const float4 *spot;                 // (x, y, E, sigma): energies for the incident total
     unsigned long long *rem;            // scratch n_spots
     unsigned long long *prefix;         // n_spots + 1
     float *wh;                          // n_spots
@@ -78,7 +84,7 @@ struct AllocJob {
 
 struct NormJob {
     const unsigned long long *tally;
-    const unsigned long long *ledger;   // LED_W
+    unsigned long long *ledger;         // reads LED_W, adds the tally sum to LED_DEP
     const float *rho;
     float *dose;
     unsigned long long n_hist;
@@ -121,21 +127,42 @@ __device__ __forceinline__ U6 uniforms6(uint4 w)
     return r;
 }
 
+// Square root through the hardware reciprocal square root (x >= 0).
+__device__ __forceinline__ float fast_sqrt(float x)
+{
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 // Box-Muller pair: r = sqrt(-2 ln ua), (r cos 2 pi ub, r sin 2 pi ub).  The
 // angle is evaluated as 2 pi ub - pi in (-pi, pi), where the fast sine and
 // cosine are accurate; cos(x + pi) = -cos x and sin(x + pi) = -sin x.
 __device__ __forceinline__ float2 box_muller(float ua, float ub)
 {
-    const float r = sqrtf(-2.0f * __logf(ua));
+    const float r = fast_sqrt(-2.0f * __logf(ua));
     const float a = __fmaf_rn(6.28318530717958647f, ub, -3.14159265358979324f);
     float s, c;
     __sincosf(a, &s, &c);
     return make_float2(-r * c, -r * s);
 }
 
+// First normal of the Box-Muller pair only.
+__device__ __forceinline__ float box_muller_first(float ua, float ub)
+{
+    const float r = fast_sqrt(-2.0f * __logf(ua));
+    const float a = __fmaf_rn(6.28318530717958647f, ub, -3.14159265358979324f);
+    return -r * __cosf(a);
+}
+
 __device__ __forceinline__ unsigned long long to_units(float e)
 {
     return __float2ull_rn(e * kQuantum);
+}
+
+// Highland coefficient (13.6 MeV / pv)^2 from the tabulated p v.
+__device__ __forceinline__ float highland_coeff(float pv)
+{
+    const float k = __fdividef(13.6f, pv);
+    return k * k;
 }
 
 // Linear interpolation on the uniform energy grid.
@@ -151,7 +178,7 @@ __device__ __forceinline__ float2 lerp_e(const float2 *t, float e)
 // Energy at a residual water range, linear on the sqrt(range) grid.
 __device__ __forceinline__ float energy_at_range(const float *er, float r, float inv_ds)
 {
-    const float x = fminf(sqrtf(fmaxf(r, 0.0f)) * inv_ds, (float)kNR);
+    const float x = fminf(fast_sqrt(r) * inv_ds, (float)kNR);
     const int i = min((int)x, kNR - 1);
     const float f = x - (float)i;
     return fmaf(f, er[i + 1] - er[i], er[i]);

@@ -11,6 +11,9 @@ __global__ void k_alloc(const AllocJob *jobs);
 __global__ void k_transport(const TJob *jobs, int n_jobs, unsigned long long total,
                             unsigned long long *counter, const Tables *gtab, float inv_ds,
                             unsigned chunk);
+__global__ void k_transport_r64(const TJob *jobs, int n_jobs, unsigned long long total,
+                                unsigned long long *counter, const Tables *gtab, float inv_ds,
+                                unsigned chunk);
 __global__ void k_normalise(const NormJob *jobs);
 __global__ void k_debug_philox(const uint4 *ctr, const uint2 *key, uint4 *out, float *uni, int n);
 __global__ void k_debug_tables(const Tables *tab, float inv_ds, const float *e, int n, float *out);

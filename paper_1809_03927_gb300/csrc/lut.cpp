@@ -8,7 +8,8 @@
 //     water at 1 g/cm^3, and its inverse E(R);
 //   * Bohr straggling variance per mm of water path,
 //     K m_e c^2 (Z/A) (1 - beta^2/2)/(1 - beta^2) / 10;
-//   * Highland coefficient (13.6 MeV / pv)^2;
+//   * p v (MeV), from which the transport forms the Highland coefficient
+//     (13.6 MeV / pv)^2 (pv is nearly linear in E, so it interpolates well);
 //   * nuclear removal Sigma_w(E) = 0.0123 (1 - exp(-(E - 7)/20)) per cm above
 //     7 MeV, stored per mm;
 //   * HU -> (density, stopping-power ratio), piecewise linear.
@@ -101,10 +102,9 @@ void build_tables(Tables *t, float *inv_ds)
         const double gamma = 1.0 + ee / MP;
         const double bohr = K * ME * ZA * 0.5 * (gamma * gamma + 1.0) / 10.0;
         const double pv = ee * (ee + 2.0 * MP) / (ee + MP);
-        const double hl = (13.6 / pv) * (13.6 / pv);
         const double sig = ee > 7.0 ? 0.0123 * (1.0 - std::exp(-(ee - 7.0) / 20.0)) / 10.0 : 0.0;
         t->re[i] = make_float2((float)R(e), (float)bohr);
-        t->hs[i] = make_float2((float)hl, (float)sig);
+        t->hs[i] = make_float2((float)pv, (float)sig);
     }
     const double ds = std::sqrt((double)kRmax) / kNR;
     for (int i = 0; i < kNR + 4; ++i) {

@@ -135,15 +135,23 @@ __global__ void __launch_bounds__(1024) k_alloc(const AllocJob *__restrict__ job
     unsigned long long local = 0;
     for (int k = a; k < b; ++k) local += J.prefix[k + 1];
     unsigned long long run = block_exclusive_u64(local, red);
+    // with the prefix sums, the incident energy of the run as the transport
+    // rounds it history by history (n_s units(E_s w_s)) and the history count
+    unsigned long long inc = 0;
     for (int k = a; k < b; ++k) {
         const unsigned long long n = J.prefix[k + 1];
-        J.wh[k] = n ? (float)((double)J.protons[k] * (double)N / ((double)n * (double)W)) : 0.0f;
+        const float w = n ? (float)((double)J.protons[k] * (double)N / ((double)n * (double)W)) : 0.0f;
+        J.wh[k] = w;
+        inc += n * to_units(J.spot[k].z * w);
         run += n;
         J.prefix[k + 1] = run;
     }
+    inc = block_sum_u64(inc, red);
     if (tid == 0) {
         J.prefix[0] = 0;
         J.ledger[LED_W] = W;
+        J.ledger[LED_INC] = inc;
+        J.ledger[LED_HIST] = N;
     }
 }
 
@@ -158,21 +166,21 @@ __device__ __forceinline__ float highland_g(float u)
 }
 
 // Per-lane running totals for the job the lane currently serves.
+// (Deposited energy is the sum of the tally, taken by k_normalise; the
+// incident energy and the history count follow from the allocation, taken
+// by k_alloc.)
 struct Ledger {
-    unsigned long long dep, esc, rem, inc;
-    unsigned steps, hist;
+    unsigned long long esc, rem;
+    unsigned steps;
 };
 
 __device__ __forceinline__ void flush_ledger(unsigned long long *led, Ledger &L)
 {
-    if (L.dep) atomicAdd(led + LED_DEP, L.dep);
     if (L.esc) atomicAdd(led + LED_ESC, L.esc);
     if (L.rem) atomicAdd(led + LED_REM, L.rem);
-    if (L.inc) atomicAdd(led + LED_INC, L.inc);
     if (L.steps) atomicAdd(led + LED_STEPS, (unsigned long long)L.steps);
-    if (L.hist) atomicAdd(led + LED_HIST, (unsigned long long)L.hist);
-    L.dep = L.esc = L.rem = L.inc = 0;
-    L.steps = L.hist = 0;
+    L.esc = L.rem = 0;
+    L.steps = 0;
 }
 
 }  // namespace
@@ -184,17 +192,21 @@ __device__ __forceinline__ void flush_ledger(unsigned long long *led, Ledger &L)
 // the counter passes `total` and every lane of the warp is idle.  Every
 // history is a pure function of (seed, history index, stream), so results do
 // not depend on the launch shape, on the chunking or on the batching.
-__global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
-                            unsigned long long *__restrict__ counter,
-                            const Tables *__restrict__ gtab, float inv_ds, unsigned chunk)
+__device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, int n_jobs,
+                                               unsigned long long total,
+                                               unsigned long long *__restrict__ counter,
+                                               const Tables *__restrict__ gtab, float inv_ds,
+                                               unsigned chunk)
 {
     extern __shared__ int4 smem[];
     {
         const int4 *src = reinterpret_cast<const int4 *>(gtab);
-        for (int i = threadIdx.x; i < (int)(sizeof(Tables) / 16); i += blockDim.x) smem[i] = src[i];
+        for (int i = threadIdx.x; i < (int)(kSmemTables / 16); i += blockDim.x) smem[i] = src[i];
     }
     __syncthreads();
+    // re, hs, er from shared memory; mat (beyond the staged part) from global
     const Tables &T = *reinterpret_cast<const Tables *>(smem);
+    const float2 *__restrict__ mat = gtab->mat;
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -205,8 +217,7 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
     unsigned step = 0;
     unsigned long long h = 0;
     int job = -1;
-    Ledger L = {0, 0, 0, 0, 0, 0};
-    unsigned long long *pend_tally = nullptr;
+    Ledger L = {0, 0, 0};
     int pend_vox = -1;
     unsigned long long pend_units = 0;
 
@@ -245,7 +256,7 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
                 const TJob &J = jobs[lo];
                 if (lo != job) {
                     if (job >= 0) flush_ledger(jobs[job].ledger, L);
-                    if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
+                    if (pend_units) atomicAdd(tally + pend_vox, pend_units);
                     pend_units = 0;
                     pend_vox = -1;
                     job = lo;
@@ -256,7 +267,6 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
                     spr_scale = J.spr_scale;
                     physics = J.physics; max_steps = J.max_steps;
                     key0 = J.key0; key1 = J.key1; stream = J.stream;
-                    pend_tally = tally;
                 }
                 h = J.hist_begin + (w - J.work_begin);
                 const int S = J.n_spots;
@@ -274,8 +284,6 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
                     const float2 z = box_muller(u.u[0], u.u[1]);
                     eta = -__logf(u.u[2]);
                     const unsigned long long e_units = to_units(E * wh);
-                    L.inc += e_units;
-                    L.hist += 1;
                     const float lb = sp.x - J.ob + sp.w * z.x;
                     const float lc = sp.y - J.oc + sp.w * z.y;
                     const int ax = J.beam_axis, sg = J.beam_sign;
@@ -320,7 +328,7 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
         L.steps += 1;
         const int vox = (iz * ny + iy) * nx + ix;
         const int hv = min(max((int)__ldg(hu + vox), kHuMin), kHuMax);
-        const float2 m = T.mat[hv - kHuMin];
+        const float2 m = __ldg(mat + (hv - kHuMin));
         const float rho = m.x;
         const float spr = m.y * spr_scale;
         const float inv_spr = __fdividef(1.0f, spr);
@@ -328,10 +336,9 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
         const float R0 = re0.x;
         if (R0 * inv_spr <= kSmin) {                   // residual range below s_min
             const unsigned long long eu = to_units(E * wh);
-            L.dep += eu;
             if (vox != pend_vox) {
-                if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
-                pend_vox = vox; pend_units = 0; pend_tally = tally;
+                if (pend_units) atomicAdd(tally + pend_vox, pend_units);
+                pend_vox = vox; pend_units = 0;
             }
             pend_units += eu;
             alive = false;
@@ -378,8 +385,8 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
         if (physics & 1u) {
             // Bohr fluctuation, truncated symmetrically at the mean loss so
             // the step's expected loss is the CSDA loss for any length
-            const float zA = box_muller(u.u[0], u.u[1]).x;
-            const float f = sqrtf(re0.y * sw) * zA;
+            const float zA = box_muller_first(u.u[0], u.u[1]);
+            const float f = fast_sqrt(re0.y * sw) * zA;
             dE = fminf(dE + fminf(fmaxf(f, -dE), dE), E);
         }
         const float E1 = E - dE;
@@ -392,10 +399,9 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
                 L.rem += to_units((E1 - kFloc * E1) * wh);
             }
             const unsigned long long eu = to_units(local * wh);
-            L.dep += eu;
             if (vox != pend_vox) {
-                if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
-                pend_vox = vox; pend_units = 0; pend_tally = tally;
+                if (pend_units) atomicAdd(tally + pend_vox, pend_units);
+                pend_vox = vox; pend_units = 0;
             }
             pend_units += eu;
             alive = false;
@@ -403,10 +409,9 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
         }
         {
             const unsigned long long eu = to_units(dE * wh);
-            L.dep += eu;
             if (vox != pend_vox) {
-                if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
-                pend_vox = vox; pend_units = 0; pend_tally = tally;
+                if (pend_units) atomicAdd(tally + pend_vox, pend_units);
+                pend_vox = vox; pend_units = 0;
             }
             pend_units += eu;
         }
@@ -416,9 +421,9 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
         if (physics & 2u) {
             const float u1 = fmaf(s * rho, kInvX0, uth);
             const float g1 = highland_g(u1);
-            const float th2 = hs.x * (g1 - gth);
+            const float th2 = highland_coeff(hs.x) * (g1 - gth);
             uth = u1; gth = g1;
-            const float th0 = sqrtf(fmaxf(th2, 0.0f));
+            const float th0 = fast_sqrt(th2);
             const float2 zu = box_muller(u.u[2], u.u[3]);
             const float2 zv = box_muller(u.u[4], u.u[5]);
             y1 = s * th0 * fmaf(zu.x, kInvSqrt12, 0.5f * zu.y);
@@ -468,8 +473,27 @@ __global__ void k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned 
             alive = false;
         }
     }
-    if (pend_units) atomicAdd(pend_tally + pend_vox, pend_units);
+    if (pend_units) atomicAdd(tally + pend_vox, pend_units);
     if (job >= 0) flush_ledger(jobs[job].ledger, L);
+}
+
+// Two register budgets of the same kernel: up to 128 registers per thread
+// (blocks of at most 512 threads) or 64 (blocks up to 1024 threads, more
+// resident warps, some spilling).  The autotuner picks; results are equal.
+__global__ void __launch_bounds__(512, 1)
+k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
+            unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
+            unsigned chunk)
+{
+    transport_body(jobs, n_jobs, total, counter, gtab, inv_ds, chunk);
+}
+
+__global__ void __launch_bounds__(1024, 1)
+k_transport_r64(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
+                unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab,
+                float inv_ds, unsigned chunk)
+{
+    transport_body(jobs, n_jobs, total, counter, gtab, inv_ds, chunk);
 }
 
 // ------------------------------------------------------------- self-tests
@@ -492,7 +516,7 @@ __global__ void k_debug_tables(const Tables *tab, float inv_ds, const float *e, 
     out[5 * i + 0] = re.x;
     out[5 * i + 1] = energy_at_range(tab->er, re.x, inv_ds);
     out[5 * i + 2] = re.y;
-    out[5 * i + 3] = hs.x;
+    out[5 * i + 3] = highland_coeff(hs.x);
     out[5 * i + 4] = hs.y;
 }
 
@@ -505,8 +529,14 @@ __global__ void k_normalise(const NormJob *__restrict__ jobs)
     const double factor = (W == 0 || J.n_hist == 0) ? 0.0
         : (double)W / (double)J.n_hist * 1.602176634e-10 / (16777216.0 * J.voxel_cm3);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < J.nvox; i += stride)
-        J.dose[i] = (float)((double)J.tally[i] * factor / (double)J.rho[i]);
+    unsigned long long dep = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < J.nvox; i += stride) {
+        const unsigned long long t = J.tally[i];
+        dep += t;
+        J.dose[i] = (float)((double)t * factor / (double)J.rho[i]);
+    }
+    dep = warp_sum_u64(dep);
+    if ((threadIdx.x & 31) == 0 && dep) atomicAdd(J.ledger + LED_DEP, dep);
 }
 
 }  // namespace dose

@@ -25,7 +25,7 @@ DOSE_OK, DOSE_EINVAL, DOSE_ENOMEM, DOSE_ECUDA, DOSE_ETIMEOUT, DOSE_ESTEPLIMIT, D
  DOSE_STATUS, DOSE_START_PHASE, DOSE_FIELD_END_NS, DOSE_EMTM_STATS, DOSE_HIST_PREFIX) = range(11)
 DOSE_PHYS_STRAGGLING, DOSE_PHYS_MCS, DOSE_PHYS_NUCLEAR, DOSE_PHYS_ALL = 1, 2, 4, 7
 (DOSE_OPT_PHYSICS, DOSE_OPT_MAX_STEPS, DOSE_OPT_BLOCK, DOSE_OPT_BLOCKS_PER_SM, DOSE_OPT_CHUNK,
- DOSE_OPT_TIMEOUT_MS, DOSE_OPT_FAIL_ALLOC_AFTER) = range(7)
+ DOSE_OPT_TIMEOUT_MS, DOSE_OPT_FAIL_ALLOC_AFTER, DOSE_OPT_REGISTERS) = range(8)
 DOSE_JOB_CLEAR, DOSE_JOB_FINISH = 1, 2
 LEDGER = ("deposited", "escaped", "removed", "incident", "steps", "histories", "flags", "protons")
 
@@ -79,6 +79,7 @@ def _load():
         "dose_last_error": ([P], C.c_char_p),
         "dose_version": ([], I),
         "dose_debug_philox": ([P, P, P, I, P], I),
+        "dose_autotune": ([P, I, U64, U64, U64, P, P], I),
         "dose_debug_tables": ([P, I, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -217,6 +218,14 @@ def dose_read(ctx, what, phase, dst, stream=None):
     p, dev = _ptr(dst)
     _check(_lib.dose_read(ctx, int(what), int(phase), p, _nbytes(dst), dev, _stream(stream)), ctx)
     return dst
+
+
+def dose_autotune(ctx, phase, n_histories, sample_histories, seed, stream=None):
+    """Returns (register option, block, chunk, microseconds of the best shape)."""
+    best = (C.c_int64 * 4)()
+    _check(_lib.dose_autotune(ctx, int(phase), int(n_histories), int(sample_histories), int(seed),
+                              _stream(stream), best), ctx)
+    return tuple(int(v) for v in best)
 
 
 def dose_set_option(ctx, option, value):

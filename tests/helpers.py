@@ -43,6 +43,40 @@ def gpu_run(D, phantom, plan, n_hist, seed, phase=0, physics=7, spr_scale=1.0,
             D.dose_destroy(ctx)
 
 
+def whole_plan_on(phase, n_phases):
+    """Delivery that puts the whole plan on one phase: start there with a
+    breathing period far longer than the delivery."""
+    return W.Delivery(n_phases=n_phases, start_phase=phase, period_ns=n_phases * 10 ** 15)
+
+
+def gpu_batches(D, phantom, plan, n_hist, seed, n_batches, phase=0, physics=7, **kw):
+    """GPU estimate of an n_hist-history dose of the whole plan on `phase`
+    as the mean of n_batches independent runs (seed + 7919 b, n_hist /
+    n_batches histories each); returns (mean dose, its standard error)."""
+    ctx = make_ctx(D, phantom)
+    try:
+        D.dose_set_option(ctx, D.DOSE_OPT_PHYSICS, physics)
+        dl = None if phase == 0 else D.delivery_struct(whole_plan_on(phase, phantom.n_phases))
+        D.dose_add_spots(ctx, D.spots_array(plan), dl)
+        shape = phantom.hu.shape[-3:]
+        nb = n_hist // n_batches
+        doses = []
+        for b in range(n_batches):
+            D.dose_run_phase(ctx, phase, nb, seed + 7919 * b, kw.get("spr_scale", 1.0),
+                             kw.get("shift", (0.0, 0.0, 0.0)))
+            doses.append(D.dose_read(ctx, D.DOSE_PHASE_DOSE, phase, np.zeros(shape, np.float32)))
+    finally:
+        D.dose_destroy(ctx)
+    doses = np.stack(doses).astype(np.float64)
+    return doses.mean(axis=0), doses.std(axis=0, ddof=1) / np.sqrt(n_batches)
+
+
+def body_mask(orc, phantom, phase=None, rho_min=0.1):
+    """Voxels inside the patient (density above air); dose outside the
+    external contour is not evaluated (Sec. 2.A: the MC is limited to it)."""
+    return orc.density(phantom, phase) >= rho_min
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_batches(orc, phantom, plan, n_hist, seed, n_batches=1, phase=None, **kw):
     """Oracle dose of an n_hist run as the mean over n_batches interleaved
