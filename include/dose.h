@@ -231,6 +231,41 @@ const char *dose_last_error(const dose_ctx *c);
 /* Library version, for the binding's load check.                           */
 int dose_version(void);
 
+/* Dose of one static plan without allocating device memory.
+ *
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc -- code inside a framework or service that owns the device's
+ * memory through its own allocator, or that must not allocate once it is
+ * running.  The caller passes device input and output buffers; every other
+ * buffer the kernels use (tally, spot table, history allocation, ledger,
+ * work counter, launch descriptors, lookup tables) lives in one fixed-size
+ * static device array that each GPU loading this library holds until the
+ * process exits.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.
+ *
+ * Computes what dose_create_grid + dose_add_spots(delivery NULL) +
+ * dose_run_phase(phase 0, spr_scale 1, no shift) compute, with default
+ * options: hu is int16[nx ny nz] in device memory (x fastest), spots is a
+ * host array, dose receives float32[nx ny nz] Gy in device memory;
+ * ledger_out (host, may be NULL) receives the 8-word ledger of
+ * DOSE_ENERGY_LEDGER, after which the call waits for the stream.
+ * Limits: nx ny nz <= DOSE_NOALLOC_MAX_VOXELS and n_spots <=
+ * DOSE_NOALLOC_MAX_SPOTS; larger inputs return DOSE_EINVAL with a message
+ * in dose_last_error(NULL).
+ * The first call on a device sets the array up for that device (finds its
+ * device address, uploads the tables) and waits for it: make that first
+ * call before any stream capture.  The call also waits for the stream while
+ * it uploads the spot table and launch descriptors.  All calls share the
+ * one array, which keeps the previous call's contents (the call clears what
+ * must start at zero): calls whose work overlaps on the GPU race with each
+ * other and must be serialised by the caller.                              */
+#define DOSE_NOALLOC_MAX_VOXELS 2097152   /* 2^21, e.g. 128^3: 16 MiB of tally */
+#define DOSE_NOALLOC_MAX_SPOTS 4096
+int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_mm, float dy_mm,
+                           float dz_mm, const float origin_mm[3], const float beam_dir[3],
+                           const dose_spot *spots, int n_spots, uint64_t n_histories, uint64_t seed,
+                           float *dose, uint64_t ledger_out[8], void *stream);
+
 /* Self-test of the device random-number generator: Philox4x32-10 (Salmon
  * et al., SC'11; the generator of Sec. 2.B, footnote b) of n counters
  * ctr[4 i..4 i+3] under keys key[2 i..2 i+1] into out[4 i..], and the six

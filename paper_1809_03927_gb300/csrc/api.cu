@@ -286,6 +286,10 @@ bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1])
 
 }  // namespace
 
+namespace dose {
+void set_thread_error(const char *msg) { g_thread_err = msg; }
+}  // namespace dose
+
 // ======================================================================== ABI
 extern "C" {
 

@@ -6,6 +6,9 @@
 
 namespace dose {
 
+// Record the message dose_last_error(NULL) returns on this thread.
+void set_thread_error(const char *msg);
+
 __global__ void k_density(const int16_t *hu, float *rho, long long n, const Tables *tab);
 __global__ void k_alloc(const AllocJob *jobs);
 __global__ void k_transport(const TJob *jobs, int n_jobs, unsigned long long total,

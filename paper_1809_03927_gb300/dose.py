@@ -80,6 +80,7 @@ def _load():
         "dose_version": ([], I),
         "dose_debug_philox": ([P, P, P, I, P], I),
         "dose_autotune": ([P, I, U64, U64, U64, P, P], I),
+        "dose_run_phase_noalloc": ([P, I, I, I, F, F, F, P, P, P, I, U64, U64, P, P, P], I),
         "dose_debug_tables": ([P, I, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -226,6 +227,23 @@ def dose_autotune(ctx, phase, n_histories, sample_histories, seed, stream=None):
     _check(_lib.dose_autotune(ctx, int(phase), int(n_histories), int(sample_histories), int(seed),
                               _stream(stream), best), ctx)
     return tuple(int(v) for v in best)
+
+
+def dose_run_phase_noalloc(hu, nx, ny, nz, dx_mm, dy_mm, dz_mm, origin_mm, beam_dir, spots,
+                           n_histories, seed, dose, stream=None):
+    """Allocation-free dose of a static plan: ``hu`` (int16) and ``dose``
+    (float32) are device tensors, ``spots`` a ``dose_spot`` array; returns
+    the 8-word ledger (the call waits for the stream)."""
+    hp, hdev = _ptr(hu)
+    dp, ddev = _ptr(dose)
+    if not (hdev and ddev):
+        raise ValueError("hu and dose must be device tensors")
+    led = (C.c_uint64 * 8)()
+    _check(_lib.dose_run_phase_noalloc(hp, int(nx), int(ny), int(nz), float(dx_mm), float(dy_mm),
+                                       float(dz_mm), _f3(origin_mm), _f3(beam_dir),
+                                       C.cast(spots, C.c_void_p), len(spots), int(n_histories),
+                                       int(seed), dp, led, _stream(stream)), None)
+    return np.array(led[:], dtype=np.uint64)
 
 
 def dose_set_option(ctx, option, value):
