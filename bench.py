@@ -46,6 +46,13 @@ def _args():
     p.add_argument("--impl", default="engine", choices=["engine", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    p.add_argument("--no-4d", action="store_true", help="skip the 4D-plan measurement")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement")
+    p.add_argument("--serve-window", type=float, default=5.0, help="seconds of Poisson arrivals")
+    p.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
+    p.add_argument("--serve-budget-gb", type=float, default=150.0, help="device memory for request slots")
+    p.add_argument("--histories-4d", type=int, default=100_000_000, help="histories per phase of the 4D plan")
     p.add_argument("--histories", type=int, default=N_HIST,
                    help="histories per step (smaller cases for profiling; the metric's workload is 1e7)")
     return p.parse_args()
@@ -164,6 +171,243 @@ def run_reference(args):
                                        "sample of the 1e7-history run; ms_per_step extrapolated"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ 4D plan
+def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
+    """Seconds per 4D dose of the synthetic 4DCT: 10 phases of 256x256x160
+    at 1x1x2.5 mm, 3000 spots on 20 layers (70-180 MeV), delivery timeline
+    (1e9 p/s, 2 ms spot switch, 1 s layer switch, 4 s period, random start),
+    n_per_phase histories per phase in one launch, EMTM accumulation onto
+    phase 0 with 2x2x5 subvoxels (0.5 mm) and the Eq. 2 sum.  Grids, DVFs
+    and plan are resident; the timed plan runs the timeline, all phases'
+    transport and the accumulation."""
+    from paper_1809_03927_gb300 import workloads as W
+    ph, dvf, geo = W.phantom_4dct()
+    plan = W.tumour_plan(geo, ph.origin)
+    dlv = D.delivery_struct(W.Delivery(seed=3))
+    nx, ny, nz = ph.n
+    hu_dev = torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda()
+    dvf_dev = torch.from_numpy(dvf).cuda()
+    del dvf
+    ctx = D.dose_create_grid(nx, ny, nz, *ph.d, ph.origin, ph.n_phases, hu_dev, ph.beam_dir, stream)
+    spots = D.spots_array(plan)
+    try:
+        D.dose_add_spots(ctx, spots, dlv, stream)
+        phase_p = D.dose_read(ctx, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
+        tune = D.dose_autotune(ctx, int(np.argmax(phase_p)), n_per_phase, 2_000_000, seed, stream)
+
+        def plan_once():
+            D.dose_add_spots(ctx, spots, dlv, stream)
+            D.dose_run_4d(ctx, n_per_phase, seed, 0, (2, 2, 5), dvf=dvf_dev, stream=stream)
+
+        plan_once()
+        torch.cuda.synchronize()
+        walls, evs = [], []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(stream)
+            plan_once()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - t0)
+            evs.append(e0.elapsed_time(e1) / 1e3)
+        # the accumulation alone
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        D.dose_accumulate_subvoxel(ctx, 0, (2, 2, 5), dvf=dvf_dev, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        emtm_s = e0.elapsed_time(e1) / 1e3
+        steps = sum(int(D.dose_read(ctx, D.DOSE_ENERGY_LEDGER, p, np.zeros(8, np.uint64))[4])
+                    for p in range(ph.n_phases) if phase_p[p] > 0)
+        n_run = int(np.count_nonzero(phase_p)) * n_per_phase
+        stats = D.dose_read(ctx, D.DOSE_EMTM_STATS, 0, np.zeros(4, np.uint64))
+    finally:
+        D.dose_destroy(ctx)
+    s_plan = float(np.median(walls))
+    return {"s_per_plan": s_plan, "s_per_plan_device": float(np.median(evs)), "reps": reps,
+            "histories_per_plan": n_run, "histories_per_s": n_run / s_plan,
+            "steps_per_history": steps / n_run, "emtm_s": emtm_s,
+            "emtm_subvoxels": int(stats[0]), "emtm_atomic_pairs": int(stats[2]),
+            "workload": "synthetic 4DCT 10 x 256x256x160 at 1x1x2.5 mm, 3000 spots / 20 layers 70-180 MeV, "
+                        f"{n_per_phase:.0e} histories per phase, EMTM 2x2x5 onto phase 0",
+            "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}}
+
+
+# ------------------------------------------------------------------ ragged batch
+def _bench_ragged(D, torch, stream, n_random=62, seed=4, reps=2):
+    """A ragged batch of dose jobs in one persistent launch against the plain
+    engine (one job per launch): 62 random cube phantoms (64-256 voxels a
+    side at 2 mm, random slabs and spheres), 20-5000 spots (70-220 MeV), 1e5-5e7
+    histories (log-uniform), plus the 4DCT plan delivered with 4x layer
+    repainting and with 30 %-duty gating (phases 4-6), every phase it reaches
+    a job of its own (1e7 histories each)."""
+    from paper_1809_03927_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    ctxs, specs = [], []
+    try:
+        for _ in range(n_random):
+            side = int(rng.choice(np.arange(64, 257, 16)))
+            ph = W.random_phantom(rng, side)
+            pl = W.random_plan(rng, W.log_uniform_int(rng, 20, 5000), side * 2.0 * 0.3)
+            n = W.log_uniform_int(rng, 1e5, 5e7)
+            c = D.dose_create_grid(side, side, side, *ph.d, ph.origin, 1,
+                                   torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda(), ph.beam_dir, stream)
+            ctxs.append(c)
+            D.dose_add_spots(c, D.spots_array(pl), None, stream)
+            specs.append(dict(ctx=c, phase=0, n_histories=n, seed=int(rng.integers(1, 2 ** 62))))
+        ph4, _, geo = W.phantom_4dct(with_dvf=False)
+        plan4 = W.tumour_plan(geo, ph4.origin)
+        hu4 = torch.from_numpy(np.ascontiguousarray(ph4.hu)).cuda()
+        for dl in (W.Delivery(seed=3, repaints=4), W.Delivery(seed=3, gated=1, gate_first=4, gate_last=6)):
+            c = D.dose_create_grid(*ph4.n, *ph4.d, ph4.origin, ph4.n_phases, hu4, ph4.beam_dir, stream)
+            ctxs.append(c)
+            D.dose_add_spots(c, D.spots_array(plan4), D.delivery_struct(dl), stream)
+            pp = D.dose_read(c, D.DOSE_SUBPLAN, 0, np.zeros((ph4.n_phases, len(plan4)), np.uint64)).sum(axis=1)
+            for p in range(ph4.n_phases):
+                if pp[p] > 0:
+                    specs.append(dict(ctx=c, phase=p, n_histories=10_000_000, seed=77 + p))
+        total = sum(sp["n_histories"] for sp in specs)
+        jobs = D.make_jobs(specs)
+        big = max(specs, key=lambda sp: sp["n_histories"])
+        tune = D.dose_autotune(big["ctx"], big["phase"], big["n_histories"], 2_000_000, 1, stream)
+        for c in ctxs:
+            for opt, v in ((D.DOSE_OPT_REGISTERS, tune[0]), (D.DOSE_OPT_BLOCK, tune[1]), (D.DOSE_OPT_CHUNK, tune[2])):
+                D.dose_set_option(c, opt, v)
+        D.dose_run_batch(jobs, stream)                    # warm-up
+        torch.cuda.synchronize()
+        tb = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            D.dose_run_batch(jobs, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tb.append(e0.elapsed_time(e1) / 1e3)
+        tp = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for sp in specs:
+                D.dose_run_phase(sp["ctx"], sp["phase"], sp["n_histories"], sp["seed"], 1.0, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tp.append(e0.elapsed_time(e1) / 1e3)
+    finally:
+        for c in ctxs:
+            D.dose_destroy(c)
+    return {"jobs": len(specs), "histories": total, "batched_s": float(np.median(tb)),
+            "batched_histories_per_s": total / float(np.median(tb)), "plain_s": float(np.median(tp)),
+            "plain_histories_per_s": total / float(np.median(tp)),
+            "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}}
+
+
+# ------------------------------------------------------------------ serving
+def _requests(window_s, rate, seed=5):
+    """Poisson arrivals (seeded exponential gaps) of robust-scenario requests:
+    nominal, +-3 mm setup shift on one axis, or +-3.5 % stopping-power scale;
+    total histories log-uniform in [1e6, 1e8] (split over the phases)."""
+    rng = np.random.default_rng(seed)
+    scen = [(1.0, (0.0, 0.0, 0.0))]
+    for ax in range(3):
+        for sgn in (1.0, -1.0):
+            sh = [0.0, 0.0, 0.0]
+            sh[ax] = 3.0 * sgn
+            scen.append((1.0, tuple(sh)))
+    scen += [(1.035, (0.0, 0.0, 0.0)), (0.965, (0.0, 0.0, 0.0))]
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > window_s:
+            return out
+        spr, sh = scen[int(rng.integers(len(scen)))]
+        n = int(round(float(np.exp(rng.uniform(np.log(1e6), np.log(1e8))))))
+        out.append(dict(t=t, n=n, seed=int(rng.integers(1, 2 ** 62)), spr=spr, shift=sh))
+
+
+def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
+    """p50/p99 latency (arrival -> dose ready) and histories/s of the
+    continuous-batching server against the plain engine (each request alone,
+    one phase job per launch, first come first served) on the same arrival
+    schedule over the resident 4DCT."""
+    from paper_1809_03927_gb300 import workloads as W
+    ph, dvf, geo = W.phantom_4dct()
+    plan = W.tumour_plan(geo, ph.origin)
+    dlv = D.delivery_struct(W.Delivery(seed=3))
+    spots = D.spots_array(plan)
+    nx, ny, nz = ph.n
+    hu_dev = torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda()
+    dvf_dev = torch.from_numpy(dvf).cuda()
+    del dvf
+    reqs = _requests(window_s, rate)
+    base = D.dose_create_grid(nx, ny, nz, *ph.d, ph.origin, ph.n_phases, hu_dev, ph.beam_dir, stream)
+    out = {"requests": len(reqs), "window_s": window_s, "rate_per_s": rate,
+           "offered_histories_per_s": sum(r["n"] for r in reqs) / window_s}
+    try:
+        # launch shape for the 4DCT from the autotuner (shared by both engines)
+        probe = D.dose_create_view(base)
+        D.dose_add_spots(probe, spots, dlv, stream)
+        pp = D.dose_read(probe, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
+        tune = D.dose_autotune(probe, int(np.argmax(pp)), 10_000_000, 2_000_000, 1, stream)
+        for opt, v in ((D.DOSE_OPT_REGISTERS, tune[0]), (D.DOSE_OPT_BLOCK, tune[1]), (D.DOSE_OPT_CHUNK, tune[2])):
+            D.dose_set_option(base, opt, v)
+            D.dose_set_option(probe, opt, v)
+        phases = [p for p in range(ph.n_phases) if pp[p] > 0]
+
+        # ---- served: continuous batching
+        srv = D.dose_server_create(base, budget_bytes, 40_000_000, spots, dlv, min_slice=20_000,
+                                   nsub=(2, 2, 5), dvf=dvf_dev)
+        lat, done_at, k, t0 = [], {}, 0, time.perf_counter()
+        ids = {}
+        max_active = 0
+        while len(done_at) < len(reqs):
+            now = time.perf_counter() - t0
+            while k < len(reqs) and reqs[k]["t"] <= now:
+                r = reqs[k]
+                ids[D.dose_server_submit(srv, r["n"], r["seed"], r["spr"], r["shift"])] = k
+                k += 1
+            st = D.dose_server_stats(srv)
+            max_active = max(max_active, st["active"] + st["queued"])
+            if st["queued"] + st["active"] == 0:
+                time.sleep(max(0.0, min(0.005, reqs[k]["t"] - now)) if k < len(reqs) else 0.0)
+                continue
+            for rid in D.dose_server_step(srv, stream):
+                done_at[ids[rid]] = time.perf_counter() - t0
+                D.dose_server_release(srv, rid)
+        total_s = time.perf_counter() - t0
+        st = D.dose_server_stats(srv)
+        D.dose_server_destroy(srv)
+        lat = [done_at[i] - reqs[i]["t"] for i in range(len(reqs))]
+        hist = sum(r["n"] // len(phases) * len(phases) for r in reqs)
+        out["served"] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                         "mean_s": float(np.mean(lat)), "histories_per_s": hist / total_s, "makespan_s": total_s,
+                         "steps": st["steps"], "slots": st["slots"], "max_in_system": max_active,
+                         "slot_gb": st["slot_bytes"] / 1e9}
+
+        # ---- plain: one request at a time, one phase job per launch
+        done_at, t0, k = {}, time.perf_counter(), 0
+        for i, r in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if r["t"] > now:
+                time.sleep(r["t"] - now)
+            n_pp = max(1, r["n"] // len(phases))
+            for p in range(ph.n_phases):
+                if p in phases:
+                    D.dose_run_phase(probe, p, n_pp, r["seed"], r["spr"], r["shift"], stream)
+            D.dose_accumulate_subvoxel(probe, 0, (2, 2, 5), dvf=dvf_dev, stream=stream)
+            torch.cuda.current_stream().synchronize()
+            done_at[i] = time.perf_counter() - t0
+        total_s = time.perf_counter() - t0
+        D.dose_destroy(probe)
+        lat = [done_at[i] - reqs[i]["t"] for i in range(len(reqs))]
+        out["plain"] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                        "mean_s": float(np.mean(lat)), "histories_per_s": hist / total_s, "makespan_s": total_s}
+        out["launch"] = {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}
+    finally:
+        D.dose_destroy(base)
+    return out
 
 
 # ------------------------------------------------------------------ engine
@@ -299,6 +543,13 @@ def run_engine(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    if not args.no_4d:
+        line["four_d"] = _bench_4d(D, torch, stream, args.histories_4d, 2, SEED)
+    if not args.no_ragged:
+        line["ragged_batch"] = _bench_ragged(D, torch, stream)
+    if not args.no_serve:
+        line["serving"] = _bench_serving(D, torch, stream, args.serve_window, args.serve_rate,
+                                         int(args.serve_budget_gb * 1e9))
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _oracle_sample(phantom, plan)
     print(json.dumps(line), flush=True)

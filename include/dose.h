@@ -178,6 +178,64 @@ typedef struct dose_job {
 } dose_job;
 int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream);
 
+/* The whole 4D dose (Sec. 2.A): the Monte Carlo of every phase's subplan
+ * (from the delivery given to dose_add_spots; Sec. 2.B-2.C) with
+ * n_histories_per_phase histories each, all phases in one persistent launch
+ * (phases without protons get zero dose), then the accumulation onto
+ * ref_phase as in dose_accumulate_subvoxel (method 0, Eqs. 2, 4-6).  Phase p
+ * uses Philox stream p under `seed`.  Reads the per-phase proton totals back
+ * to the host (a short wait on the stream) to skip empty phases.           */
+int dose_run_4d(dose_ctx *c, uint64_t n_histories_per_phase, uint64_t seed, float spr_scale,
+                const float shift_mm[3], int ref_phase, const int nsub[3], const float *dvf,
+                int dvf_on_device, const uint8_t *mask, int mask_on_device, void *stream);
+
+/* ---- Serving: continuous batching of dose requests ---------------------
+ * Requests are robust scenarios of one plan over the resident 4DCT of
+ * `base` (the multiple runs of Sec. 4.C and the robust optimisation of
+ * Sec. 4.C/5 need many such doses): seed, total histories (split evenly
+ * over the phases the plan reaches), stopping-power scale and setup shift.
+ * dose_server_step admits queued requests into free slots -- each slot is a
+ * view of the base grid with the plan loaded once, created while
+ * memory_budget_bytes allows and then reused -- gives every active request
+ * an equal share of step_histories (at least min_slice per phase), runs all
+ * those slices in one persistent launch, finishes the requests whose last
+ * slice ran (normalisation, and the accumulation onto ref_phase when
+ * `accumulate`; dvf is a device array as in dose_accumulate_subvoxel) and
+ * waits for the stream.  A request's result is bit-identical to the same
+ * request served alone: histories are keyed by (seed, history, phase).     */
+typedef struct dose_server dose_server;
+typedef struct dose_server_config {
+    uint64_t memory_budget_bytes;
+    uint64_t step_histories;
+    uint64_t min_slice;
+    int32_t max_active;        /* 0: no cap beyond the budget */
+    int32_t ref_phase;
+    int32_t nsub[3];
+    int32_t accumulate;
+    const float *dvf;          /* device, n_phases x 3 x nvox mm, or NULL = identity */
+} dose_server_config;
+typedef struct dose_request {
+    uint64_t n_histories;
+    uint64_t seed;
+    float spr_scale;
+    float shift_mm[3];
+} dose_request;
+int dose_server_create(dose_ctx *base, const dose_server_config *cfg, const dose_spot *spots,
+                       int64_t n_spots, const dose_delivery *delivery, dose_server **out);
+int dose_server_submit(dose_server *s, const dose_request *req, int64_t *id);
+/* completed (host, max_completed entries) receives the ids finished by this step. */
+int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_completed,
+                     int *n_completed);
+/* Read a finished request's result (selectors as dose_read); valid until
+ * dose_server_release frees its slot.                                      */
+int dose_server_result(dose_server *s, int64_t id, int what, int phase, void *dst, size_t bytes,
+                       int dst_on_device, void *stream);
+int dose_server_release(dose_server *s, int64_t id);
+/* out: queued, active, slots, completed, histories run, steps, bytes per
+ * slot, finished but not released.                                         */
+int dose_server_stats(const dose_server *s, uint64_t out[8]);
+void dose_server_destroy(dose_server *s);
+
 /* Supply the dose of one phase from outside (float32[nvox] Gy), e.g. to
  * accumulate doses computed elsewhere.                                     */
 int dose_set_phase_dose(dose_ctx *c, int phase, const float *dose, int dose_on_device,

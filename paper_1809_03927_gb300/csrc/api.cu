@@ -288,6 +288,22 @@ bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1])
 
 namespace dose {
 void set_thread_error(const char *msg) { g_thread_err = msg; }
+
+void grid_info(const dose_ctx *c, int dims[4])
+{
+    dims[0] = c->g->n[0]; dims[1] = c->g->n[1]; dims[2] = c->g->n[2]; dims[3] = c->g->n_phases;
+}
+
+int set_phase_zero(dose_ctx *c, int phase, void *stream)
+{
+    int rc;
+    if ((rc = use_device(c))) return rc;
+    if ((rc = ensure_results(c, S(stream)))) return rc;
+    CK(c, cudaMemsetAsync(c->ph[phase].dose, 0, c->g->nvox * sizeof(float), S(stream)));
+    c->ph[phase].has_dose = true;
+    c->have_accum = false;
+    return DOSE_OK;
+}
 }  // namespace dose
 
 // ======================================================================== ABI
@@ -716,6 +732,43 @@ done:
         best[3] = (int64_t)(best_ms * 1000.0f);
     }
     return rc;
+}
+
+int dose_run_4d(dose_ctx *c, uint64_t n_histories_per_phase, uint64_t seed, float spr_scale,
+                const float shift_mm[3], int ref_phase, const int nsub[3], const float *dvf,
+                int dvf_on_device, const uint8_t *mask, int mask_on_device, void *stream)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (!c->have_plan) return fail(c, DOSE_ESTATE, "no spots loaded");
+    if (n_histories_per_phase == 0) return fail(c, DOSE_EINVAL, "n_histories_per_phase is 0");
+    const int P = c->g->n_phases;
+    if (ref_phase < 0 || ref_phase >= P) return fail(c, DOSE_EINVAL, "ref_phase out of range");
+    int rc;
+    if ((rc = use_device(c))) return rc;
+    cudaStream_t st = S(stream);
+    // per-phase proton totals of the subplans (skip phases with none)
+    std::vector<unsigned long long> pp((size_t)P * c->n_spots);
+    CK(c, cudaMemcpyAsync(pp.data(), c->pp, pp.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if ((rc = sync_stream(c, st))) return rc;
+    if ((rc = ensure_results(c, st))) return rc;
+    std::vector<dose_job> jobs;
+    for (int p = 0; p < P; ++p) {
+        unsigned long long w = 0;
+        for (int s = 0; s < c->n_spots; ++s) w += pp[(size_t)p * c->n_spots + s];
+        if (w == 0) {
+            CK(c, cudaMemsetAsync(c->ph[p].dose, 0, c->g->nvox * sizeof(float), st));
+            c->ph[p].has_dose = true;
+            continue;
+        }
+        dose_job j;
+        j.ctx = c; j.phase = p; j.flags = DOSE_JOB_CLEAR | DOSE_JOB_FINISH;
+        j.n_histories = n_histories_per_phase; j.hist_begin = 0; j.hist_end = n_histories_per_phase;
+        j.seed = seed; j.spr_scale = spr_scale;
+        for (int k = 0; k < 3; ++k) j.shift_mm[k] = shift_mm ? shift_mm[k] : 0.0f;
+        jobs.push_back(j);
+    }
+    if (!jobs.empty() && (rc = dose_run_batch(jobs.data(), (int)jobs.size(), stream))) return rc;
+    return dose_accumulate_subvoxel(c, ref_phase, nsub, dvf, dvf_on_device, mask, mask_on_device, 0, stream);
 }
 
 int dose_set_phase_dose(dose_ctx *c, int phase, const float *dose, int on_device, void *stream)

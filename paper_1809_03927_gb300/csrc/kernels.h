@@ -8,6 +8,13 @@ namespace dose {
 
 // Record the message dose_last_error(NULL) returns on this thread.
 void set_thread_error(const char *msg);
+}  // namespace dose
+struct dose_ctx;
+namespace dose {
+// nx, ny, nz, n_phases of a context's grid.
+void grid_info(const dose_ctx *c, int dims[4]);
+// Give a phase zero dose (a phase its plan does not reach).
+int set_phase_zero(dose_ctx *c, int phase, void *stream);
 
 __global__ void k_density(const int16_t *hu, float *rho, long long n, const Tables *tab);
 __global__ void k_alloc(const AllocJob *jobs);

@@ -1,0 +1,276 @@
+// Continuous-batching dose server on top of the C ABI.
+//
+// Requests (robust scenarios of one plan over one resident 4DCT: seed,
+// history count, stopping-power scale, setup shift) wait in a FIFO queue.
+// Each step admits queued requests into free slots -- a slot is a view of
+// the resident grid with the plan loaded once, created while the memory
+// budget allows and reused afterwards -- then gives every active request a
+// share of the step's history budget over its phases and runs all those
+// slices in ONE persistent launch (dose_run_batch).  A request whose last
+// slice ran is finished (normalised, accumulated onto the reference phase)
+// and reported.  Requests that arrive while others are running join at the
+// next step, so short requests are not stuck behind long ones, and their
+// work shares launches with everything else in flight.  Because histories
+// are keyed by (seed, history, phase), a request's result does not depend
+// on the mix it was served in.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include "dose.h"
+#include "kernels.h"
+
+struct dose_server {
+    struct Slot {
+        dose_ctx *view = nullptr;
+        int64_t request = -1;          // -1: free
+    };
+    struct Active {
+        int64_t id;
+        dose_request req;
+        int slot;
+        uint64_t per_phase;            // histories per phase with protons
+        uint64_t next;                 // next history index (same for every phase)
+    };
+    dose_ctx *base = nullptr;
+    dose_server_config cfg{};
+    std::vector<dose_spot> spots;
+    dose_delivery delivery{};
+    bool has_delivery = false;
+    std::vector<int> phases;           // phases whose subplan has protons
+    size_t slot_bytes = 0;
+    std::vector<Slot> slots;
+    std::deque<std::pair<int64_t, dose_request>> queue;
+    std::vector<Active> active;
+    std::vector<int64_t> done;         // finished, result not yet released
+    std::vector<std::pair<int64_t, int>> finished_slot;  // id -> slot
+    int64_t next_id = 0;
+    uint64_t histories_done = 0, completed = 0, steps = 0;
+    std::string err;
+};
+
+namespace {
+
+int sfail(dose_server *s, int code, const char *msg)
+{
+    if (s) s->err = msg;
+    dose::set_thread_error(msg);
+    return code;
+}
+
+// Device bytes one slot holds: tallies, doses and ledgers of every phase,
+// the EMTM E/M arrays, the accumulated dose, the per-phase allocation
+// arrays and the plan (an upper bound, rounded up).
+size_t slot_footprint(int nx, int ny, int nz, int n_phases, int64_t n_spots, bool accumulate)
+{
+    const size_t nvox = (size_t)nx * ny * nz, P = (size_t)n_phases;
+    size_t b = P * nvox * (8 + 4) + P * 64;
+    if (accumulate) b += 2 * P * nvox * 8 + nvox * 4 + P * 4 + 64 + nvox * 4;
+    b += P * (size_t)(n_spots + 1) * (8 + 4 + 8) + (size_t)n_spots * (16 + 8 + 4 + 4 + 8 * P) + (1 << 20);
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dose_server_create(dose_ctx *base, const dose_server_config *cfg, const dose_spot *spots, int64_t n_spots,
+                       const dose_delivery *delivery, dose_server **out)
+{
+    if (!out) return sfail(nullptr, DOSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!base || !cfg || !spots || n_spots <= 0) return sfail(nullptr, DOSE_EINVAL, "base, cfg and spots are required");
+    if (cfg->step_histories == 0) return sfail(nullptr, DOSE_EINVAL, "step_histories must be positive");
+    if (cfg->accumulate && (cfg->nsub[0] < 1 || cfg->nsub[1] < 1 || cfg->nsub[2] < 1))
+        return sfail(nullptr, DOSE_EINVAL, "nsub must be positive");
+    dose_server *s = new dose_server;
+    s->base = base;
+    s->cfg = *cfg;
+    s->spots.assign(spots, spots + n_spots);
+    if (delivery) { s->delivery = *delivery; s->has_delivery = true; }
+    // the base carries the grid; find the phases the plan reaches with a
+    // scratch view (its subplan is also the template every slot reproduces)
+    dose_ctx *probe = nullptr;
+    int rc = dose_create_view(base, &probe);
+    if (rc) { delete s; return rc; }
+    rc = dose_add_spots(probe, spots, n_spots, delivery, nullptr);
+    int dims[4] = {0, 0, 0, 0};
+    if (!rc) dose::grid_info(probe, dims);
+    std::vector<uint64_t> pp;
+    if (!rc) {
+        pp.resize((size_t)dims[3] * n_spots);
+        rc = dose_read(probe, DOSE_SUBPLAN, 0, pp.data(), pp.size() * 8, 0, nullptr);
+    }
+    dose_destroy(probe);
+    if (rc) { delete s; return rc; }
+    for (int p = 0; p < dims[3]; ++p) {
+        uint64_t w = 0;
+        for (int64_t k = 0; k < n_spots; ++k) w += pp[(size_t)p * n_spots + k];
+        if (w) s->phases.push_back(p);
+    }
+    if (s->phases.empty()) { delete s; return sfail(nullptr, DOSE_EINVAL, "the plan delivers no protons"); }
+    s->slot_bytes = slot_footprint(dims[0], dims[1], dims[2], dims[3], n_spots, cfg->accumulate != 0);
+    if (cfg->memory_budget_bytes < s->slot_bytes) {
+        delete s;
+        return sfail(nullptr, DOSE_EINVAL, "memory budget is smaller than one request slot");
+    }
+    *out = s;
+    return DOSE_OK;
+}
+
+int dose_server_submit(dose_server *s, const dose_request *req, int64_t *id)
+{
+    if (!s || !req) return sfail(s, DOSE_EINVAL, "server and request are required");
+    if (req->n_histories == 0) return sfail(s, DOSE_EINVAL, "request has no histories");
+    const int64_t rid = s->next_id++;
+    s->queue.emplace_back(rid, *req);
+    if (id) *id = rid;
+    return DOSE_OK;
+}
+
+int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_completed, int *n_completed)
+{
+    if (!s) return sfail(s, DOSE_EINVAL, "server is NULL");
+    if (n_completed) *n_completed = 0;
+    const size_t max_slots = std::max<size_t>(1, s->cfg.memory_budget_bytes / s->slot_bytes);
+    const size_t cap = s->cfg.max_active > 0 ? std::min<size_t>(max_slots, (size_t)s->cfg.max_active) : max_slots;
+    // admit: free slots first, then new slots while the budget allows
+    while (!s->queue.empty()) {
+        int slot = -1;
+        for (size_t k = 0; k < s->slots.size(); ++k)
+            if (s->slots[k].request < 0) { slot = (int)k; break; }
+        if (slot < 0 && s->slots.size() < cap) {
+            dose_server::Slot sl;
+            int rc = dose_create_view(s->base, &sl.view);
+            if (!rc) rc = dose_add_spots(sl.view, s->spots.data(), (int64_t)s->spots.size(),
+                                         s->has_delivery ? &s->delivery : nullptr, stream);
+            if (rc) {
+                if (sl.view) dose_destroy(sl.view);
+                if (rc == DOSE_ENOMEM) break;            // no room now; retry next step
+                return rc;
+            }
+            s->slots.push_back(sl);
+            slot = (int)s->slots.size() - 1;
+        }
+        if (slot < 0) break;
+        auto q = s->queue.front();
+        s->queue.pop_front();
+        dose_server::Active a;
+        a.id = q.first;
+        a.req = q.second;
+        a.slot = slot;
+        a.per_phase = std::max<uint64_t>(1, q.second.n_histories / s->phases.size());
+        a.next = 0;
+        s->slots[slot].request = a.id;
+        s->active.push_back(a);
+    }
+    if (s->active.empty()) return DOSE_OK;
+    // every active request gets an equal share of the step's histories
+    const uint64_t share = std::max<uint64_t>(
+        s->cfg.min_slice ? s->cfg.min_slice : 1,
+        s->cfg.step_histories / (s->active.size() * s->phases.size()));
+    std::vector<dose_job> jobs;
+    std::vector<int> finishing;
+    for (size_t i = 0; i < s->active.size(); ++i) {
+        auto &a = s->active[i];
+        const uint64_t end = std::min(a.per_phase, a.next + share);
+        for (int p : s->phases) {
+            dose_job j;
+            j.ctx = s->slots[a.slot].view;
+            j.phase = p;
+            j.flags = (a.next == 0 ? DOSE_JOB_CLEAR : 0u) | (end == a.per_phase ? DOSE_JOB_FINISH : 0u);
+            j.n_histories = a.per_phase;
+            j.hist_begin = a.next;
+            j.hist_end = end;
+            j.seed = a.req.seed;
+            j.spr_scale = a.req.spr_scale;
+            for (int k = 0; k < 3; ++k) j.shift_mm[k] = a.req.shift_mm[k];
+            jobs.push_back(j);
+        }
+        s->histories_done += (end - a.next) * s->phases.size();
+        a.next = end;
+        if (end == a.per_phase) finishing.push_back((int)i);
+    }
+    int rc = dose_run_batch(jobs.data(), (int)jobs.size(), stream);
+    if (rc) return rc;
+    for (int i : finishing) {
+        auto &a = s->active[i];
+        dose_ctx *v = s->slots[a.slot].view;
+        int dims[4];
+        dose::grid_info(v, dims);
+        // phases the plan does not reach carry zero dose
+        for (int p = 0; p < dims[3]; ++p)
+            if (std::find(s->phases.begin(), s->phases.end(), p) == s->phases.end())
+                if ((rc = dose::set_phase_zero(v, p, stream))) return rc;
+        if (s->cfg.accumulate &&
+            (rc = dose_accumulate_subvoxel(v, s->cfg.ref_phase, s->cfg.nsub, s->cfg.dvf, 1, nullptr, 0, 0, stream)))
+            return rc;
+    }
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return sfail(s, DOSE_ECUDA, cudaGetErrorString(e));
+    ++s->steps;
+    std::vector<dose_server::Active> keep;
+    int nc = 0;
+    for (size_t i = 0; i < s->active.size(); ++i) {
+        const bool fin = std::find(finishing.begin(), finishing.end(), (int)i) != finishing.end();
+        if (!fin) { keep.push_back(s->active[i]); continue; }
+        s->done.push_back(s->active[i].id);
+        s->finished_slot.emplace_back(s->active[i].id, s->active[i].slot);
+        ++s->completed;
+        if (completed && nc < max_completed) completed[nc] = s->active[i].id;
+        ++nc;
+    }
+    s->active.swap(keep);
+    if (n_completed) *n_completed = std::min(nc, max_completed);
+    return DOSE_OK;
+}
+
+int dose_server_result(dose_server *s, int64_t id, int what, int phase, void *dst, size_t bytes, int dst_on_device,
+                       void *stream)
+{
+    if (!s) return sfail(s, DOSE_EINVAL, "server is NULL");
+    for (auto &f : s->finished_slot)
+        if (f.first == id)
+            return dose_read(s->slots[f.second].view, what, phase, dst, bytes, dst_on_device, stream);
+    return sfail(s, DOSE_ESTATE, "request is not finished or was released");
+}
+
+int dose_server_release(dose_server *s, int64_t id)
+{
+    if (!s) return sfail(s, DOSE_EINVAL, "server is NULL");
+    for (size_t k = 0; k < s->finished_slot.size(); ++k) {
+        if (s->finished_slot[k].first != id) continue;
+        s->slots[s->finished_slot[k].second].request = -1;
+        s->finished_slot.erase(s->finished_slot.begin() + k);
+        s->done.erase(std::remove(s->done.begin(), s->done.end(), id), s->done.end());
+        return DOSE_OK;
+    }
+    return sfail(s, DOSE_ESTATE, "request is not finished or was released");
+}
+
+int dose_server_stats(const dose_server *s, uint64_t out[8])
+{
+    if (!s || !out) return sfail(nullptr, DOSE_EINVAL, "server and out are required");
+    out[0] = s->queue.size();
+    out[1] = s->active.size();
+    out[2] = s->slots.size();
+    out[3] = s->completed;
+    out[4] = s->histories_done;
+    out[5] = s->steps;
+    out[6] = s->slot_bytes;
+    out[7] = s->done.size();
+    return DOSE_OK;
+}
+
+void dose_server_destroy(dose_server *s)
+{
+    if (!s) return;
+    for (auto &sl : s->slots) dose_destroy(sl.view);
+    delete s;
+}
+
+}  // extern "C"

@@ -56,7 +56,19 @@ class dose_job(C.Structure):
                 ("seed", C.c_uint64), ("spr_scale", C.c_float), ("shift_mm", C.c_float * 3)]
 
 
+class dose_server_config(C.Structure):
+    _fields_ = [("memory_budget_bytes", C.c_uint64), ("step_histories", C.c_uint64),
+                ("min_slice", C.c_uint64), ("max_active", C.c_int32), ("ref_phase", C.c_int32),
+                ("nsub", C.c_int32 * 3), ("accumulate", C.c_int32), ("dvf", C.c_void_p)]
+
+
+class dose_request(C.Structure):
+    _fields_ = [("n_histories", C.c_uint64), ("seed", C.c_uint64), ("spr_scale", C.c_float),
+                ("shift_mm", C.c_float * 3)]
+
+
 assert C.sizeof(dose_spot) == 32 and C.sizeof(dose_job) == 64
+assert C.sizeof(dose_server_config) == 56 and C.sizeof(dose_request) == 32
 
 
 def _load():
@@ -71,6 +83,7 @@ def _load():
         "dose_add_spots": ([P, P, I64, P, P], I),
         "dose_run_phase": ([P, I, U64, U64, F, P, P], I),
         "dose_run_batch": ([P, I, P], I),
+        "dose_run_4d": ([P, U64, U64, F, P, I, P, P, I, P, I, P], I),
         "dose_set_phase_dose": ([P, I, P, I, P], I),
         "dose_accumulate_subvoxel": ([P, I, P, P, I, P, I, I, P], I),
         "dose_read": ([P, I, I, P, C.c_size_t, I, P], I),
@@ -80,6 +93,13 @@ def _load():
         "dose_version": ([], I),
         "dose_debug_philox": ([P, P, P, I, P], I),
         "dose_autotune": ([P, I, U64, U64, U64, P, P], I),
+        "dose_server_create": ([P, P, P, I64, P, C.POINTER(P)], I),
+        "dose_server_submit": ([P, P, C.POINTER(I64)], I),
+        "dose_server_step": ([P, P, P, I, C.POINTER(I)], I),
+        "dose_server_result": ([P, I64, I, I, P, C.c_size_t, I, P], I),
+        "dose_server_release": ([P, I64], I),
+        "dose_server_stats": ([P, P], I),
+        "dose_server_destroy": ([P], None),
         "dose_run_phase_noalloc": ([P, I, I, I, F, F, F, P, P, P, I, U64, U64, P, P, P], I),
         "dose_debug_tables": ([P, I, P, P], I),
     }
@@ -198,6 +218,20 @@ def dose_run_batch(jobs, stream=None):
     _check(rc, jobs[0].ctx if len(jobs) else None)
 
 
+def dose_run_4d(ctx, n_histories_per_phase, seed, ref_phase, nsub, dvf=None, mask=None,
+                spr_scale=1.0, shift_mm=None, stream=None):
+    ns = (C.c_int * 3)(*[int(v) for v in nsub])
+    if dvf is not None and not _is_torch(dvf):
+        dvf = np.ascontiguousarray(dvf, dtype=np.float32)
+    if mask is not None and not _is_torch(mask):
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    dp, ddev = _ptr(dvf)
+    mp, mdev = _ptr(mask)
+    sh = _f3(shift_mm) if shift_mm is not None else None
+    _check(_lib.dose_run_4d(ctx, int(n_histories_per_phase), int(seed), float(spr_scale), sh,
+                            int(ref_phase), ns, dp, ddev, mp, mdev, _stream(stream)), ctx)
+
+
 def dose_set_phase_dose(ctx, phase, dose, stream=None):
     p, dev = _ptr(dose)
     _check(_lib.dose_set_phase_dose(ctx, int(phase), p, dev, _stream(stream)), ctx)
@@ -244,6 +278,63 @@ def dose_run_phase_noalloc(hu, nx, ny, nz, dx_mm, dy_mm, dz_mm, origin_mm, beam_
                                        C.cast(spots, C.c_void_p), len(spots), int(n_histories),
                                        int(seed), dp, led, _stream(stream)), None)
     return np.array(led[:], dtype=np.uint64)
+
+
+def dose_server_create(base, memory_budget_bytes, step_histories, spots, delivery=None,
+                       min_slice=0, max_active=0, ref_phase=0, nsub=(2, 2, 5), accumulate=1,
+                       dvf=None):
+    """``dvf``: device tensor (n_phases x 3 x nvox) or None (identity)."""
+    cfg = dose_server_config()
+    cfg.memory_budget_bytes, cfg.step_histories, cfg.min_slice = (
+        int(memory_budget_bytes), int(step_histories), int(min_slice))
+    cfg.max_active, cfg.ref_phase, cfg.accumulate = int(max_active), int(ref_phase), int(accumulate)
+    cfg.nsub[:] = [int(v) for v in nsub]
+    if dvf is not None:
+        p, dev = _ptr(dvf)
+        if not dev:
+            raise ValueError("the server's DVF must be a device tensor")
+        cfg.dvf = p
+    out = C.c_void_p()
+    dl = C.byref(delivery) if delivery is not None else None
+    _check(_lib.dose_server_create(base, C.byref(cfg), C.cast(spots, C.c_void_p), len(spots), dl,
+                                   C.byref(out)), None)
+    return out.value
+
+
+def dose_server_submit(server, n_histories, seed, spr_scale=1.0, shift_mm=(0.0, 0.0, 0.0)):
+    r = dose_request(int(n_histories), int(seed), float(spr_scale), _f3(shift_mm))
+    rid = C.c_int64()
+    _check(_lib.dose_server_submit(server, C.byref(r), C.byref(rid)), None)
+    return rid.value
+
+
+def dose_server_step(server, stream=None, max_completed=4096):
+    ids = (C.c_int64 * max_completed)()
+    n = C.c_int()
+    _check(_lib.dose_server_step(server, _stream(stream), ids, max_completed, C.byref(n)), None)
+    return [int(ids[i]) for i in range(n.value)]
+
+
+def dose_server_result(server, rid, what, phase, dst, stream=None):
+    p, dev = _ptr(dst)
+    _check(_lib.dose_server_result(server, int(rid), int(what), int(phase), p, _nbytes(dst), dev,
+                                   _stream(stream)), None)
+    return dst
+
+
+def dose_server_release(server, rid):
+    _check(_lib.dose_server_release(server, int(rid)), None)
+
+
+def dose_server_stats(server):
+    out = (C.c_uint64 * 8)()
+    _check(_lib.dose_server_stats(server, out), None)
+    return dict(zip(("queued", "active", "slots", "completed", "histories", "steps", "slot_bytes",
+                     "unreleased"), [int(v) for v in out]))
+
+
+def dose_server_destroy(server):
+    _lib.dose_server_destroy(server)
 
 
 def dose_set_option(ctx, option, value):

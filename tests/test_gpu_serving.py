@@ -1,0 +1,115 @@
+"""Continuous-batching server: requests that arrive while others run are
+admitted at the next step and share launches; each result must be the same
+bits as the request served alone (histories are keyed by seed, history and
+phase, and slicing a run does not change its tally)."""
+import numpy as np
+import pytest
+
+from paper_1809_03927_gb300 import workloads as W
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+NSUB = (2, 2, 5)
+
+
+def _setup(D):
+    import torch
+    ph, dvf, geo = W.phantom_4dct(48, 48, 32, (1.0, 1.0, 2.5), n_phases=4, motion_pp=8.0)
+    plan = W.tumour_plan(geo, ph.origin, n_layers=3, per_layer=12, e_lo=70.0, e_hi=100.0)
+    dlv = D.delivery_struct(W.Delivery(n_phases=4, start_phase=-1, seed=21, period_ns=20_000_000,
+                                       spot_switch_ns=200_000, layer_switch_ns=3_000_000))
+    base = H.make_ctx(D, ph)
+    return ph, torch.from_numpy(dvf).cuda(), D.spots_array(plan), dlv, base
+
+
+REQUESTS = [  # (histories, seed, spr scale, shift)
+    (40_000, 1, 1.0, (0.0, 0.0, 0.0)),
+    (8_000, 2, 1.035, (0.0, 0.0, 0.0)),
+    (120_000, 3, 1.0, (3.0, 0.0, 0.0)),
+    (4_000, 4, 0.965, (0.0, -3.0, 0.0)),
+    (60_000, 5, 1.0, (0.0, 0.0, 3.0)),
+]
+
+
+def _serve(D, base, spots, dlv, dvf, arrivals, shape, **kw):
+    """Serve REQUESTS; request k is submitted before step arrivals[k]."""
+    srv = D.dose_server_create(base, 1 << 34, kw.get("step", 30_000), spots, dlv, min_slice=kw.get("min_slice", 50),
+                               max_active=kw.get("max_active", 0), nsub=NSUB, dvf=dvf)
+    out, ids, step, pending = {}, {}, 0, list(range(len(REQUESTS)))
+    try:
+        while len(out) < len(REQUESTS):
+            for k in list(pending):
+                if arrivals[k] <= step:
+                    n, seed, spr, sh = REQUESTS[k]
+                    ids[D.dose_server_submit(srv, n, seed, spr, sh)] = k
+                    pending.remove(k)
+            for rid in D.dose_server_step(srv):
+                acc = D.dose_server_result(srv, rid, D.DOSE_ACCUM, 0, np.zeros(shape, np.float32))
+                ph2 = D.dose_server_result(srv, rid, D.DOSE_PHASE_DOSE, 2, np.zeros(shape, np.float32))
+                out[ids[rid]] = (acc, ph2)
+                D.dose_server_release(srv, rid)
+            step += 1
+            assert step < 10_000
+        stats = D.dose_server_stats(srv)
+    finally:
+        D.dose_server_destroy(srv)
+    return out, stats
+
+
+def test_served_results_equal_alone(gpu):
+    D = gpu
+    ph, dvf, spots, dlv, base = _setup(D)
+    shape = ph.hu.shape[1:]
+    try:
+        mixed, stats = _serve(D, base, spots, dlv, dvf, [0, 1, 1, 3, 6], shape)
+        assert stats["completed"] == len(REQUESTS) and stats["queued"] == 0 and stats["active"] == 0
+        assert stats["steps"] > 3 and stats["slots"] >= 2
+        # each request alone: dose_run_4d with the server's even split over the phases
+        view = D.dose_create_view(base)
+        try:
+            D.dose_add_spots(view, spots, dlv)
+            for k, (n, seed, spr, sh) in enumerate(REQUESTS):
+                D.dose_run_4d(view, n // 4, seed, 0, NSUB, dvf=dvf, spr_scale=spr, shift_mm=sh)
+                acc = D.dose_read(view, D.DOSE_ACCUM, 0, np.zeros(shape, np.float32))
+                ph2 = D.dose_read(view, D.DOSE_PHASE_DOSE, 2, np.zeros(shape, np.float32))
+                np.testing.assert_array_equal(mixed[k][0], acc)
+                np.testing.assert_array_equal(mixed[k][1], ph2)
+        finally:
+            D.dose_destroy(view)
+    finally:
+        D.dose_destroy(base)
+
+
+def test_slot_cap_and_reuse(gpu):
+    """With one slot, requests run one at a time and reuse it; results are
+    unchanged."""
+    D = gpu
+    ph, dvf, spots, dlv, base = _setup(D)
+    shape = ph.hu.shape[1:]
+    try:
+        capped, stats = _serve(D, base, spots, dlv, dvf, [0] * len(REQUESTS), shape, max_active=1)
+        assert stats["slots"] == 1
+        free, _ = _serve(D, base, spots, dlv, dvf, [0] * len(REQUESTS), shape, step=1_000_000)
+        for k in range(len(REQUESTS)):
+            np.testing.assert_array_equal(capped[k][0], free[k][0])
+    finally:
+        D.dose_destroy(base)
+
+
+def test_server_rejects_bad_input(gpu):
+    D = gpu
+    ph, dvf, spots, dlv, base = _setup(D)
+    try:
+        with pytest.raises(D.DoseError):
+            D.dose_server_create(base, 1000, 30_000, spots, dlv, dvf=dvf)       # budget below one slot
+        srv = D.dose_server_create(base, 1 << 34, 30_000, spots, dlv, dvf=dvf)
+        try:
+            with pytest.raises(D.DoseError):
+                D.dose_server_submit(srv, 0, 1)
+            with pytest.raises(D.DoseError):
+                D.dose_server_result(srv, 12345, D.DOSE_ACCUM, 0, np.zeros(ph.hu.shape[1:], np.float32))
+        finally:
+            D.dose_server_destroy(srv)
+    finally:
+        D.dose_destroy(base)
