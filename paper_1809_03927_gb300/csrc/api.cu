@@ -593,6 +593,7 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
             t.spot = c->spot; t.wh = P.wh; t.prefix = P.prefix; t.n_spots = c->n_spots;
             t.nx = g.n[0]; t.ny = g.n[1]; t.nz = g.n[2];
             t.dx = g.d[0]; t.dy = g.d[1]; t.dz = g.d[2];
+            t.idx = 1.0f / g.d[0]; t.idy = 1.0f / g.d[1]; t.idz = 1.0f / g.d[2];
             const int a = g.beam_axis, b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
             t.ob = g.origin[b] + J.shift_mm[b];
             t.oc = g.origin[cc] + J.shift_mm[cc];
@@ -623,7 +624,7 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
     if (work) {
         CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
         CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
-        const size_t smem = kSmemTables;
+        const size_t smem = kSmemTransport;
         auto kern = c0->regs ? k_transport_r64 : k_transport;
         if (!c0->regs && c0->block > 512)
             return fail(c0, DOSE_EINVAL, "block %d needs the 64-register variant (DOSE_OPT_REGISTERS 1)", c0->block);
@@ -689,8 +690,8 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
     j.shift_mm[0] = j.shift_mm[1] = j.shift_mm[2] = 0.0f;
     c->blocks_per_sm = 0;
     // the occupancy query needs the kernels' dynamic shared-memory limit set
-    CK(c, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables));
-    CK(c, cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables));
+    CK(c, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransport));
+    CK(c, cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransport));
     // allocate the phase's histories once; each trial then only transports
     j.flags = DOSE_JOB_CLEAR; j.hist_begin = 0; j.hist_end = 0;
     if ((rc = dose_run_batch(&j, 1, stream))) goto done;
@@ -699,7 +700,7 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
             if (!regs && b > 512) continue;
             int fits = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, regs ? k_transport_r64 : k_transport, b,
-                                                              kSmemTables) != cudaSuccess || fits <= 0) {
+                                                              kSmemTransport) != cudaSuccess || fits <= 0) {
                 cudaGetLastError();
                 continue;
             }

@@ -61,6 +61,7 @@ struct TJob {
     int n_spots;
     int nx, ny, nz;
     float dx, dy, dz;
+    float idx, idy, idz;                // 1 / voxel sizes
     float ob, oc;                       // lateral patient->grid offsets (origin + shift)
     int beam_axis, beam_sign;
     float spr_scale;
@@ -70,6 +71,12 @@ struct TJob {
     unsigned long long hist_begin;      // first history of this slice
     unsigned long long work_begin;      // offset in the launch's work index
 };
+
+// A transport launch with at most kSmemJobs jobs stages their descriptors
+// and per-job counters (escaped, removed, steps, flags) in shared memory
+// after the tables; larger launches read them from global memory.
+constexpr int kSmemJobs = 32;
+constexpr size_t kSmemTransport = kSmemTables + kSmemJobs * sizeof(TJob) + kSmemJobs * 4 * sizeof(unsigned long long);
 
 struct AllocJob {
     const unsigned long long *protons;  // n_spots, this phase's subplan

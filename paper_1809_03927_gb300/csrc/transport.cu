@@ -165,24 +165,6 @@ __device__ __forceinline__ float highland_g(float u)
     return u * t * t;
 }
 
-// Per-lane running totals for the job the lane currently serves.
-// (Deposited energy is the sum of the tally, taken by k_normalise; the
-// incident energy and the history count follow from the allocation, taken
-// by k_alloc.)
-struct Ledger {
-    unsigned long long esc, rem;
-    unsigned steps;
-};
-
-__device__ __forceinline__ void flush_ledger(unsigned long long *led, Ledger &L)
-{
-    if (L.esc) atomicAdd(led + LED_ESC, L.esc);
-    if (L.rem) atomicAdd(led + LED_REM, L.rem);
-    if (L.steps) atomicAdd(led + LED_STEPS, (unsigned long long)L.steps);
-    L.esc = L.rem = 0;
-    L.steps = 0;
-}
-
 }  // namespace
 
 // Persistent kernel: every warp pulls `chunk` consecutive work items (one
@@ -199,16 +181,37 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                                                unsigned chunk)
 {
     extern __shared__ int4 smem[];
+    TJob *s_jobs = reinterpret_cast<TJob *>(reinterpret_cast<char *>(smem) + kSmemTables);
+    unsigned long long *s_led = reinterpret_cast<unsigned long long *>(
+        reinterpret_cast<char *>(smem) + kSmemTables + kSmemJobs * sizeof(TJob));
+    const bool staged = n_jobs <= kSmemJobs;
     {
         const int4 *src = reinterpret_cast<const int4 *>(gtab);
         for (int i = threadIdx.x; i < (int)(kSmemTables / 16); i += blockDim.x) smem[i] = src[i];
+        if (staged) {
+            const int words = n_jobs * (int)(sizeof(TJob) / 4);
+            const int *js = reinterpret_cast<const int *>(jobs);
+            int *jd = reinterpret_cast<int *>(s_jobs);
+            for (int i = threadIdx.x; i < words; i += blockDim.x) jd[i] = js[i];
+            for (int i = threadIdx.x; i < n_jobs * 4; i += blockDim.x) s_led[i] = 0ull;
+        }
     }
     __syncthreads();
     // re, hs, er from shared memory; mat (beyond the staged part) from global
     const Tables &T = *reinterpret_cast<const Tables *>(smem);
     const float2 *__restrict__ mat = gtab->mat;
+    // job descriptors: shared memory when staged, else global (generic loads)
+    const TJob *jt = staged ? s_jobs : jobs;
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+
+    // Per-job counters: escaped and removed energy, steps, flags.  Staged
+    // launches add them in shared memory and flush once per block.
+    auto led_add = [&](int j, int which, unsigned long long v) {
+        if (!v) return;
+        if (staged) atomicAdd(s_led + 4 * j + which, v);
+        else atomicAdd(jobs[j].ledger + (which == 0 ? LED_ESC : which == 1 ? LED_REM : LED_STEPS), v);
+    };
 
     // per-lane history state
     bool alive = false;
@@ -216,17 +219,9 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
     int ix = 0, iy = 0, iz = 0;
     unsigned step = 0;
     unsigned long long h = 0;
-    int job = -1;
-    Ledger L = {0, 0, 0};
+    int job = 0;
     int pend_vox = -1;
     unsigned long long pend_units = 0;
-
-    // job fields the step loop uses (refreshed when the lane changes job)
-    const int16_t *hu = nullptr;
-    unsigned long long *tally = nullptr;
-    int nx = 0, ny = 0, nz = 0;
-    float dx = 1, dy = 1, dz = 1, idx = 1, idy = 1, idz = 1, spr_scale = 1;
-    unsigned physics = 0, max_steps = 0, key0 = 0, key1 = 0, stream = 0;
 
     // warp-uniform queue state
     unsigned long long pool_next = 0, pool_end = 0;
@@ -251,56 +246,50 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                 int lo = 0, hi = n_jobs;
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
-                    if (jobs[mid].work_begin <= w) lo = mid; else hi = mid;
+                    if (jt[mid].work_begin <= w) lo = mid; else hi = mid;
                 }
-                const TJob &J = jobs[lo];
-                if (lo != job) {
-                    if (job >= 0) flush_ledger(jobs[job].ledger, L);
-                    if (pend_units) atomicAdd(tally + pend_vox, pend_units);
+                const TJob &J = jt[lo];
+                if (lo != job && pend_units) {
+                    atomicAdd(jt[job].tally + pend_vox, pend_units);
                     pend_units = 0;
                     pend_vox = -1;
-                    job = lo;
-                    hu = J.hu; tally = J.tally;
-                    nx = J.nx; ny = J.ny; nz = J.nz;
-                    dx = J.dx; dy = J.dy; dz = J.dz;
-                    idx = 1.0f / dx; idy = 1.0f / dy; idz = 1.0f / dz;
-                    spr_scale = J.spr_scale;
-                    physics = J.physics; max_steps = J.max_steps;
-                    key0 = J.key0; key1 = J.key1; stream = J.stream;
                 }
+                job = lo;
                 h = J.hist_begin + (w - J.work_begin);
                 const int S = J.n_spots;
-                if (h < J.prefix[S]) {
+                const unsigned long long *prefix = J.prefix;
+                if (h < prefix[S]) {
                     int a = 0, b = S;
                     while (b - a > 1) {
                         const int m = (a + b) >> 1;
-                        if (J.prefix[m] <= h) a = m; else b = m;
+                        if (prefix[m] <= h) a = m; else b = m;
                     }
                     const float4 sp = J.spot[a];
                     wh = J.wh[a];
                     E = sp.z;
                     const U6 u = uniforms6(philox4x32_10(
-                        make_uint4(0u, (unsigned)h, (unsigned)(h >> 32), stream), key0, key1));
+                        make_uint4(0u, (unsigned)h, (unsigned)(h >> 32), J.stream), J.key0, J.key1));
                     const float2 z = box_muller(u.u[0], u.u[1]);
                     eta = -__logf(u.u[2]);
-                    const unsigned long long e_units = to_units(E * wh);
                     const float lb = sp.x - J.ob + sp.w * z.x;
                     const float lc = sp.y - J.oc + sp.w * z.y;
                     const int ax = J.beam_axis, sg = J.beam_sign;
+                    const int nx = J.nx, ny = J.ny, nz = J.nz;
+                    const float dx = J.dx, dy = J.dy, dz = J.dz;
                     bool inside;
                     ux = uy = uz = 0.0f;
                     if (ax == 2) {
                         inside = lb >= 0.0f && lb < nx * dx && lc >= 0.0f && lc < ny * dy;
                         px = lb; py = lc; pz = sg > 0 ? 0.0f : nz * dz; uz = (float)sg;
-                        ix = (int)floorf(px * idx); iy = (int)floorf(py * idy); iz = sg > 0 ? 0 : nz - 1;
+                        ix = (int)floorf(px * J.idx); iy = (int)floorf(py * J.idy); iz = sg > 0 ? 0 : nz - 1;
                     } else if (ax == 1) {
                         inside = lb >= 0.0f && lb < nx * dx && lc >= 0.0f && lc < nz * dz;
                         px = lb; pz = lc; py = sg > 0 ? 0.0f : ny * dy; uy = (float)sg;
-                        ix = (int)floorf(px * idx); iz = (int)floorf(pz * idz); iy = sg > 0 ? 0 : ny - 1;
+                        ix = (int)floorf(px * J.idx); iz = (int)floorf(pz * J.idz); iy = sg > 0 ? 0 : ny - 1;
                     } else {
                         inside = lb >= 0.0f && lb < ny * dy && lc >= 0.0f && lc < nz * dz;
                         py = lb; pz = lc; px = sg > 0 ? 0.0f : nx * dx; ux = (float)sg;
-                        iy = (int)floorf(py * idy); iz = (int)floorf(pz * idz); ix = sg > 0 ? 0 : nx - 1;
+                        iy = (int)floorf(py * J.idy); iz = (int)floorf(pz * J.idz); ix = sg > 0 ? 0 : nx - 1;
                     }
                     // guard the floor against rounding at the far faces
                     ix = min(max(ix, 0), nx - 1); iy = min(max(iy, 0), ny - 1); iz = min(max(iz, 0), nz - 1);
@@ -308,7 +297,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                         uth = 0.0f; gth = 0.0f; step = 0;
                         alive = true;
                     } else {
-                        L.esc += e_units;
+                        led_add(job, 0, to_units(E * wh));
                     }
                 }
             }
@@ -319,31 +308,37 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         if (!alive) continue;
 
         // ---------------- one condensed-history step
-        if (step >= max_steps) {
-            L.esc += to_units(E * wh);
-            atomicOr(jobs[job].ledger + LED_FLAGS, (unsigned long long)FLAG_STEPLIMIT);
+        const TJob &J = jt[job];
+        if (step >= J.max_steps) {
+            led_add(job, 0, to_units(E * wh));
+            led_add(job, 2, step);
+            if (staged) atomicOr(s_led + 4 * job + 3, (unsigned long long)FLAG_STEPLIMIT);
+            else atomicOr(jobs[job].ledger + LED_FLAGS, (unsigned long long)FLAG_STEPLIMIT);
             alive = false;
             continue;
         }
-        L.steps += 1;
+        const int nx = J.nx, ny = J.ny;
         const int vox = (iz * ny + iy) * nx + ix;
-        const int hv = min(max((int)__ldg(hu + vox), kHuMin), kHuMax);
+        const int hv = min(max((int)__ldg(J.hu + vox), kHuMin), kHuMax);
         const float2 m = __ldg(mat + (hv - kHuMin));
         const float rho = m.x;
-        const float spr = m.y * spr_scale;
+        const float spr = m.y * J.spr_scale;
         const float inv_spr = __fdividef(1.0f, spr);
         const float2 re0 = lerp_e(T.re, E);
         const float R0 = re0.x;
+        ++step;
         if (R0 * inv_spr <= kSmin) {                   // residual range below s_min
             const unsigned long long eu = to_units(E * wh);
             if (vox != pend_vox) {
-                if (pend_units) atomicAdd(tally + pend_vox, pend_units);
+                if (pend_units) atomicAdd(J.tally + pend_vox, pend_units);
                 pend_vox = vox; pend_units = 0;
             }
             pend_units += eu;
+            led_add(job, 2, step);
             alive = false;
             continue;
         }
+        const float dx = J.dx, dy = J.dy, dz = J.dz;
         // distance to the faces of the current voxel (ties: lowest axis)
         const float inf = __int_as_float(0x7f800000);
         float tx = ux > 0.0f ? ((ix + 1) * dx - px) * __fdividef(1.0f, ux)
@@ -366,6 +361,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         float E1c = energy_at_range(T.er, R0 - sw, inv_ds);
         float Emean = 0.5f * (E + E1c);
         float2 hs = lerp_e(T.hs, Emean);
+        const unsigned physics = J.physics;
         bool nuclear = false;
         if (physics & 4u) {
             const float tau = hs.y * sw;
@@ -380,7 +376,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
             }
         }
         const U6 u = uniforms6(philox4x32_10(
-            make_uint4(step + 1u, (unsigned)h, (unsigned)(h >> 32), stream), key0, key1));
+            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), J.stream), J.key0, J.key1));
         float dE = E - E1c;
         if (physics & 1u) {
             // Bohr fluctuation, truncated symmetrically at the mean loss so
@@ -396,21 +392,22 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
             float local = E;                              // stop: dE + E1
             if (nuclear) {
                 local = dE + kFloc * E1;
-                L.rem += to_units((E1 - kFloc * E1) * wh);
+                led_add(job, 1, to_units((E1 - kFloc * E1) * wh));
             }
             const unsigned long long eu = to_units(local * wh);
             if (vox != pend_vox) {
-                if (pend_units) atomicAdd(tally + pend_vox, pend_units);
+                if (pend_units) atomicAdd(J.tally + pend_vox, pend_units);
                 pend_vox = vox; pend_units = 0;
             }
             pend_units += eu;
+            led_add(job, 2, step);
             alive = false;
             continue;
         }
         {
             const unsigned long long eu = to_units(dE * wh);
             if (vox != pend_vox) {
-                if (pend_units) atomicAdd(tally + pend_vox, pend_units);
+                if (pend_units) atomicAdd(J.tally + pend_vox, pend_units);
                 pend_vox = vox; pend_units = 0;
             }
             pend_units += eu;
@@ -447,7 +444,6 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         const float nrm = rsqrtf(ux * ux + uy * uy + uz * uz);
         ux *= nrm; uy *= nrm; uz *= nrm;
         E = E1;
-        ++step;
 
         // voxel update: the crossed axis steps by one and its coordinate is
         // put on the crossed face; every other axis keeps its index while the
@@ -456,25 +452,36 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         if (geom && across == 0) {
             if (ux0 > 0.0f) { ix += 1; px = ix * dx; } else { px = ix * dx; ix -= 1; }
         } else if (!(px >= ix * dx && px <= (ix + 1) * dx)) {
-            ix = (int)floorf(px * idx);
+            ix = (int)floorf(px * J.idx);
         }
         if (geom && across == 1) {
             if (uy0 > 0.0f) { iy += 1; py = iy * dy; } else { py = iy * dy; iy -= 1; }
         } else if (!(py >= iy * dy && py <= (iy + 1) * dy)) {
-            iy = (int)floorf(py * idy);
+            iy = (int)floorf(py * J.idy);
         }
         if (geom && across == 2) {
             if (uz0 > 0.0f) { iz += 1; pz = iz * dz; } else { pz = iz * dz; iz -= 1; }
         } else if (!(pz >= iz * dz && pz <= (iz + 1) * dz)) {
-            iz = (int)floorf(pz * idz);
+            iz = (int)floorf(pz * J.idz);
         }
-        if ((unsigned)ix >= (unsigned)nx || (unsigned)iy >= (unsigned)ny || (unsigned)iz >= (unsigned)nz) {
-            L.esc += to_units(E * wh);
+        if ((unsigned)ix >= (unsigned)nx || (unsigned)iy >= (unsigned)ny || (unsigned)iz >= (unsigned)J.nz) {
+            led_add(job, 0, to_units(E * wh));
+            led_add(job, 2, step);
             alive = false;
         }
     }
-    if (pend_units) atomicAdd(tally + pend_vox, pend_units);
-    if (job >= 0) flush_ledger(jobs[job].ledger, L);
+    if (pend_units) atomicAdd(jt[job].tally + pend_vox, pend_units);
+    if (staged) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_jobs * 4; i += blockDim.x) {
+            const unsigned long long v = s_led[i];
+            if (!v) continue;
+            const int j = i >> 2, which = i & 3;
+            unsigned long long *led = jobs[j].ledger;
+            if (which == 3) atomicOr(led + LED_FLAGS, v);
+            else atomicAdd(led + (which == 0 ? LED_ESC : which == 1 ? LED_REM : LED_STEPS), v);
+        }
+    }
 }
 
 // Two register budgets of the same kernel: up to 128 registers per thread
