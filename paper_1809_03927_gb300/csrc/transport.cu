@@ -14,6 +14,7 @@ namespace dose {
 
 namespace {
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRefillMin = 6;        // idle lanes that trigger a warp's refill
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 {
@@ -220,8 +221,6 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
     unsigned step = 0;
     unsigned long long h = 0;
     int job = 0;
-    int pend_vox = -1;
-    unsigned long long pend_units = 0;
 
     // warp-uniform queue state
     unsigned long long pool_next = 0, pool_end = 0;
@@ -229,7 +228,11 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
 
     for (;;) {
         // ---------------- refill idle lanes from the warp's chunk
+        // (a warp refills only once kRefillMin lanes are idle, or all are:
+        // the refill runs with the idle lanes only, so batching them
+        // amortises it over more histories)
         unsigned need = __ballot_sync(kFull, !alive);
+        if (__popc(need) < kRefillMin && need != kFull) need = 0;
         while (need && !queue_done) {
             if (pool_next >= pool_end) {
                 unsigned long long base = 0;
@@ -249,11 +252,6 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                     if (jt[mid].work_begin <= w) lo = mid; else hi = mid;
                 }
                 const TJob &J = jt[lo];
-                if (lo != job && pend_units) {
-                    atomicAdd(jt[job].tally + pend_vox, pend_units);
-                    pend_units = 0;
-                    pend_vox = -1;
-                }
                 job = lo;
                 h = J.hist_begin + (w - J.work_begin);
                 const int S = J.n_spots;
@@ -327,13 +325,13 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         const float2 re0 = lerp_e(T.re, E);
         const float R0 = re0.x;
         ++step;
+        // this step's random numbers: independent of the geometry below, so
+        // the generator's rounds can interleave with the table lookups
+        const U6 u = uniforms6(philox4x32_10(
+            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), J.stream), J.key0, J.key1));
         if (R0 * inv_spr <= kSmin) {                   // residual range below s_min
             const unsigned long long eu = to_units(E * wh);
-            if (vox != pend_vox) {
-                if (pend_units) atomicAdd(J.tally + pend_vox, pend_units);
-                pend_vox = vox; pend_units = 0;
-            }
-            pend_units += eu;
+            atomicAdd(J.tally + vox, eu);
             led_add(job, 2, step);
             alive = false;
             continue;
@@ -375,8 +373,6 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                 eta -= tau;
             }
         }
-        const U6 u = uniforms6(philox4x32_10(
-            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), J.stream), J.key0, J.key1));
         float dE = E - E1c;
         if (physics & 1u) {
             // Bohr fluctuation, truncated symmetrically at the mean loss so
@@ -395,22 +391,14 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                 led_add(job, 1, to_units((E1 - kFloc * E1) * wh));
             }
             const unsigned long long eu = to_units(local * wh);
-            if (vox != pend_vox) {
-                if (pend_units) atomicAdd(J.tally + pend_vox, pend_units);
-                pend_vox = vox; pend_units = 0;
-            }
-            pend_units += eu;
+            atomicAdd(J.tally + vox, eu);
             led_add(job, 2, step);
             alive = false;
             continue;
         }
         {
             const unsigned long long eu = to_units(dE * wh);
-            if (vox != pend_vox) {
-                if (pend_units) atomicAdd(J.tally + pend_vox, pend_units);
-                pend_vox = vox; pend_units = 0;
-            }
-            pend_units += eu;
+            atomicAdd(J.tally + vox, eu);
         }
 
         // multiple Coulomb scattering over the step (cumulative Highland)
@@ -470,7 +458,6 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
             alive = false;
         }
     }
-    if (pend_units) atomicAdd(jt[job].tally + pend_vox, pend_units);
     if (staged) {
         __syncthreads();
         for (int i = threadIdx.x; i < n_jobs * 4; i += blockDim.x) {
