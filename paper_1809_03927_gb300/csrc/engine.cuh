@@ -114,23 +114,24 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
 }
 
 // Six 21-bit uniforms (k + 1/2) 2^-21 from the 128 bits of a block, bits
-// [21 i, 21 i + 21) of the little-endian word concatenation.
+// [21 i, 21 i + 21) of the little-endian word concatenation.  Each value is
+// assembled exactly: k goes into the top of the mantissa of 1.0f with the
+// half-unit bit set, which reads 1 + (k + 1/2) 2^-21, and 1 is subtracted
+// (exact: the difference has at most 22 significant bits).
 struct U6 { float u[6]; };
+__device__ __forceinline__ float unit_from_bits(unsigned b)   // k in bits [2, 23)
+{
+    return __int_as_float((b & 0x007FFFFCu) | 0x3F800002u) - 1.0f;
+}
 __device__ __forceinline__ U6 uniforms6(uint4 w)
 {
-    const unsigned long long lo = (unsigned long long)w.x | ((unsigned long long)w.y << 32);
-    const unsigned long long hi = (unsigned long long)w.z | ((unsigned long long)w.w << 32);
-    const unsigned long long M = 0x1FFFFFull;
-    unsigned k[6];
-    k[0] = (unsigned)(lo & M);
-    k[1] = (unsigned)((lo >> 21) & M);
-    k[2] = (unsigned)((lo >> 42) & M);
-    k[3] = (unsigned)(((lo >> 63) | (hi << 1)) & M);
-    k[4] = (unsigned)((hi >> 20) & M);
-    k[5] = (unsigned)((hi >> 41) & M);
     U6 r;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) r.u[i] = __fmaf_rn((float)k[i], 4.76837158203125e-7f, 2.384185791015625e-7f);
+    r.u[0] = unit_from_bits(w.x << 2);                          // bits 0..20
+    r.u[1] = unit_from_bits(__funnelshift_r(w.x, w.y, 19));     // bits 21..41
+    r.u[2] = unit_from_bits(w.y >> 8);                          // bits 42..62
+    r.u[3] = unit_from_bits(__funnelshift_r(w.y, w.z, 29));     // bits 63..83
+    r.u[4] = unit_from_bits(__funnelshift_r(w.z, w.w, 18));     // bits 84..104
+    r.u[5] = unit_from_bits(w.w >> 7);                          // bits 105..125
     return r;
 }
 
@@ -145,7 +146,9 @@ __device__ __forceinline__ float fast_sqrt(float x)
 // cosine are accurate; cos(x + pi) = -cos x and sin(x + pi) = -sin x.
 __device__ __forceinline__ float2 box_muller(float ua, float ub)
 {
-    const float r = fast_sqrt(-2.0f * __logf(ua));
+    // ua is in (0, 1), so t > 0; the floor only keeps rsqrt finite
+    const float t = fmaxf(-2.0f * __logf(ua), 1e-30f);
+    const float r = t * rsqrtf(t);
     const float a = __fmaf_rn(6.28318530717958647f, ub, -3.14159265358979324f);
     float s, c;
     __sincosf(a, &s, &c);
@@ -155,7 +158,8 @@ __device__ __forceinline__ float2 box_muller(float ua, float ub)
 // First normal of the Box-Muller pair only.
 __device__ __forceinline__ float box_muller_first(float ua, float ub)
 {
-    const float r = fast_sqrt(-2.0f * __logf(ua));
+    const float t = fmaxf(-2.0f * __logf(ua), 1e-30f);
+    const float r = t * rsqrtf(t);
     const float a = __fmaf_rn(6.28318530717958647f, ub, -3.14159265358979324f);
     return -r * __cosf(a);
 }
@@ -175,8 +179,8 @@ __device__ __forceinline__ float highland_coeff(float pv)
 // Linear interpolation on the uniform energy grid.
 __device__ __forceinline__ float2 lerp_e(const float2 *t, float e)
 {
-    const float x = fminf(fmaxf(e * kInvDE, 0.0f), (float)kNE);
-    const int i = min((int)x, kNE - 1);
+    const float x = e * kInvDE;                      // e >= 0 on every call
+    const int i = (int)min((unsigned)(int)x, (unsigned)(kNE - 1));
     const float f = x - (float)i;
     const float2 a = t[i], b = t[i + 1];
     return make_float2(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y));
@@ -185,8 +189,8 @@ __device__ __forceinline__ float2 lerp_e(const float2 *t, float e)
 // Energy at a residual water range, linear on the sqrt(range) grid.
 __device__ __forceinline__ float energy_at_range(const float *er, float r, float inv_ds)
 {
-    const float x = fminf(fast_sqrt(r) * inv_ds, (float)kNR);
-    const int i = min((int)x, kNR - 1);
+    const float x = fast_sqrt(r) * inv_ds;
+    const int i = (int)min((unsigned)(int)x, (unsigned)(kNR - 1));
     const float f = x - (float)i;
     return fmaf(f, er[i + 1] - er[i], er[i]);
 }
