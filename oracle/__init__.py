@@ -108,6 +108,7 @@ def lib():
         L.or_normalise.argtypes = [C.c_int64, P, P, C.c_double, C.c_double, P]
         L.or_timeline.argtypes = [C.c_int64, P, P, P, C.POINTER(DeliveryC), P, P, P, C.c_int32]
         L.or_emtm.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P, P]
+        L.or_dim.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P]
         L.or_init_tables()
         _lib = L
     return _lib
@@ -348,3 +349,26 @@ def emtm(dose_phases, rho_phases, d, ref_phase, nsub, dvf=None, mask=None, retur
     if return_sums:
         return acc, es, ms, int(dropped[0])
     return acc, int(dropped[0])
+
+
+def dim(dose_phases, d, ref_phase, nsub, dvf=None, mask=None):
+    """Dose-interpolation accumulation (Eq. 3) onto ``ref_phase`` plus Eq. 2.
+
+    ``dose_phases``: float32 (P, nz, ny, nx) Gy; ``dvf`` float32
+    (P, 3, nz, ny, nx) mm, the displacement carrying a reference-phase point
+    to phase p, given at the reference voxel centres (None = identity);
+    ``mask`` uint8 (nz, ny, nx).  Returns the FP64 accumulated dose.
+    """
+    ds = np.ascontiguousarray(dose_phases, np.float32)
+    P_, nz, ny, nx = ds.shape
+    n = np.array([nx, ny, nz], np.int32)
+    dm = np.array(d, np.float32)
+    ns = np.array(nsub, np.int32)
+    dv = None if dvf is None else np.ascontiguousarray(dvf, np.float32)
+    mk = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+    acc = np.zeros((nz, ny, nx), np.float64)
+    rc = lib().or_dim(_ptr(n), _ptr(dm), P_, int(ref_phase), _ptr(ns), _ptr(ds), _ptr(dv), _ptr(mk),
+                      _ptr(acc))
+    if rc:
+        raise ValueError(f"or_dim failed: {rc}")
+    return acc
