@@ -189,6 +189,7 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
     nx, ny, nz = ph.n
     hu_dev = torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda()
     dvf_dev = torch.from_numpy(dvf).cuda()
+    pull_dev = torch.from_numpy(W.reference_to_phase_field(dvf)).cuda()
     del dvf
     ctx = D.dose_create_grid(nx, ny, nz, *ph.d, ph.origin, ph.n_phases, hu_dev, ph.beam_dir, stream)
     spots = D.spots_array(plan)
@@ -220,10 +221,26 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
         e1.record(stream)
         torch.cuda.synchronize()
         emtm_s = e0.elapsed_time(e1) / 1e3
+        stats = D.dose_read(ctx, D.DOSE_EMTM_STATS, 0, np.zeros(4, np.uint64))
+        # both accumulation methods against the subvoxel count (the paper's
+        # study of n): EMTM pushes with the phase->reference field, DIM
+        # pulls with the reference->phase field
+        study = {}
+        for name, method, field in (("emtm", D.ACCUM_EMTM, dvf_dev), ("dim", D.ACCUM_DIM, pull_dev)):
+            study[name] = {}
+            for nsub in ((1, 1, 1), (2, 2, 2), (2, 2, 5), (4, 4, 4)):
+                ts = []
+                for _ in range(2):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    D.dose_accumulate_subvoxel(ctx, 0, nsub, dvf=field, method=method, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+                study[name]["x".join(map(str, nsub))] = min(ts)
         steps = sum(int(D.dose_read(ctx, D.DOSE_ENERGY_LEDGER, p, np.zeros(8, np.uint64))[4])
                     for p in range(ph.n_phases) if phase_p[p] > 0)
         n_run = int(np.count_nonzero(phase_p)) * n_per_phase
-        stats = D.dose_read(ctx, D.DOSE_EMTM_STATS, 0, np.zeros(4, np.uint64))
     finally:
         D.dose_destroy(ctx)
     s_plan = float(np.median(walls))
@@ -231,6 +248,7 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
             "histories_per_plan": n_run, "histories_per_s": n_run / s_plan,
             "steps_per_history": steps / n_run, "emtm_s": emtm_s,
             "emtm_subvoxels": int(stats[0]), "emtm_atomic_pairs": int(stats[2]),
+            "dim_s": study["dim"]["2x2x5"], "accumulation_s_by_subvoxels": study,
             "workload": "synthetic 4DCT 10 x 256x256x160 at 1x1x2.5 mm, 3000 spots / 20 layers 70-180 MeV, "
                         f"{n_per_phase:.0e} histories per phase, EMTM 2x2x5 onto phase 0",
             "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}}
@@ -340,6 +358,7 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
     nx, ny, nz = ph.n
     hu_dev = torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda()
     dvf_dev = torch.from_numpy(dvf).cuda()
+    pull_dev = torch.from_numpy(W.reference_to_phase_field(dvf)).cuda()
     del dvf
     reqs = _requests(window_s, rate)
     base = D.dose_create_grid(nx, ny, nz, *ph.d, ph.origin, ph.n_phases, hu_dev, ph.beam_dir, stream)

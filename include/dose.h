@@ -251,8 +251,17 @@ int dose_set_phase_dose(dose_ctx *c, int phase, const float *dose, int dose_on_d
  * D_i = D_i^R + sum_S D_i^S (Eq. 2), zero where mask == 0.
  * dvf: float32[n_phases * 3 * nvox] mm, the displacement carrying a point
  * of phase S to the reference (component-major per phase); NULL = identity.
- * mask: uint8[nvox] or NULL (all ones).  method 1 (DIM, Eq. 3) is not
- * provided and returns DOSE_EINVAL.  Every phase must have a dose.         */
+ * mask: uint8[nvox] or NULL (all ones).
+ * method 1 is the dose-interpolation method of Eq. 3: every voxel i of the
+ * reference phase is split into nsub subvoxels whose centres are carried to
+ * each source phase S by the reference-to-S displacement, the dose of S is
+ * interpolated trilinearly (between voxel centres, clamped at the edges) at
+ * each carried point, and D_i^S is the mean over the subvoxels; then Eq. 2
+ * and the mask as above.  For method 1, dvf holds for each phase S the
+ * displacement (mm) carrying a reference point to S, given at the reference
+ * voxel centres -- the opposite direction to method 0, as the paper notes.
+ * Every phase must have a dose.  DOSE_EMTM_STATS is only readable after
+ * method 0.                                                                */
 int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], const float *dvf,
                              int dvf_on_device, const uint8_t *mask, int mask_on_device,
                              int method, void *stream);

@@ -89,6 +89,7 @@ struct dose_ctx {
     unsigned long long *emtm_stats = nullptr;
     float *accum = nullptr;
     bool have_accum = false;
+    int accum_method = 0;              // method of the last accumulation
     TJob *d_jobs = nullptr;
     int cap_jobs = 0;
     AllocJob *d_alloc = nullptr;
@@ -793,7 +794,7 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
                              void *stream)
 {
     if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
-    if (method != 0) return fail(c, DOSE_EINVAL, "only method 0 (energy/mass transfer) is provided");
+    if (method != 0 && method != 1) return fail(c, DOSE_EINVAL, "method must be 0 (EMTM) or 1 (DIM)");
     const Grid &g = *c->g;
     if (ref_phase < 0 || ref_phase >= g.n_phases) return fail(c, DOSE_EINVAL, "ref_phase out of range");
     if (!nsub || nsub[0] < 1 || nsub[1] < 1 || nsub[2] < 1 || nsub[0] > 64 || nsub[1] > 64 || nsub[2] > 64)
@@ -803,9 +804,10 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
     int rc;
     if ((rc = use_device(c))) return rc;
     const size_t nvox = (size_t)g.nvox, P = (size_t)g.n_phases;
-    if (!c->em) {
+    if (!c->accum && (rc = dalloc_t(c, &c->accum, nvox))) return rc;
+    if (method == 0 && !c->em) {
         if ((rc = dalloc_t(c, &c->em, 2 * P * nvox)) || (rc = dalloc_t(c, &c->maxbits, P)) ||
-            (rc = dalloc_t(c, &c->emtm_stats, 4)) || (rc = dalloc_t(c, &c->accum, nvox)))
+            (rc = dalloc_t(c, &c->emtm_stats, 4)))
             return rc;
     }
     cudaStream_t st = S(stream);
@@ -820,6 +822,19 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
         if (!c->mask_buf && (rc = dalloc_t(c, &c->mask_buf, nvox))) return rc;
         CK(c, cudaMemcpyAsync(c->mask_buf, mask, nvox, cudaMemcpyHostToDevice, st));
         mask_dev = c->mask_buf;
+    }
+    if (method == 1) {
+        DimArgs a;
+        a.dose = c->dose_all; a.dvf = dvf_dev; a.mask = mask_dev; a.accum = c->accum;
+        a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
+        a.idx = 1.0f / g.d[0]; a.idy = 1.0f / g.d[1]; a.idz = 1.0f / g.d[2];
+        a.nsx = nsub[0]; a.nsy = nsub[1]; a.nsz = nsub[2];
+        a.ref = ref_phase; a.n_phases = (int)P;
+        k_dim<<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(a);
+        CK(c, cudaGetLastError());
+        c->have_accum = true;
+        c->accum_method = 1;
+        return DOSE_OK;
     }
     CK(c, cudaMemsetAsync(c->em, 0, 2 * P * nvox * sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(c->maxbits, 0, P * sizeof(unsigned), st));
@@ -839,6 +854,7 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
     k_emtm_sum<<<1216, 256, 0, st>>>(a);
     CK(c, cudaGetLastError());
     c->have_accum = true;
+    c->accum_method = 0;
     return DOSE_OK;
 }
 
@@ -883,7 +899,7 @@ int dose_read(dose_ctx *c, int what, int phase, void *dst, size_t bytes, int dst
         if (!c->have_plan) return fail(c, DOSE_ESTATE, "no plan");
         src = c->field_end; need = c->n_fields * sizeof(int64_t); break;
     case DOSE_EMTM_STATS:
-        if (!c->have_accum) return fail(c, DOSE_ESTATE, "no accumulated dose");
+        if (!c->have_accum || c->accum_method != 0) return fail(c, DOSE_ESTATE, "no energy/mass-transfer accumulation");
         src = c->emtm_stats; need = 4 * sizeof(unsigned long long); break;
     case DOSE_HIST_PREFIX:
         if (!phase_ok()) return fail(c, DOSE_EINVAL, "phase out of range");

@@ -61,4 +61,16 @@ __global__ void k_emtm_max(EmtmArgs a);
 __global__ void k_emtm(EmtmArgs a);
 __global__ void k_emtm_sum(EmtmArgs a);
 
+struct DimArgs {
+    const float *dose;               // n_phases x nvox
+    const float *dvf;                // n_phases x 3 x nvox (reference -> phase, mm), or null
+    const uint8_t *mask;             // nvox or null
+    float *accum;                    // nvox
+    int nx, ny, nz;
+    float idx, idy, idz;             // 1 / voxel sizes (mm -> voxels)
+    int nsx, nsy, nsz;
+    int ref, n_phases;
+};
+__global__ void k_dim(DimArgs a);
+
 }  // namespace dose

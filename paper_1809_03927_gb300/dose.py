@@ -237,7 +237,13 @@ def dose_set_phase_dose(ctx, phase, dose, stream=None):
     _check(_lib.dose_set_phase_dose(ctx, int(phase), p, dev, _stream(stream)), ctx)
 
 
-def dose_accumulate_subvoxel(ctx, ref_phase, nsub, dvf=None, mask=None, method=0, stream=None):
+ACCUM_EMTM = 0      # energy/mass transfer, Eqs. 4-6 (dvf: phase -> reference)
+ACCUM_DIM = 1       # dose interpolation, Eq. 3 (dvf: reference -> phase)
+
+
+def dose_accumulate_subvoxel(ctx, ref_phase, nsub, dvf=None, mask=None, method=ACCUM_EMTM, stream=None):
+    """Accumulate every phase's dose onto ``ref_phase`` (Eq. 2) by ``method``;
+    ``dvf`` float32 (P, 3, nz, ny, nx) mm in the direction the method needs."""
     ns = (C.c_int * 3)(*[int(v) for v in nsub])
     if dvf is not None and not _is_torch(dvf):
         dvf = np.ascontiguousarray(dvf, dtype=np.float32)

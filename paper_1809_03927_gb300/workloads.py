@@ -236,6 +236,17 @@ def phantom_4dct(nx=256, ny=256, nz=160, d=(1.0, 1.0, 2.5), n_phases=10,
     return ph, dvf, geo
 
 
+def reference_to_phase_field(dvf):
+    """The dose-interpolation method pulls dose and needs the field in the
+    other direction from the one ``phantom_4dct`` returns: the displacement
+    carrying a phase-0 (reference) point to phase p, given at the reference
+    voxel centres.  The breathing model moves points along z by the same
+    weight map m(r) in both images, so that field is the negated one (like
+    the fields of a registration run in each direction, the two are not
+    exact inverses where m varies)."""
+    return None if dvf is None else (-dvf).astype(np.float32)
+
+
 def tumour_plan(geo: Geometry4D, origin, seed=3, n_layers=20, per_layer=150,
                 e_lo=70.0, e_hi=180.0, pitch=5.0, sigma=4.0, w_lo=0.5e6, w_hi=1.5e6):
     """AP plan over the tumour and its motion: on each of ``n_layers`` layers
