@@ -109,6 +109,7 @@ def lib():
         L.or_timeline.argtypes = [C.c_int64, P, P, P, C.POINTER(DeliveryC), P, P, P, C.c_int32]
         L.or_emtm.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P, P]
         L.or_dim.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P]
+        L.or_dvf_decode.argtypes = [P] * 13
         L.or_init_tables()
         _lib = L
     return _lib
@@ -372,3 +373,30 @@ def dim(dose_phases, d, ref_phase, nsub, dvf=None, mask=None):
     if rc:
         raise ValueError(f"or_dim failed: {rc}")
     return acc
+
+
+def dvf_decode(grid, delta, n, d, origin):
+    """Decode a registration's vector grid (App. B, Eqs. 7-8) onto a CT grid.
+
+    ``grid``: dict with ``n`` (N_X, N_Y, N_Z), ``start_mm`` (centre of grid
+    voxel 0), ``spacing_mm``, ``row_cos`` (U), ``col_cos`` (V) and optional
+    ``pre``/``post`` row-major 4x4 rigid transforms; ``delta`` float32
+    (N_Z, N_Y, N_X, 3) mm; the CT grid is ``n`` = (nx, ny, nz) voxels of
+    size ``d`` with corner ``origin``.  Returns the FP64 displacement
+    (3, nz, ny, nx) in mm and the uint8 inside mask (nz, ny, nx).
+    """
+    f32 = lambda v: np.ascontiguousarray(np.asarray(v, np.float32).ravel())
+    eye = np.eye(4, dtype=np.float32)
+    gn = np.array(grid["n"], np.int32)
+    args = [gn, f32(grid["start_mm"]), f32(grid["spacing_mm"]), f32(grid["row_cos"]), f32(grid["col_cos"]),
+            f32(grid.get("pre", eye)), f32(grid.get("post", eye))]
+    dl = np.ascontiguousarray(delta, np.float32)
+    assert dl.shape == (gn[2], gn[1], gn[0], 3), dl.shape
+    nx, ny, nz = (int(v) for v in n)
+    disp = np.zeros((3, nz, ny, nx), np.float64)
+    inside = np.zeros((nz, ny, nx), np.uint8)
+    args += [dl, np.array(n, np.int32), f32(d), f32(origin), disp, inside]   # kept alive for the call
+    rc = lib().or_dvf_decode(*[_ptr(a) for a in args])
+    if rc:
+        raise ValueError(f"or_dvf_decode failed: {rc}")
+    return disp, inside

@@ -41,6 +41,12 @@
  *   or_emtm            Sec. 2.D.2, Eqs. 2, 4-6.  Pinned: identity-DVF test
  *                      of Sec. 2.E, integer translation, mass conservation,
  *                      brute force.
+ *   or_dvf_decode      App. B, Eqs. 7-8, and the DICOM rule that positions
+ *                      between grid voxels interpolate trilinearly.  Pinned:
+ *                      uniform and affine translations (exact under
+ *                      trilinear interpolation), rotated grid axes, the
+ *                      depth axis W = U x V, rigid pre/post transforms, the
+ *                      grid-hull mask.
  *   or_dim             Sec. 2.D.2, Eqs. 2-3.  Pinned: identity at n = 1,
  *                      exactness of trilinear interpolation on linear dose
  *                      and displacement fields, the interpolation error of a
@@ -1162,5 +1168,122 @@ int or_dim(const int32_t n[3], const float dmm[3], int32_t n_phases, int32_t ref
     }
     if (mask)
         for (size_t i = 0; i < nvox; ++i) if (!mask[i]) accum[i] = 0.0;
+    return OR_OK;
+}
+
+/* ======================================================================= */
+/* Decoding a registration's vector grid (App. B, Eqs. 7-8) onto the CT     */
+/* grid.                                                                    */
+/*                                                                          */
+/* Grid voxel (i, j, k) sits at r0 = start + i dX U + j dY V + k dZ W with  */
+/* W = U x V (Eq. 8) and maps to r_f = M_post (M_pre r0 + Delta_ijk)        */
+/* (Eq. 7).  A point between grid voxels maps to the trilinear interpolant  */
+/* of the r_f of the eight around it.  For each CT voxel centre p (patient  */
+/* frame: origin + (idx + 1/2) d) the continuous grid index is              */
+/* (U.(p - start)/dX, V.(p - start)/dY, W.(p - start)/dZ); the voxel is     */
+/* inside when every component lies in [0, N - 1], and then its             */
+/* displacement is r_f(p) - p; outside, the displacement is 0 and the       */
+/* voxel is left out of the mask (Sec. 2.D.2: dose is reported only where   */
+/* every DVF is defined).                                                   */
+/*                                                                          */
+/* Inside-ness is an integer decided by floating point: the continuous     */
+/* index is formed in single precision in the order written below, the     */
+/* precision and order of the GPU kernel.  Positions and interpolation are  */
+/* FP64.  pre, post: row-major 4 x 4.  delta: (Dx, Dy, Dz) per grid voxel,  */
+/* x fastest.                                                               */
+/* ======================================================================= */
+static void or_affine(const float *M, const double v[3], double out[3])
+{
+    for (int r = 0; r < 3; ++r)
+        out[r] = (double)M[4 * r + 0] * v[0] + (double)M[4 * r + 1] * v[1] +
+                 (double)M[4 * r + 2] * v[2] + (double)M[4 * r + 3];
+}
+
+static float or_f_mul(float a, float b) { volatile float r = a * b; return r; }
+static float or_f_add(float a, float b) { volatile float r = a + b; return r; }
+static float or_f_sub(float a, float b) { volatile float r = a - b; return r; }
+static float or_f_div(float a, float b) { volatile float r = a / b; return r; }
+
+int or_dvf_decode(const int32_t gn[3], const float gstart[3], const float gsp[3],
+                  const float U[3], const float V[3], const float pre[16],
+                  const float post[16], const float *delta, const int32_t n[3],
+                  const float d[3], const float origin[3], double *disp, uint8_t *inside)
+{
+    if (gn[0] <= 0 || gn[1] <= 0 || gn[2] <= 0 || !(gsp[0] > 0) || !(gsp[1] > 0) ||
+        !(gsp[2] > 0))
+        return OR_EINVAL;
+    const size_t ng = (size_t)gn[0] * gn[1] * gn[2];
+    const size_t nvox = (size_t)n[0] * n[1] * n[2];
+    double *rf = (double *)malloc(3 * ng * sizeof(double));
+    if (!rf) return OR_ENOMEM;
+    /* depth direction W = U x V (FP64 for positions, FP32 for the decision) */
+    const double Wd[3] = { (double)U[1] * V[2] - (double)U[2] * V[1],
+                           (double)U[2] * V[0] - (double)U[0] * V[2],
+                           (double)U[0] * V[1] - (double)U[1] * V[0] };
+    const float Wf[3] = { or_f_sub(or_f_mul(U[1], V[2]), or_f_mul(U[2], V[1])),
+                          or_f_sub(or_f_mul(U[2], V[0]), or_f_mul(U[0], V[2])),
+                          or_f_sub(or_f_mul(U[0], V[1]), or_f_mul(U[1], V[0])) };
+    for (int32_t k = 0; k < gn[2]; ++k)
+    for (int32_t j = 0; j < gn[1]; ++j)
+    for (int32_t i = 0; i < gn[0]; ++i) {
+        size_t g = ((size_t)k * gn[1] + j) * gn[0] + i;
+        double r0[3], a[3], b[3];
+        for (int c = 0; c < 3; ++c)           /* Eq. 8 */
+            r0[c] = (double)gstart[c] + (double)i * gsp[0] * U[c] + (double)j * gsp[1] * V[c] +
+                    (double)k * gsp[2] * Wd[c];
+        or_affine(pre, r0, a);                /* Eq. 7 */
+        for (int c = 0; c < 3; ++c) a[c] += (double)delta[3 * g + c];
+        or_affine(post, a, b);
+        for (int c = 0; c < 3; ++c) rf[c * ng + g] = b[c];
+    }
+    const float *axes[3] = { U, V, Wf };
+    for (int32_t iz = 0; iz < n[2]; ++iz)
+    for (int32_t iy = 0; iy < n[1]; ++iy)
+    for (int32_t ix = 0; ix < n[0]; ++ix) {
+        size_t v = ((size_t)iz * n[1] + iy) * n[0] + ix;
+        int32_t ii[3] = { ix, iy, iz };
+        float rel[3];
+        double p[3];
+        for (int c = 0; c < 3; ++c) {
+            float pc = or_f_add(origin[c], or_f_mul(or_f_add((float)ii[c], 0.5f), d[c]));
+            rel[c] = or_f_sub(pc, gstart[c]);
+            p[c] = (double)origin[c] + ((double)ii[c] + 0.5) * (double)d[c];
+        }
+        float q[3];
+        int in = 1;
+        for (int a = 0; a < 3; ++a) {
+            const float *ax = axes[a];
+            float dot = or_f_add(or_f_add(or_f_mul(ax[0], rel[0]), or_f_mul(ax[1], rel[1])),
+                                 or_f_mul(ax[2], rel[2]));
+            q[a] = or_f_div(dot, gsp[a]);
+            if (!(q[a] >= 0.0f && q[a] <= (float)(gn[a] - 1))) in = 0;
+        }
+        inside[v] = (uint8_t)in;
+        if (!in) {
+            for (int c = 0; c < 3; ++c) disp[c * nvox + v] = 0.0;
+            continue;
+        }
+        int32_t lo[3], hi[3];
+        double f[3];
+        for (int a = 0; a < 3; ++a) {
+            double fl = floor((double)q[a]);
+            f[a] = (double)q[a] - fl;
+            lo[a] = (int32_t)fl;
+            hi[a] = lo[a] + 1 > gn[a] - 1 ? gn[a] - 1 : lo[a] + 1;
+        }
+        for (int c = 0; c < 3; ++c) {
+            double val = 0.0;
+            for (int corner = 0; corner < 8; ++corner) {
+                int32_t x = (corner & 1) ? hi[0] : lo[0];
+                int32_t y = (corner & 2) ? hi[1] : lo[1];
+                int32_t z = (corner & 4) ? hi[2] : lo[2];
+                double w = ((corner & 1) ? f[0] : 1.0 - f[0]) * ((corner & 2) ? f[1] : 1.0 - f[1]) *
+                           ((corner & 4) ? f[2] : 1.0 - f[2]);
+                val += w * rf[c * ng + ((size_t)z * gn[1] + y) * gn[0] + x];
+            }
+            disp[c * nvox + v] = val - p[c];
+        }
+    }
+    free(rf);
     return OR_OK;
 }
