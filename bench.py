@@ -190,6 +190,12 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
     hu_dev = torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda()
     dvf_dev = torch.from_numpy(dvf).cuda()
     pull_dev = torch.from_numpy(W.reference_to_phase_field(dvf)).cuda()
+    # the registrations as a DIR system would store them: each phase's
+    # field on a grid of every other CT voxel centre (2 x 2 x 5 mm)
+    reg_grid = dict(n=(nx // 2, ny // 2, nz // 2), start_mm=tuple(ph.origin[k] + 0.5 * ph.d[k] for k in range(3)),
+                    spacing_mm=tuple(2.0 * v for v in ph.d), row_cos=(1, 0, 0), col_cos=(0, 1, 0))
+    reg_delta = [torch.from_numpy(np.ascontiguousarray(np.moveaxis(dvf[p][:, ::2, ::2, ::2], 0, -1))).cuda()
+                 for p in range(ph.n_phases)]
     del dvf
     ctx = D.dose_create_grid(nx, ny, nz, *ph.d, ph.origin, ph.n_phases, hu_dev, ph.beam_dir, stream)
     spots = D.spots_array(plan)
@@ -238,6 +244,23 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
                     torch.cuda.synchronize()
                     ts.append(e0.elapsed_time(e1) / 1e3)
                 study[name]["x".join(map(str, nsub))] = min(ts)
+        # decoding every phase's registration onto the CT grid (App. B)
+        nvox = nx * ny * nz
+        decoded = torch.empty(ph.n_phases * 3 * nvox, dtype=torch.float32, device="cuda")
+        dmask = torch.empty(nvox, dtype=torch.uint8, device="cuda")
+        ts = []
+        for _ in range(3):
+            dmask.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for p in range(1, ph.n_phases):
+                D.dose_decode_dvf(ctx, reg_grid, reg_delta[p], decoded[p * 3 * nvox:(p + 1) * 3 * nvox],
+                                  mask=dmask, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        decode_s = min(ts)
+        del decoded, dmask
         steps = sum(int(D.dose_read(ctx, D.DOSE_ENERGY_LEDGER, p, np.zeros(8, np.uint64))[4])
                     for p in range(ph.n_phases) if phase_p[p] > 0)
         n_run = int(np.count_nonzero(phase_p)) * n_per_phase
@@ -249,6 +272,9 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
             "steps_per_history": steps / n_run, "emtm_s": emtm_s,
             "emtm_subvoxels": int(stats[0]), "emtm_atomic_pairs": int(stats[2]),
             "dim_s": study["dim"]["2x2x5"], "accumulation_s_by_subvoxels": study,
+            "dvf_decode_s": decode_s,
+            "dvf_decode": f"{ph.n_phases - 1} registrations on {nx // 2}x{ny // 2}x{nz // 2} grids "
+                          "(every other CT voxel centre) decoded onto the CT grid with the report mask",
             "workload": "synthetic 4DCT 10 x 256x256x160 at 1x1x2.5 mm, 3000 spots / 20 layers 70-180 MeV, "
                         f"{n_per_phase:.0e} histories per phase, EMTM 2x2x5 onto phase 0",
             "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}}
@@ -359,6 +385,12 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
     hu_dev = torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda()
     dvf_dev = torch.from_numpy(dvf).cuda()
     pull_dev = torch.from_numpy(W.reference_to_phase_field(dvf)).cuda()
+    # the registrations as a DIR system would store them: each phase's
+    # field on a grid of every other CT voxel centre (2 x 2 x 5 mm)
+    reg_grid = dict(n=(nx // 2, ny // 2, nz // 2), start_mm=tuple(ph.origin[k] + 0.5 * ph.d[k] for k in range(3)),
+                    spacing_mm=tuple(2.0 * v for v in ph.d), row_cos=(1, 0, 0), col_cos=(0, 1, 0))
+    reg_delta = [torch.from_numpy(np.ascontiguousarray(np.moveaxis(dvf[p][:, ::2, ::2, ::2], 0, -1))).cuda()
+                 for p in range(ph.n_phases)]
     del dvf
     reqs = _requests(window_s, rate)
     base = D.dose_create_grid(nx, ny, nz, *ph.d, ph.origin, ph.n_phases, hu_dev, ph.beam_dir, stream)

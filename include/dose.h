@@ -241,6 +241,41 @@ void dose_server_destroy(dose_server *s);
 int dose_set_phase_dose(dose_ctx *c, int phase, const float *dose, int dose_on_device,
                         void *stream);
 
+/* A deformable registration's vector grid as DICOM stores it (App. B):
+ * N_X x N_Y x N_Z grid voxels, the patient-frame centre of voxel (0,0,0),
+ * the spacings dX, dY, dZ, the row (U) and column (V) direction cosines
+ * (orthonormal; the depth direction is W = U x V) and the rigid transforms
+ * applied before and after the deformation (row-major 4 x 4; the identity
+ * between 4DCT phases).                                                   */
+typedef struct dose_dvf_grid {
+    int32_t n[3];
+    float start_mm[3];
+    float spacing_mm[3];
+    float row_cos[3];
+    float col_cos[3];
+    float pre[16];
+    float post[16];
+} dose_dvf_grid;
+
+/* Decode a registration onto this context's CT grid (App. B, Eqs. 7-8):
+ * grid voxel (i, j, k) sits at r0 = start + i dX U + j dY V + k dZ W
+ * (Eq. 8) and maps to r_f = M_post (M_pre r0 + Delta_ijk) (Eq. 7); a point
+ * between grid voxels maps to the trilinear interpolant of the r_f around
+ * it (the DICOM rule the paper quotes).  Every CT voxel centre p = origin +
+ * (i + 1/2) d inside the hull of grid voxel centres gets the displacement
+ * r_f(p) - p in dvf_out; outside it gets 0, and mask_inout (if not NULL) is
+ * cleared there, so decoding every phase's registration into one mask
+ * leaves the region all of them cover (the report mask of Sec. 2.D.2).
+ * translation: float32[N_Z][N_Y][N_X][3] mm (x fastest, components
+ * interleaved), host or device.  dvf_out: device float32[3 * nvox] (x, y,
+ * z component planes: one phase's block of the dvf argument below).
+ * mask_inout: device uint8[nvox] or NULL.  The inside test is taken in
+ * single precision in a fixed order, so it is reproducible bit for bit.
+ * Errors: DOSE_EINVAL for a non-positive size or spacing, direction cosines
+ * that are not orthonormal (1e-4) or outputs that are not device memory.  */
+int dose_decode_dvf(dose_ctx *c, const dose_dvf_grid *grid, const float *translation,
+                    int translation_on_device, float *dvf_out, uint8_t *mask_inout, void *stream);
+
 /* Accumulate the phase doses onto ref_phase (Sec. 2.D.2).  method 0 is the
  * energy/mass-transfer method of Eqs. 4-6: every voxel of each source phase
  * S != ref_phase is split into nsub[0] x nsub[1] x nsub[2] subvoxels whose

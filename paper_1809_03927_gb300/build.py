@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(PKG, "lib")
 OBJ_DIR = os.path.join(PKG, "lib", "obj")
 LIB = os.path.join(OUT_DIR, "libdose.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "transport.cu", "timeline.cu", "emtm.cu", "dim.cu", "lut.cpp", "noalloc.cu", "serve.cpp"]
+SOURCES = ["api.cu", "transport.cu", "timeline.cu", "emtm.cu", "dim.cu", "dvf.cu", "lut.cpp", "noalloc.cu", "serve.cpp"]
 
 
 def nvcc() -> str:

@@ -85,6 +85,9 @@ struct dose_ctx {
     unsigned long long *em = nullptr;        // E then M, n_phases x nvox each
     float *dvf_buf = nullptr;                // staging for host DVFs
     uint8_t *mask_buf = nullptr;             // staging for a host mask
+    float *dvfgrid_e = nullptr;              // decoded registration grid (r_f - r0), 3 x cap
+    float *dvfgrid_delta = nullptr;          // staging for host translations, 3 x cap
+    size_t dvfgrid_cap = 0;                  // grid voxels the two buffers hold
     unsigned *maxbits = nullptr;
     unsigned long long *emtm_stats = nullptr;
     float *accum = nullptr;
@@ -855,6 +858,76 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
     CK(c, cudaGetLastError());
     c->have_accum = true;
     c->accum_method = 0;
+    return DOSE_OK;
+}
+
+int dose_decode_dvf(dose_ctx *c, const dose_dvf_grid *grid, const float *translation,
+                    int translation_on_device, float *dvf_out, uint8_t *mask_inout, void *stream)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (!grid || !translation || !dvf_out) return fail(c, DOSE_EINVAL, "grid, translation and dvf_out are required");
+    const dose_dvf_grid &G = *grid;
+    for (int k = 0; k < 3; ++k) {
+        if (G.n[k] < 1) return fail(c, DOSE_EINVAL, "grid size must be positive");
+        if (!(G.spacing_mm[k] > 0.0f)) return fail(c, DOSE_EINVAL, "grid spacing must be positive");
+    }
+    double uu = 0, vv = 0, uv = 0;
+    for (int k = 0; k < 3; ++k) {
+        uu += (double)G.row_cos[k] * G.row_cos[k];
+        vv += (double)G.col_cos[k] * G.col_cos[k];
+        uv += (double)G.row_cos[k] * G.col_cos[k];
+    }
+    if (std::fabs(uu - 1.0) > 1e-4 || std::fabs(vv - 1.0) > 1e-4 || std::fabs(uv) > 1e-4)
+        return fail(c, DOSE_EINVAL, "row and column direction cosines must be orthonormal");
+    for (void *ptr : {(void *)dvf_out, (void *)mask_inout}) {
+        if (!ptr) continue;
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(c, DOSE_EINVAL, "dvf_out and mask_inout must be device memory");
+        }
+    }
+    int rc;
+    if ((rc = use_device(c))) return rc;
+    const Grid &g = *c->g;
+    const size_t ng = (size_t)G.n[0] * G.n[1] * G.n[2];
+    if (ng > (size_t)INT32_MAX) return fail(c, DOSE_EINVAL, "registration grid has 2^31 voxels or more");
+    cudaStream_t st = S(stream);
+    if (ng > c->dvfgrid_cap) {
+        if (c->dvfgrid_e) { dfree(c, c->dvfgrid_e); c->dvfgrid_e = nullptr; }
+        if (c->dvfgrid_delta) { dfree(c, c->dvfgrid_delta); c->dvfgrid_delta = nullptr; }
+        c->dvfgrid_cap = 0;
+        if ((rc = dalloc_t(c, &c->dvfgrid_e, 3 * ng)) || (rc = dalloc_t(c, &c->dvfgrid_delta, 3 * ng))) return rc;
+        c->dvfgrid_cap = ng;
+    }
+    const float *delta = translation;
+    if (!translation_on_device) {
+        CK(c, cudaMemcpyAsync(c->dvfgrid_delta, translation, 3 * ng * sizeof(float), cudaMemcpyHostToDevice, st));
+        delta = c->dvfgrid_delta;
+    }
+    DvfArgs a;
+    for (int k = 0; k < 3; ++k) {
+        a.gn[k] = G.n[k]; a.start[k] = G.start_mm[k]; a.sp[k] = G.spacing_mm[k];
+        a.U[k] = G.row_cos[k]; a.V[k] = G.col_cos[k];
+        a.n[k] = g.n[k]; a.d[k] = g.d[k]; a.origin[k] = g.origin[k];
+    }
+    const double U[3] = {G.row_cos[0], G.row_cos[1], G.row_cos[2]}, V[3] = {G.col_cos[0], G.col_cos[1], G.col_cos[2]};
+    a.W[0] = (float)(U[1] * V[2] - U[2] * V[1]);
+    a.W[1] = (float)(U[2] * V[0] - U[0] * V[2]);
+    a.W[2] = (float)(U[0] * V[1] - U[1] * V[0]);
+    for (int k = 0; k < 16; ++k) { a.pre[k] = G.pre[k]; a.post[k] = G.post[k]; }
+    for (int r = 0; r < 3; ++r)
+        for (int m = 0; m < 3; ++m) {
+            double v = (r == m) ? -1.0 : 0.0;
+            for (int t = 0; t < 3; ++t) v += (double)G.post[4 * r + t] * G.pre[4 * t + m];
+            a.RR[3 * r + m] = (float)v;
+        }
+    a.delta = delta; a.e = c->dvfgrid_e; a.out = dvf_out; a.mask = mask_inout;
+    k_dvf_grid<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(a);
+    CK(c, cudaGetLastError());
+    k_dvf_resample<<<(unsigned)((g.nvox + 255) / 256), 256, 0, st>>>(a);
+    CK(c, cudaGetLastError());
     return DOSE_OK;
 }
 

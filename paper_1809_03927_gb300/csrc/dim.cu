@@ -55,9 +55,10 @@ __global__ void __launch_bounds__(256, 3) k_dim(DimArgs a)
     const long long nvox = (long long)a.nx * a.ny * a.nz;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nvox) return;
-    const int ix = (int)(i % a.nx);
-    const int iy = (int)((i / a.nx) % a.ny);
-    const int iz = (int)(i / ((long long)a.nx * a.ny));
+    const unsigned iu = (unsigned)i, row = iu / (unsigned)a.nx;     // nvox < 2^31
+    const int ix = (int)(iu - row * (unsigned)a.nx);
+    const int iy = (int)(row % (unsigned)a.ny);
+    const int iz = (int)(row / (unsigned)a.ny);
     const int ns[3] = {a.nsx, a.nsy, a.nsz};
     const int ii[3] = {ix, iy, iz};
     const int nn[3] = {a.nx, a.ny, a.nz};

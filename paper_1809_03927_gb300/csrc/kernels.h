@@ -73,4 +73,20 @@ struct DimArgs {
 };
 __global__ void k_dim(DimArgs a);
 
+struct DvfArgs {
+    int gn[3];                       // registration grid voxels
+    float start[3], sp[3];           // centre of grid voxel 0, spacing (mm)
+    float U[3], V[3], W[3];          // row, column, depth direction cosines (W = U x V)
+    float pre[16], post[16];         // rigid transforms, row-major
+    float RR[9];                     // R_post R_pre - I
+    const float *delta;              // grid voxels x 3 (interleaved), mm
+    float *e;                        // 3 x grid voxels: r_f - r0
+    int n[3];                        // CT grid
+    float d[3], origin[3];
+    float *out;                      // 3 x nvox displacement, mm
+    uint8_t *mask;                   // nvox, cleared outside the grid hull, or null
+};
+__global__ void k_dvf_grid(DvfArgs a);
+__global__ void k_dvf_resample(DvfArgs a);
+
 }  // namespace dose

@@ -67,6 +67,12 @@ class dose_request(C.Structure):
                 ("shift_mm", C.c_float * 3)]
 
 
+class dose_dvf_grid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("start_mm", C.c_float * 3), ("spacing_mm", C.c_float * 3),
+                ("row_cos", C.c_float * 3), ("col_cos", C.c_float * 3), ("pre", C.c_float * 16),
+                ("post", C.c_float * 16)]
+
+
 assert C.sizeof(dose_spot) == 32 and C.sizeof(dose_job) == 64
 assert C.sizeof(dose_server_config) == 56 and C.sizeof(dose_request) == 32
 
@@ -102,6 +108,7 @@ def _load():
         "dose_server_destroy": ([P], None),
         "dose_run_phase_noalloc": ([P, I, I, I, F, F, F, P, P, P, I, U64, U64, P, P, P], I),
         "dose_debug_tables": ([P, I, P, P], I),
+        "dose_decode_dvf": ([P, P, P, I, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -253,6 +260,34 @@ def dose_accumulate_subvoxel(ctx, ref_phase, nsub, dvf=None, mask=None, method=A
     mp, mdev = _ptr(mask)
     _check(_lib.dose_accumulate_subvoxel(ctx, int(ref_phase), ns, dp, ddev, mp, mdev, int(method),
                                          _stream(stream)), ctx)
+
+
+def dvf_grid_struct(grid):
+    """dose_dvf_grid from a dict: n, start_mm, spacing_mm, row_cos, col_cos
+    and optional pre/post (row-major 4x4, default identity)."""
+    g = dose_dvf_grid()
+    for name in ("n", "start_mm", "spacing_mm", "row_cos", "col_cos"):
+        getattr(g, name)[:] = [v for v in grid[name]]
+    eye = np.eye(4).ravel()
+    g.pre[:] = [float(v) for v in np.asarray(grid.get("pre", eye), np.float64).ravel()]
+    g.post[:] = [float(v) for v in np.asarray(grid.get("post", eye), np.float64).ravel()]
+    return g
+
+
+def dose_decode_dvf(ctx, grid, translation, dvf_out, mask=None, stream=None):
+    """Decode a registration grid (App. B, Eqs. 7-8) into ``dvf_out``, a
+    device tensor of 3 x nvox floats (one phase's block); ``mask`` (device
+    uint8, nvox) is cleared outside the grid's hull."""
+    g = dvf_grid_struct(grid)
+    if not _is_torch(translation):
+        translation = np.ascontiguousarray(translation, dtype=np.float32)
+    tp, tdev = _ptr(translation)
+    op, odev = _ptr(dvf_out)
+    mp, mdev = _ptr(mask)
+    if not odev or (mask is not None and not mdev):
+        raise ValueError("dvf_out and mask must be device tensors")
+    _check(_lib.dose_decode_dvf(ctx, C.byref(g), tp, tdev, op, mp, _stream(stream)), ctx)
+    return dvf_out
 
 
 def dose_read(ctx, what, phase, dst, stream=None):
