@@ -73,6 +73,17 @@ class DeliveryC(C.Structure):
         ("period_ns", C.c_int64), ("period_sigma_ns", C.c_int64), ("spot_switch_ns", C.c_int64),
         ("layer_switch_ns", C.c_int64), ("discard_ns", C.c_int64),
         ("rate_protons_per_s", C.c_uint64), ("seed", C.c_uint64),
+        ("synchrotron", C.c_int32), ("reserved", C.c_int32), ("fill_protons", C.c_uint64),
+        ("extraction_limit_ns", C.c_int64), ("max_protons_per_paint", C.c_uint64),
+    ]
+
+
+class SpreadC(C.Structure):
+    _fields_ = [
+        ("period_min_ns", C.c_int64), ("period_max_ns", C.c_int64), ("period_step_ns", C.c_int64),
+        ("spot_switch_sigma_ns", C.c_int64), ("layer_switch_sigma_ns", C.c_int64),
+        ("discard_sigma_ns", C.c_int64), ("rate_sigma", C.c_int64), ("fill_protons_sigma", C.c_int64),
+        ("extraction_limit_sigma_ns", C.c_int64),
     ]
 
 
@@ -107,6 +118,10 @@ def lib():
         L.or_frame.argtypes = [P, P, P]
         L.or_normalise.argtypes = [C.c_int64, P, P, C.c_double, C.c_double, P]
         L.or_timeline.argtypes = [C.c_int64, P, P, P, C.POINTER(DeliveryC), P, P, P, C.c_int32]
+        L.or_trial_delivery.argtypes = [C.POINTER(DeliveryC), C.POINTER(SpreadC), C.c_uint64,
+                                        C.POINTER(DeliveryC)]
+        L.or_breathing_deviate.argtypes = [C.c_uint64, C.c_int32, C.c_uint64]
+        L.or_breathing_deviate.restype = C.c_int64
         L.or_emtm.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P, P]
         L.or_dim.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P]
         L.or_dvf_decode.argtypes = [P] * 13
@@ -307,9 +322,7 @@ def timeline(plan, delivery, n_fields=None):
     n = len(plan)
     if n_fields is None:
         n_fields = int(np.max(plan.field)) + 1
-    D = DeliveryC()
-    for name, _ in DeliveryC._fields_:
-        setattr(D, name, int(getattr(delivery, name)))
+    D = _delivery_c(delivery)
     p = np.ascontiguousarray(plan.protons, np.uint64)
     la = np.ascontiguousarray(plan.layer, np.int32)
     fi = np.ascontiguousarray(plan.field, np.int32)
@@ -321,6 +334,32 @@ def timeline(plan, delivery, n_fields=None):
     if rc:
         raise ValueError(f"or_timeline failed: {rc}")
     return pp, fe, sp
+
+
+def _delivery_c(delivery):
+    D = DeliveryC()
+    for name, _ in DeliveryC._fields_:
+        setattr(D, name, int(getattr(delivery, name, 0)))
+    return D
+
+
+def trial_delivery(mean, spread, trial):
+    """Trial ``trial``'s delivery parameters (the uncertainty trials of Sec.
+    2.B), drawn from ``mean`` and the ``spread`` (object with the SpreadC
+    field names).  Returns a dict of the sampled delivery's fields."""
+    S = SpreadC()
+    for name, _ in SpreadC._fields_:
+        setattr(S, name, int(getattr(spread, name, 0)))
+    out = DeliveryC()
+    rc = lib().or_trial_delivery(C.byref(_delivery_c(mean)), C.byref(S), int(trial), C.byref(out))
+    if rc:
+        raise ValueError(f"or_trial_delivery failed: {rc}")
+    return {name: getattr(out, name) for name, _ in DeliveryC._fields_}
+
+
+def breathing_deviate(seed, field, cycle):
+    """2^21 times the Irwin-Hall deviate of breathing cycle ``cycle``."""
+    return int(lib().or_breathing_deviate(int(seed), int(field), int(cycle)))
 
 
 def emtm(dose_phases, rho_phases, d, ref_phase, nsub, dvf=None, mask=None, return_sums=False):

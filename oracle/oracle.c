@@ -37,7 +37,13 @@
  *                      Pinned: hand-worked unit conversion.
  *   or_timeline        Sec. 2.B, App. A.  Pinned: invariants (protons
  *                      conserved, clock total), the one-phase test of
- *                      Sec. 2.E, hand-worked examples.
+ *                      Sec. 2.E, hand-worked examples (simple clock,
+ *                      synchrotron fills, charge and time limits, gate
+ *                      holds, capped repainting), the synchrotron model
+ *                      reducing to the simple clock without limits, the
+ *                      moments and bounds of the breathing deviates.
+ *   or_trial_delivery  Sec. 2.B (the 25 uncertainty trials).  Pinned:
+ *                      discrete-uniform periods, Gaussian moments.
  *   or_emtm            Sec. 2.D.2, Eqs. 2, 4-6.  Pinned: identity-DVF test
  *                      of Sec. 2.E, integer translation, mass conservation,
  *                      brute force.
@@ -828,22 +834,118 @@ void or_normalise(int64_t nvox, const double *edep, const double *rho,
 /* Delivery timeline (Sec. 2.B, App. A): integer-ns breathing and spot     */
 /* clocks; each spot (or portion of a spot) is assigned to the breathing   */
 /* phase during which it is delivered.                                     */
+/*                                                                         */
+/* Breathing clock of field f.  The clock starts (t = 0) at the beginning  */
+/* of phase p0 of cycle 0; p0 is given or drawn as word 0 of Philox4x32-10 */
+/* (counter (f, 0, 0, 0), key seed) mod N.  Cycle c lasts N t_c with       */
+/* t_c = floor(T_c / N) (Sec. 2.B: t_ph ~ N(mu, sigma) / N, one draw per   */
+/* cycle).  T_c = mu when sigma = 0; otherwise T_c = max(N, mu +           */
+/* round(sigma Z_c)) with Z_c = sum of twelve uniforms - 6 (Irwin-Hall),   */
+/* the uniforms being those of the blocks (f, c, 1, 0) and (f, c, 2, 0),  */
+/* so that T_c = mu + floor((sigma (K - 6 (2^21 - 1)) + 2^20) / 2^21) with */
+/* K the sum of their twelve 21-bit integers: exact integer arithmetic.    */
+/*                                                                         */
+/* Spill clock, common rules: spots of a field go in plan order; a layer   */
+/* is a maximal run of equal layer ids; a spill of w protons lasts         */
+/* floor(w 1e9 / rate) ns and is split over the phase slots it spans by    */
+/* time share (floor for each portion, the remainder to the last).  Each   */
+/* layer is painted `repaints` times (floor(p / R) per painting, the       */
+/* remainder in the last) or, when max_protons_per_paint = m > 0, painted  */
+/* until done with min(left, m) per spot and painting (isolayered          */
+/* repainting with a maximum per spot delivery, Sec. 2.B).                 */
+/*                                                                         */
+/* synchrotron = 0 (the clock of Sec. 2.B): switch times precede every     */
+/* spill but the first of a field (layer_switch_ns before a layer's first  */
+/* spill, spot_switch_ns otherwise); gated delivery skips from a gate-off  */
+/* phase to the start of the next gate_first phase and adds discard_ns.    */
+/*                                                                         */
+/* synchrotron = 1 (App. A): protons come in fills.  A fill starts with a  */
+/* reset of layer_switch_ns (not for the field's first fill), then, when   */
+/* gated, a hold until the gate is on, then the beam discard of            */
+/* discard_ns, then extraction.  A new layer always takes a new fill.  A   */
+/* fill holds fill_protons (0: unlimited) and extracts for at most         */
+/* extraction_limit_ns after its extraction starts (0: unlimited).  Spills */
+/* of one fill are separated by spot_switch_ns.  A spill that meets the    */
+/* fill's charge, its time limit or a gate-off stops there: the part       */
+/* delivered has the remaining charge, or floor(w elapsed / duration)      */
+/* protons for a time cut, and the rest continues (without a spot switch) */
+/* after the next extraction start: after a gate-off the beam holds until */
+/* the gate is on and discards discard_ns again; after the charge or the  */
+/* time limit a new fill starts.                                           */
 /* ======================================================================= */
 typedef struct {
     int32_t n_phases, start_phase, gated, gate_first, gate_last, repaints;
     int64_t period_ns, period_sigma_ns, spot_switch_ns, layer_switch_ns, discard_ns;
     uint64_t rate_protons_per_s, seed;
+    int32_t synchrotron, reserved;
+    uint64_t fill_protons;
+    int64_t extraction_limit_ns;
+    uint64_t max_protons_per_paint;
 } or_delivery;
+
+/* Irwin-Hall sum of the twelve 21-bit integers of blocks (a, b, c1, 0)
+ * and (a, b, c1 + 1, 0) minus 6 (2^21 - 1): 2^21 times a standard deviate. */
+static int64_t or_irwin_hall(uint64_t seed, uint32_t a, uint32_t b, uint32_t c1)
+{
+    int64_t K = 0;
+    for (uint32_t blk = 0; blk < 2; ++blk) {
+        uint32_t ctr[4] = { a, b, c1 + blk, 0u };
+        uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+        uint32_t w[4];
+        or_philox4x32_10(ctr, key, w);
+        unsigned __int128 v = (unsigned __int128)w[0] | ((unsigned __int128)w[1] << 32) |
+                              ((unsigned __int128)w[2] << 64) | ((unsigned __int128)w[3] << 96);
+        for (int i = 0; i < 6; ++i) K += (int64_t)((v >> (21 * i)) & 0x1FFFFFu);
+    }
+    return K - 6 * (int64_t)0x1FFFFF;
+}
+
+/* mean + round(sigma Z) with Z = zk / 2^21 (round half up), exact. */
+static int64_t or_gauss_ns(int64_t mean, int64_t sigma, int64_t zk)
+{
+    __int128 num = (__int128)sigma * zk + ((__int128)1 << 20);
+    __int128 q = num >> 21;                    /* floor division by 2^21 */
+    return mean + (int64_t)q;
+}
 
 typedef struct {
     const or_delivery *D;
-    int64_t tph;
-    uint32_t p0;
+    int32_t f;
+    int64_t N;
+    uint64_t cycle;
+    int64_t cyc_start, tph;
 } or_clock;
 
-static uint32_t or_phase_at(const or_clock *C, int64_t t)
+static int64_t or_cycle_tph(const or_clock *C, uint64_t c)
 {
-    return (uint32_t)((C->p0 + (uint64_t)(t / C->tph)) % (uint64_t)C->D->n_phases);
+    int64_t T = C->D->period_ns;
+    if (C->D->period_sigma_ns > 0) {
+        T = or_gauss_ns(T, C->D->period_sigma_ns,
+                        or_irwin_hall(C->D->seed, (uint32_t)C->f, (uint32_t)c, 1u));
+        if (T < C->N) T = C->N;
+    }
+    return T / C->N;
+}
+
+static void or_clock_sync(or_clock *C, int64_t t)
+{
+    while (t >= C->cyc_start + C->N * C->tph) {
+        C->cyc_start += C->N * C->tph;
+        C->cycle += 1;
+        C->tph = or_cycle_tph(C, C->cycle);
+    }
+}
+
+static uint32_t or_phase_at(or_clock *C, int64_t t)
+{
+    or_clock_sync(C, t);
+    return (uint32_t)((t - C->cyc_start) / C->tph);
+}
+
+static int64_t or_slot_end(or_clock *C, int64_t t)
+{
+    or_clock_sync(C, t);
+    return C->cyc_start + ((t - C->cyc_start) / C->tph + 1) * C->tph;
 }
 
 static int or_gate_on(const or_clock *C, uint32_t ph)
@@ -851,19 +953,156 @@ static int or_gate_on(const or_clock *C, uint32_t ph)
     return !C->D->gated || ((int32_t)ph >= C->D->gate_first && (int32_t)ph <= C->D->gate_last);
 }
 
-/* Advance t to the start of the next slot whose phase is the first gate-on
- * phase, then add the beam-discard time; repeat while the gate is off.    */
-static int64_t or_wait_gate(const or_clock *C, int64_t t)
+/* the start of the next gate-on slot at or after t */
+static int64_t or_hold(or_clock *C, int64_t t)
 {
-    while (!or_gate_on(C, or_phase_at(C, t))) {
-        int64_t slot = t / C->tph;
-        int64_t N = C->D->n_phases;
-        int64_t next = slot + 1;
-        int64_t ph_next = (int64_t)((C->p0 + (uint64_t)next) % (uint64_t)N);
-        int64_t delta = ((int64_t)C->D->gate_first - ph_next) % N;
-        if (delta < 0) delta += N;
-        t = (next + delta) * C->tph + C->D->discard_ns;
+    while (!or_gate_on(C, or_phase_at(C, t))) t = or_slot_end(C, t);
+    return t;
+}
+
+/* the end of the gate-on run containing t (looked up on a copy of the clock) */
+static int64_t or_gate_off_after(const or_clock *C, int64_t t)
+{
+    or_clock L = *C;
+    while (or_gate_on(&L, or_phase_at(&L, t))) t = or_slot_end(&L, t);
+    return t;
+}
+
+/* Deliver w protons over [t, end), split at slot ends by time share. */
+static void or_deposit(or_clock *C, int64_t t, int64_t end, uint64_t w, uint64_t *pp,
+                       int64_t n_spots, int64_t q)
+{
+    if (w == 0) return;
+    if (end <= t) {
+        pp[(size_t)or_phase_at(C, t) * (size_t)n_spots + (size_t)q] += w;
+        return;
     }
+    const uint64_t dur = (uint64_t)(end - t);
+    uint64_t given = 0;
+    while (t < end) {
+        int64_t se = or_slot_end(C, t);
+        int64_t e = se < end ? se : end;
+        uint32_t ph = or_phase_at(C, t);
+        uint64_t pj = (e == end) ? w - given
+                                 : (uint64_t)((unsigned __int128)w * (uint64_t)(e - t) / dur);
+        given += pj;
+        pp[(size_t)ph * (size_t)n_spots + (size_t)q] += pj;
+        t = e;
+    }
+}
+
+static int64_t or_spill_ns(uint64_t w, uint64_t rate)
+{
+    return (int64_t)((unsigned __int128)w * 1000000000u / rate);
+}
+
+/* Parameters that make every fill and every gate window deliver at least
+ * one proton (so the clock always advances): checked on both sides.     */
+static int or_delivery_ok(const or_delivery *D)
+{
+    if (D->n_phases <= 0 || D->repaints <= 0 || D->period_ns <= 0 || D->rate_protons_per_s == 0 ||
+        D->period_sigma_ns < 0 || D->spot_switch_ns < 0 || D->layer_switch_ns < 0 ||
+        D->discard_ns < 0 || D->start_phase >= D->n_phases || D->extraction_limit_ns < 0)
+        return 0;
+    if (D->max_protons_per_paint > 0 && D->repaints != 1) return 0;
+    if (D->synchrotron != 0 && D->synchrotron != 1) return 0;
+    /* shortest cycle: mu - 6 sigma (the Irwin-Hall bound), at least N ns */
+    __int128 tmin = (__int128)D->period_ns - 6 * (__int128)D->period_sigma_ns;
+    if (tmin < D->n_phases) return 0;
+    int64_t tph_min = (int64_t)(tmin / D->n_phases);
+    int64_t proton_ns = (int64_t)((1000000000ull + D->rate_protons_per_s - 1) / D->rate_protons_per_s);
+    if (D->gated) {
+        if (D->gate_first < 0 || D->gate_last >= D->n_phases || D->gate_first > D->gate_last) return 0;
+        int64_t window = (int64_t)(D->gate_last - D->gate_first + 1) * tph_min;
+        if (D->discard_ns >= window) return 0;
+        if (D->synchrotron && window - D->discard_ns < proton_ns) return 0;
+    }
+    if (D->synchrotron && D->extraction_limit_ns > 0 && D->extraction_limit_ns < proton_ns) return 0;
+    return 1;
+}
+
+typedef struct {                          /* synchrotron fill state */
+    int in_fill, fills, spills, empty;
+    int64_t ext_start;
+    uint64_t left, got;
+} or_fill;
+
+#define OR_MAX_EMPTY_FILLS 64
+
+/* Start a fill's extraction (App. A): reset, hold for the gate, discard.
+ * Returns -1 when too many fills in a row delivered nothing.            */
+static int64_t or_fill_start(or_clock *C, or_fill *F, int64_t t)
+{
+    const or_delivery *D = C->D;
+    if (F->fills > 0) {
+        F->empty = F->got ? 0 : F->empty + 1;
+        if (F->empty > OR_MAX_EMPTY_FILLS) return -1;
+        t += D->layer_switch_ns;
+    }
+    F->fills += 1;
+    if (D->gated) t = or_hold(C, t);
+    t += D->discard_ns;
+    F->ext_start = t;
+    F->left = D->fill_protons;
+    F->in_fill = 1;
+    F->spills = 0;
+    F->got = 0;
+    return t;
+}
+
+/* One spot portion of w protons under the synchrotron rules; -1 when the
+ * delivery makes no progress.                                           */
+static int64_t or_sync_spill(or_clock *C, or_fill *F, int64_t t, uint64_t w, uint64_t *pp,
+                             int64_t n_spots, int64_t q)
+{
+    const or_delivery *D = C->D;
+    int first = 1;
+    while (w > 0) {
+        if (!F->in_fill) {
+            if ((t = or_fill_start(C, F, t)) < 0) return -1;
+        } else if (first && F->spills > 0) {
+            t += D->spot_switch_ns;
+        }
+        first = 0;
+        const int64_t lim = D->extraction_limit_ns > 0 ? F->ext_start + D->extraction_limit_ns : INT64_MAX;
+        if (D->gated && !or_gate_on(C, or_phase_at(C, t))) {
+            const int64_t resume = or_hold(C, t) + D->discard_ns;   /* paused at a gate-off */
+            if (resume >= lim) {                 /* the fill expires while held */
+                if (t < lim) t = lim;
+                F->in_fill = 0;
+                continue;
+            }
+            t = resume;
+        }
+        if (t >= lim) { F->in_fill = 0; continue; }
+        uint64_t part = w;
+        if (D->fill_protons > 0 && F->left < part) part = F->left;
+        const int64_t dur = or_spill_ns(part, D->rate_protons_per_s);
+        int64_t end = t + dur;
+        int cut = 0;                                    /* 1: time limit, 2: gate-off */
+        if (end > lim) { end = lim; cut = 1; }
+        if (D->gated) {
+            int64_t off = or_gate_off_after(C, t);
+            if (end > off) { end = off; cut = 2; }
+        }
+        uint64_t now = part;
+        if (cut) now = (uint64_t)((unsigned __int128)part * (uint64_t)(end - t) / (uint64_t)dur);
+        or_deposit(C, t, end, now, pp, n_spots, q);
+        t = end;
+        w -= now;
+        F->got += now;
+        F->spills += 1;
+        if (D->fill_protons > 0) F->left -= now;
+        if (cut == 1 || (D->fill_protons > 0 && F->left == 0)) F->in_fill = 0;
+    }
+    return t;
+}
+
+/* Simple-clock gate: from a gate-off phase, skip to the start of the next
+ * gate_first phase and add the beam discard.                            */
+static int64_t or_wait_gate(or_clock *C, int64_t t)
+{
+    if (C->D->gated && !or_gate_on(C, or_phase_at(C, t))) t = or_hold(C, t) + C->D->discard_ns;
     return t;
 }
 
@@ -871,45 +1110,34 @@ int or_timeline(int64_t n_spots, const uint64_t *protons, const int32_t *layer,
                 const int32_t *field, const or_delivery *D, uint64_t *pp,
                 int64_t *field_end_ns, int32_t *start_phase_out, int32_t n_fields)
 {
-    if (n_spots <= 0 || D->n_phases <= 0 || D->repaints <= 0 || D->period_ns <= 0 ||
-        D->rate_protons_per_s == 0 || D->period_sigma_ns != 0 || n_fields <= 0 ||
-        D->spot_switch_ns < 0 || D->layer_switch_ns < 0)
-        return OR_EINVAL;
-    int64_t tph = D->period_ns / D->n_phases;
-    if (tph <= 0) return OR_EINVAL;
-    if (D->gated) {
-        if (D->gate_first < 0 || D->gate_last >= D->n_phases || D->gate_first > D->gate_last)
-            return OR_EINVAL;
-        if (D->discard_ns < 0 || D->discard_ns >= (int64_t)(D->gate_last - D->gate_first + 1) * tph)
-            return OR_EINVAL;
-    }
-    if (D->start_phase >= D->n_phases) return OR_EINVAL;
+    if (n_spots <= 0 || n_fields <= 0 || !or_delivery_ok(D)) return OR_EINVAL;
     for (int64_t s = 0; s < n_spots; ++s)
         if (field[s] < 0 || field[s] >= n_fields) return OR_EINVAL;
     memset(pp, 0, sizeof(uint64_t) * (size_t)(n_spots * D->n_phases));
-    size_t cap = 64;
-    int64_t *pd = (int64_t *)malloc(sizeof(int64_t) * cap);
-    uint32_t *pph = (uint32_t *)malloc(sizeof(uint32_t) * cap);
-    if (!pd || !pph) { free(pd); free(pph); return OR_ENOMEM; }
+    uint64_t *left = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n_spots);
+    if (!left) return OR_ENOMEM;
+    const uint64_t R = (uint64_t)D->repaints, cap = D->max_protons_per_paint;
     int rc = OR_OK;
     for (int32_t f = 0; f < n_fields && rc == OR_OK; ++f) {
-        or_clock C = { D, tph, 0u };
+        uint32_t p0;
         if (D->start_phase >= 0) {
-            C.p0 = (uint32_t)D->start_phase;
+            p0 = (uint32_t)D->start_phase;
         } else {
             /* random start phase: word 0 of Philox(counter (f,0,0,0), key seed) mod N */
             uint32_t ctr[4] = { (uint32_t)f, 0u, 0u, 0u };
             uint32_t key[2] = { (uint32_t)D->seed, (uint32_t)(D->seed >> 32) };
             uint32_t w[4];
             or_philox4x32_10(ctr, key, w);
-            C.p0 = w[0] % (uint32_t)D->n_phases;
+            p0 = w[0] % (uint32_t)D->n_phases;
         }
-        start_phase_out[f] = (int32_t)C.p0;
+        start_phase_out[f] = (int32_t)p0;
+        or_clock C = { D, f, D->n_phases, 0u, 0, 0 };
+        C.tph = or_cycle_tph(&C, 0);
+        C.cyc_start = -(int64_t)p0 * C.tph;
+        or_fill F = { 0, 0, 0, 0, 0, 0, 0 };
         int64_t t = 0;
         int delivered_any = 0;
         int64_t s = 0;
-        /* the field's spots in plan order; a layer is a maximal run of equal
-           layer ids among them and is painted `repaints` times in a row     */
         while (s < n_spots && rc == OR_OK) {
             if (field[s] != f) { ++s; continue; }
             int64_t l0 = s, l1 = s;
@@ -920,57 +1148,120 @@ int or_timeline(int64_t n_spots, const uint64_t *protons, const int32_t *layer,
             }
             s = l1 + 1;
             int layer_started = 0;
-            for (int32_t r = 0; r < D->repaints && rc == OR_OK; ++r) {
+            F.in_fill = 0;                          /* a new energy takes a new fill */
+            for (int64_t q = l0; q <= l1; ++q) left[q] = protons[q];
+            for (uint64_t r = 0; rc == OR_OK; ++r) {
+                if (cap == 0 && r == R) break;
+                int any = 0;
                 for (int64_t q = l0; q <= l1; ++q) {
                     if (field[q] != f) continue;
-                    uint64_t w = protons[q] / (uint64_t)D->repaints;
-                    if (r == D->repaints - 1) w += protons[q] % (uint64_t)D->repaints;
+                    uint64_t w;
+                    if (cap > 0) {
+                        w = left[q] < cap ? left[q] : cap;
+                    } else {
+                        w = protons[q] / R;
+                        if (r == R - 1) w += protons[q] % R;
+                    }
                     if (w == 0) continue;
+                    left[q] -= w;
+                    any = 1;
+                    if (D->synchrotron) {
+                        t = or_sync_spill(&C, &F, t, w, pp, n_spots, q);
+                        if (t < 0) { rc = OR_ESTEP; break; }
+                        continue;
+                    }
                     if (delivered_any)
                         t += layer_started ? D->spot_switch_ns : D->layer_switch_ns;
                     delivered_any = 1;
                     layer_started = 1;
                     /* spill time of this portion, ns */
-                    int64_t dur = (int64_t)((unsigned __int128)w * 1000000000u / D->rate_protons_per_s);
-                    if (D->gated) t = or_wait_gate(&C, t);
-                    size_t np = 0;
-                    if (dur == 0) { pph[0] = or_phase_at(&C, t); pd[0] = 0; np = 1; }
+                    const int64_t dur = or_spill_ns(w, D->rate_protons_per_s);
+                    t = or_wait_gate(&C, t);
+                    if (dur == 0) {
+                        pp[(size_t)or_phase_at(&C, t) * (size_t)n_spots + (size_t)q] += w;
+                        continue;
+                    }
+                    /* split over slots by time share, pausing at gate-offs */
                     int64_t rem = dur;
+                    uint64_t given = 0;
                     while (rem > 0) {
-                        if (D->gated) t = or_wait_gate(&C, t);
-                        int64_t slot = t / tph;
-                        int64_t seg = (slot + 1) * tph - t;
+                        t = or_wait_gate(&C, t);
+                        int64_t seg = or_slot_end(&C, t) - t;
                         int64_t d = rem < seg ? rem : seg;
-                        if (np == cap) {
-                            cap *= 2;
-                            int64_t *nd = (int64_t *)realloc(pd, sizeof(int64_t) * cap);
-                            if (nd) pd = nd;
-                            uint32_t *nph = (uint32_t *)realloc(pph, sizeof(uint32_t) * cap);
-                            if (nph) pph = nph;
-                            if (!nd || !nph) { rc = OR_ENOMEM; break; }
-                        }
-                        pph[np] = or_phase_at(&C, t); pd[np] = d; ++np;
+                        uint32_t ph = or_phase_at(&C, t);
                         t += d;
                         rem -= d;
-                    }
-                    if (rc) break;
-                    /* protons by time share: floor for every portion but the
-                       last, which takes the remainder                        */
-                    uint64_t given = 0;
-                    for (size_t j = 0; j < np; ++j) {
-                        uint64_t pj;
-                        if (j == np - 1) pj = w - given;
-                        else pj = (uint64_t)((unsigned __int128)w * (uint64_t)pd[j] / (uint64_t)dur);
+                        uint64_t pj = rem > 0 ? (uint64_t)((unsigned __int128)w * (uint64_t)d / (uint64_t)dur)
+                                              : w - given;
                         given += pj;
-                        pp[(size_t)pph[j] * (size_t)n_spots + (size_t)q] += pj;
+                        pp[(size_t)ph * (size_t)n_spots + (size_t)q] += pj;
                     }
                 }
+                if (cap > 0 && !any) break;
             }
         }
         field_end_ns[f] = t;
     }
-    free(pd); free(pph);
+    free(left);
     return rc;
+}
+
+/* ======================================================================= */
+/* Uncertainty trials (Sec. 2.B, the 25-trial study): trial k's delivery   */
+/* draws, from Philox4x32-10 under key `seed`, a breathing period from the */
+/* discrete uniform set {min, min + step, ..., max} (word 0 of block (k,   */
+/* 0, 3, 0) mod the set size) and each synchrotron parameter from          */
+/* N(mean, sigma) (Irwin-Hall blocks (k, j, 4, 0), (k, j, 5, 0) for        */
+/* parameter j = 0 spot switch, 1 layer switch, 2 discard, 3 rate, 4 fill  */
+/* charge, 5 extraction limit; round half up; clamped at 0, the rate at   */
+/* 1).  The trial's own seed, which draws its start phase and breathing    */
+/* cycles, is seed + k 0x9E3779B97F4A7C15 (mod 2^64).                      */
+/* ======================================================================= */
+typedef struct {
+    int64_t period_min_ns, period_max_ns, period_step_ns;
+    int64_t spot_switch_sigma_ns, layer_switch_sigma_ns, discard_sigma_ns;
+    int64_t rate_sigma, fill_protons_sigma, extraction_limit_sigma_ns;
+} or_spread;
+
+static int64_t or_clamp0(int64_t v) { return v < 0 ? 0 : v; }
+
+int or_trial_delivery(const or_delivery *mean, const or_spread *S, uint64_t trial, or_delivery *out)
+{
+    *out = *mean;
+    const uint64_t seed = mean->seed;
+    if (S->period_max_ns > S->period_min_ns) {
+        if (S->period_step_ns <= 0 || S->period_min_ns <= 0) return OR_EINVAL;
+        uint64_t n = (uint64_t)((S->period_max_ns - S->period_min_ns) / S->period_step_ns) + 1;
+        uint32_t ctr[4] = { (uint32_t)trial, 0u, 3u, 0u };
+        uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+        uint32_t w[4];
+        or_philox4x32_10(ctr, key, w);
+        out->period_ns = S->period_min_ns + (int64_t)(w[0] % n) * S->period_step_ns;
+    }
+    const int64_t sig[6] = { S->spot_switch_sigma_ns, S->layer_switch_sigma_ns, S->discard_sigma_ns,
+                             S->rate_sigma, S->fill_protons_sigma, S->extraction_limit_sigma_ns };
+    int64_t val[6] = { mean->spot_switch_ns, mean->layer_switch_ns, mean->discard_ns,
+                       (int64_t)mean->rate_protons_per_s, (int64_t)mean->fill_protons,
+                       mean->extraction_limit_ns };
+    for (int j = 0; j < 6; ++j) {
+        if (sig[j] < 0) return OR_EINVAL;
+        if (sig[j] == 0) continue;
+        val[j] = or_clamp0(or_gauss_ns(val[j], sig[j], or_irwin_hall(seed, (uint32_t)trial, (uint32_t)j, 4u)));
+    }
+    out->spot_switch_ns = val[0];
+    out->layer_switch_ns = val[1];
+    out->discard_ns = val[2];
+    out->rate_protons_per_s = (uint64_t)(val[3] < 1 ? 1 : val[3]);
+    out->fill_protons = (uint64_t)val[4];
+    out->extraction_limit_ns = val[5];
+    out->seed = seed + trial * 0x9E3779B97F4A7C15ull;
+    return OR_OK;
+}
+
+/* 2^21 Z of cycle c of field f (exposed for the distribution pins). */
+int64_t or_breathing_deviate(uint64_t seed, int32_t f, uint64_t c)
+{
+    return or_irwin_hall(seed, (uint32_t)f, (uint32_t)c, 1u);
 }
 
 /* ======================================================================= */

@@ -94,6 +94,27 @@ class Delivery:
     discard_ns: int = 0
     rate_protons_per_s: int = 1_000_000_000
     seed: int = 3
+    synchrotron: int = 0              # 1: fills with charge / extraction-time limits (App. A)
+    reserved: int = 0
+    fill_protons: int = 0             # protons per synchrotron fill (0: unlimited)
+    extraction_limit_ns: int = 0      # extraction time per fill (0: unlimited)
+    max_protons_per_paint: int = 0    # isolayered repainting cap per spot (0: off)
+
+
+@dataclass
+class DeliverySpread:
+    """Spread of the delivery parameters over uncertainty trials (Sec. 2.B):
+    the breathing period from a discrete uniform set, the synchrotron
+    parameters Gaussian about the delivery's values."""
+    period_min_ns: int = 0
+    period_max_ns: int = 0
+    period_step_ns: int = 0
+    spot_switch_sigma_ns: int = 0
+    layer_switch_sigma_ns: int = 0
+    discard_sigma_ns: int = 0
+    rate_sigma: int = 0
+    fill_protons_sigma: int = 0
+    extraction_limit_sigma_ns: int = 0
 
 
 def _plan(xs, ys, es, sig, protons, layers, fields):
