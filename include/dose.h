@@ -71,22 +71,65 @@ typedef struct dose_spot {
 } dose_spot;
 
 /* Delivery-clock inputs of the beam-delivery simulation (Sec. 2.B, App. A),
- * integer nanoseconds.  start_phase < 0 draws the start phase of field f as
- * word 0 of Philox4x32-10(counter (f,0,0,0), key seed) mod n_phases.  Gated
- * delivery (gated != 0) beams only in phases gate_first..gate_last; at a
- * gate-off the clock skips to the start of the next gate_first phase and
- * adds discard_ns.  Each layer is painted `repaints` times, a spot giving
- * floor(protons/repaints) per painting and the remainder in the last.
- * A spot's spill time is protons * 1e9 / rate_protons_per_s ns; a spill
- * that crosses a phase boundary is split by time share (floor per portion,
- * remainder to the last).  Switch times precede every spill but the first
- * of a field: layer_switch_ns before a layer's first spill, spot_switch_ns
- * otherwise.  period_sigma_ns must be 0.                                  */
+ * integer nanoseconds.
+ * Breathing: start_phase < 0 draws the start phase of field f as word 0 of
+ * Philox4x32-10(counter (f,0,0,0), key seed) mod n_phases.  Cycle c of the
+ * breathing lasts n_phases t_c, t_c = floor(T_c / n_phases), with T_c =
+ * period_ns, or, when period_sigma_ns > 0 (irregular breathing, one draw
+ * per cycle), max(n_phases, period_ns + round(period_sigma_ns Z_c)) where
+ * Z_c is the Irwin-Hall sum of the twelve 21-bit uniforms of Philox blocks
+ * (f, c, 1, 0) and (f, c, 2, 0) minus 6 -- exact integers.
+ * Spills: a spot's spill lasts protons * 1e9 / rate_protons_per_s ns; a
+ * spill crossing a phase boundary is split by time share (floor per
+ * portion, remainder to the last).  Each layer (a maximal run of equal
+ * `layer` values within a field) is painted `repaints` times (floor(p/R)
+ * per painting, the remainder in the last) or, if max_protons_per_paint =
+ * m > 0 (then repaints must be 1), until done with min(left, m) per spot
+ * and painting (isolayered repainting with a maximum per spot delivery).
+ * synchrotron = 0: switch times precede every spill but a field's first
+ * (layer_switch_ns before a layer's first spill, spot_switch_ns otherwise);
+ * gated delivery (gated != 0) beams only in phases gate_first..gate_last
+ * and at a gate-off skips to the next gate_first phase start and adds
+ * discard_ns.
+ * synchrotron = 1 (App. A): protons come in fills.  A fill starts with a
+ * reset of layer_switch_ns (not for a field's first fill), a hold until the
+ * gate is on (gated) and the beam discard of discard_ns; every layer takes a
+ * new fill; a fill holds fill_protons (0: unlimited) and extracts for at
+ * most extraction_limit_ns after its extraction starts (0: unlimited);
+ * spills of a fill are separated by spot_switch_ns.  A spill stops at the
+ * fill's charge, its time limit (then floor(w elapsed / duration) protons)
+ * or a gate-off, and the rest follows at the next extraction start (a hold
+ * and discard after a gate-off, a new fill otherwise).
+ * Parameters must let every fill and gate window deliver a proton
+ * (period_ns - 6 period_sigma_ns >= n_phases; discard shorter than the
+ * gate window; with synchrotron, window - discard and extraction_limit_ns
+ * at least one proton's spill time).                                      */
 typedef struct dose_delivery {
     int32_t n_phases, start_phase, gated, gate_first, gate_last, repaints;
     int64_t period_ns, period_sigma_ns, spot_switch_ns, layer_switch_ns, discard_ns;
     uint64_t rate_protons_per_s, seed;
+    int32_t synchrotron, reserved;
+    uint64_t fill_protons;
+    int64_t extraction_limit_ns;
+    uint64_t max_protons_per_paint;
 } dose_delivery;
+
+/* Spread of the delivery over uncertainty trials (Sec. 2.B: start phase,
+ * breathing period and synchrotron parameters varied together over 25
+ * trials).  Trial k draws, under key `seed` of the mean delivery, the
+ * period from {period_min_ns, + period_step_ns, ..., period_max_ns} (word 0
+ * of Philox block (k,0,3,0) mod the set size; used when max > min) and each
+ * synchrotron parameter j (0 spot switch, 1 layer switch, 2 discard, 3 rate,
+ * 4 fill protons, 5 extraction limit) from N(mean, sigma_j) (Irwin-Hall of
+ * blocks (k,j,4,0), (k,j,5,0); round half up; clamped at 0, the rate at 1;
+ * sigma_j = 0 keeps the mean; sigma_j <= 2^38).  The trial's own seed,
+ * which draws its start phases and breathing cycles, is seed + k *
+ * 0x9E3779B97F4A7C15 (mod 2^64).                                         */
+typedef struct dose_delivery_spread {
+    int64_t period_min_ns, period_max_ns, period_step_ns;
+    int64_t spot_switch_sigma_ns, layer_switch_sigma_ns, discard_sigma_ns;
+    int64_t rate_sigma, fill_protons_sigma, extraction_limit_sigma_ns;
+} dose_delivery_spread;
 
 /* dose_read selectors */
 enum {
@@ -104,8 +147,10 @@ enum {
     DOSE_FIELD_END_NS = 8,   /* int64[n_fields]  delivery clock at each field's end */
     DOSE_EMTM_STATS = 9,     /* uint64[4]: subvoxels pushed, dropped (mapped outside),
                                 atomic pairs issued, reserved                       */
-    DOSE_HIST_PREFIX = 10    /* uint64[n_spots + 1] of phase `phase`: first history of
+    DOSE_HIST_PREFIX = 10,   /* uint64[n_spots + 1] of phase `phase`: first history of
                                 each spot (histories of spot s = p[s+1] - p[s])      */
+    DOSE_DELIVERY = 11       /* dose_delivery: the delivery the timeline ran (a
+                                trial's sampled one after dose_add_spots_trials)    */
 };
 
 /* Physics switches (dose_set_option DOSE_OPT_PHYSICS), all on by default. */
@@ -145,9 +190,22 @@ int dose_create_view(dose_ctx *base, dose_ctx **out);
 /* Load the plan (host array of n spots) and run the delivery simulation on
  * the device (Sec. 2.B): the per-phase subplans (protons per phase and
  * spot).  delivery = NULL puts every spot wholly on phase 0 (a static, 3D
- * delivery).  Replaces any previous plan and clears all phase results.     */
+ * delivery).  Replaces any previous plan and clears all phase results.
+ * With the synchrotron model the call waits for the stream and reports a
+ * delivery that stops making progress (DOSE_EINVAL).                      */
 int dose_add_spots(dose_ctx *c, const dose_spot *spots, int64_t n,
                    const dose_delivery *delivery, void *stream);
+
+/* Uncertainty trials (Sec. 2.B): load the plan into each of n_trials
+ * contexts (views of one grid, typically) and run, in one launch, the
+ * delivery simulation of trials first_trial .. first_trial + n_trials - 1,
+ * each drawing its delivery from `mean` and `spread` as dose_delivery_spread
+ * describes.  Waits for the stream; DOSE_EINVAL if a sampled delivery
+ * breaks the progress conditions above (message names the trial).  The
+ * per-phase subplans are then ready for dose_run_batch.                   */
+int dose_add_spots_trials(dose_ctx *const *ctxs, int n_trials, const dose_spot *spots, int64_t n,
+                          const dose_delivery *mean, const dose_delivery_spread *spread,
+                          uint64_t first_trial, void *stream);
 
 /* Monte Carlo dose of one phase's subplan (Sec. 2.C): allocate n_histories
  * over the spots in proportion to their protons (floor + largest remainder,

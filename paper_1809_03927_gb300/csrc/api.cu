@@ -26,6 +26,7 @@ namespace {
 constexpr int kVersion = 1;
 constexpr int kMaxSpots = 16384;
 constexpr int kMaxFields = 64;
+static_assert(sizeof(dose_delivery) == 112 && sizeof(dose_delivery_spread) == 72, "ABI layout");
 constexpr int kMaxDevices = 64;
 
 thread_local std::string g_thread_err;
@@ -78,6 +79,12 @@ struct dose_ctx {
     int *start_phase = nullptr;
     long long *field_end = nullptr;
     bool have_plan = false;
+    bool have_delivery = false;              // the plan ran through the timeline
+    TimelineArgs *tl_args = nullptr;         // device timeline arguments, cap_tl entries
+    int cap_tl = 0;
+    dose_delivery_spread *tl_spread = nullptr;
+    dose_delivery *tl_used = nullptr;        // the delivery the timeline ran
+    int *tl_status = nullptr;
     std::vector<PhaseState> ph;
     unsigned long long *tally_all = nullptr; // n_phases x nvox
     float *dose_all = nullptr;               // n_phases x nvox
@@ -257,6 +264,7 @@ void free_plan(dose_ctx *c)
         P.allocated = false; P.has_dose = false; P.n_hist = 0;
     }
     c->have_plan = false;
+    c->have_delivery = false;
     c->have_accum = false;
     c->n_spots = 0;
 }
@@ -441,14 +449,15 @@ int dose_set_option(dose_ctx *c, int option, int64_t value)
     }
 }
 
-int dose_add_spots(dose_ctx *c, const dose_spot *spots, int64_t n, const dose_delivery *dl, void *stream)
+namespace {
+
+// Check a plan's spots; n_fields and the proton total on success.
+int check_spots(dose_ctx *c, const dose_spot *spots, int64_t n, int *n_fields, unsigned long long *total)
 {
-    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
     if (!spots) return fail(c, DOSE_EINVAL, "spots is NULL");
     if (n <= 0 || n > kMaxSpots) return fail(c, DOSE_EINVAL, "number of spots must be in 1..%d", kMaxSpots);
-    const int P = c->g->n_phases;
-    int n_fields = 0;
-    unsigned long long max_p = 0;
+    int nf = 0;
+    unsigned long long tot = 0;
     for (int64_t s = 0; s < n; ++s) {
         const dose_spot &q = spots[s];
         if (!(q.energy_MeV >= 1.0f && q.energy_MeV <= 250.0f))
@@ -457,38 +466,39 @@ int dose_add_spots(dose_ctx *c, const dose_spot *spots, int64_t n, const dose_de
             return fail(c, DOSE_EINVAL, "spot %lld: position and sigma must be finite, sigma >= 0", (long long)s);
         if (q.field < 0 || q.field >= kMaxFields)
             return fail(c, DOSE_EINVAL, "spot %lld: field %d outside 0..%d", (long long)s, q.field, kMaxFields - 1);
-        n_fields = std::max(n_fields, q.field + 1);
-        max_p = std::max(max_p, (unsigned long long)q.protons);
+        nf = std::max(nf, q.field + 1);
+        if (tot + q.protons < tot) return fail(c, DOSE_EINVAL, "total protons overflow 64 bits");
+        tot += q.protons;
     }
-    unsigned long long total = 0;
-    for (int64_t s = 0; s < n; ++s) {
-        if (total + spots[s].protons < total) return fail(c, DOSE_EINVAL, "total protons overflow 64 bits");
-        total += spots[s].protons;
-    }
-    if (dl) {
-        if (dl->n_phases != P) return fail(c, DOSE_EINVAL, "delivery n_phases %d != grid phases %d", dl->n_phases, P);
-        if (dl->repaints < 1) return fail(c, DOSE_EINVAL, "repaints must be >= 1");
-        if (dl->period_ns <= 0 || dl->period_ns / P <= 0) return fail(c, DOSE_EINVAL, "period too short");
-        if (dl->period_sigma_ns != 0) return fail(c, DOSE_EINVAL, "irregular breathing (period_sigma_ns != 0) is not supported");
-        if (dl->rate_protons_per_s == 0) return fail(c, DOSE_EINVAL, "rate must be positive");
-        if (dl->spot_switch_ns < 0 || dl->layer_switch_ns < 0) return fail(c, DOSE_EINVAL, "switch times must be >= 0");
-        if (dl->start_phase >= P) return fail(c, DOSE_EINVAL, "start phase %d >= n_phases", dl->start_phase);
-        if (dl->gated) {
-            if (dl->gate_first < 0 || dl->gate_last >= P || dl->gate_first > dl->gate_last)
-                return fail(c, DOSE_EINVAL, "gate window must satisfy 0 <= first <= last < n_phases");
-            const long long tph = dl->period_ns / P;
-            if (dl->discard_ns < 0 || dl->discard_ns >= (long long)(dl->gate_last - dl->gate_first + 1) * tph)
-                return fail(c, DOSE_EINVAL, "discard time must be shorter than the gate window");
-        }
-        // the clock must stay far from overflow: total spill + switches < 2^62 ns
-        const long double spill = (long double)total * 1e9L / (long double)dl->rate_protons_per_s;
-        const long double sw = (long double)n * dl->repaints * (long double)std::max(dl->spot_switch_ns, dl->layer_switch_ns);
-        const long double waits = (long double)n * dl->repaints * (long double)dl->period_ns;
-        if (spill + sw + waits > 4.0e18L) return fail(c, DOSE_EINVAL, "delivery clock would overflow");
-    }
+    *n_fields = nf;
+    *total = tot;
+    return DOSE_OK;
+}
+
+// A delivery the clock can run: the grid's phase count, the progress
+// conditions, and a clock far from overflow.
+int check_delivery(dose_ctx *c, const dose_delivery *dl, int64_t n, unsigned long long total)
+{
+    const int P = c->g->n_phases;
+    if (dl->n_phases != P) return fail(c, DOSE_EINVAL, "delivery n_phases %d != grid phases %d", dl->n_phases, P);
+    if (!delivery_ok(*dl))
+        return fail(c, DOSE_EINVAL, "delivery parameters out of range or unable to progress (period, sigma, "
+                                    "gate window, discard, extraction limit, repainting)");
+    const long double spill = (long double)total * 1e9L / (long double)dl->rate_protons_per_s;
+    const long double paints = dl->max_protons_per_paint ? (long double)total / dl->max_protons_per_paint + 1 : dl->repaints;
+    const long double sw = (long double)n * paints * (long double)std::max(dl->spot_switch_ns, dl->layer_switch_ns);
+    const long double waits = (long double)n * paints * (long double)(dl->period_ns + 6 * dl->period_sigma_ns);
+    if (spill + sw + waits > 4.0e18L) return fail(c, DOSE_EINVAL, "delivery clock would overflow");
+    return DOSE_OK;
+}
+
+// Replace the plan of c and upload the spots.
+int load_plan(dose_ctx *c, const dose_spot *spots, int64_t n, int n_fields, cudaStream_t st)
+{
     int rc;
     if ((rc = use_device(c))) return rc;
     free_plan(c);
+    const int P = c->g->n_phases;
     std::vector<float4> sp(n);
     std::vector<unsigned long long> pr(n);
     std::vector<int> la(n), fi(n);
@@ -507,28 +517,130 @@ int dose_add_spots(dose_ctx *c, const dose_spot *spots, int64_t n, const dose_de
         free_plan(c);
         return rc;
     }
-    cudaStream_t st = S(stream);
+    if (!c->tl_used && ((rc = dalloc_t(c, &c->tl_used, 1)) || (rc = dalloc_t(c, &c->tl_status, 1)))) return rc;
     CK(c, cudaMemcpyAsync(c->spot, sp.data(), n * sizeof(float4), cudaMemcpyHostToDevice, st));
     CK(c, cudaMemcpyAsync(c->protons, pr.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
     CK(c, cudaMemcpyAsync(c->layer, la.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(c, cudaMemcpyAsync(c->field, fi.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(c, cudaMemsetAsync(c->pp, 0, (size_t)n * P * sizeof(unsigned long long), st));
+    CK(c, cudaMemsetAsync(c->tl_status, 0, sizeof(int), st));
+    return DOSE_OK;
+}
+
+TimelineArgs timeline_args(dose_ctx *c, const dose_delivery &d)
+{
+    TimelineArgs a;
+    a.protons = c->protons; a.layer = c->layer; a.field = c->field;
+    a.n_spots = c->n_spots; a.n_fields = c->n_fields;
+    a.d = d; a.spread = nullptr; a.trial = 0;
+    a.pp = c->pp; a.field_end = c->field_end; a.start_out = c->start_phase;
+    a.used = c->tl_used; a.status = c->tl_status;
+    return a;
+}
+
+// Launch the timelines of `args` (one block each) from c's argument buffer.
+int launch_timelines(dose_ctx *c, const std::vector<TimelineArgs> &args, cudaStream_t st)
+{
+    int rc;
+    if ((int)args.size() > c->cap_tl) {
+        if (c->tl_args) { dfree(c, c->tl_args); c->tl_args = nullptr; c->cap_tl = 0; }
+        if ((rc = dalloc_t(c, &c->tl_args, args.size()))) return rc;
+        c->cap_tl = (int)args.size();
+    }
+    CK(c, cudaMemcpyAsync(c->tl_args, args.data(), args.size() * sizeof(TimelineArgs), cudaMemcpyHostToDevice, st));
+    k_timeline<<<(unsigned)args.size(), kMaxFields, 0, st>>>(c->tl_args);
+    CK(c, cudaGetLastError());
+    return DOSE_OK;
+}
+
+// Wait for the stream and turn a timeline status into an error.
+int timeline_status(dose_ctx *c, dose_ctx *report, int trial, bool is_trial, cudaStream_t st)
+{
+    int rc, status = 0;
+    if ((rc = sync_stream(report, st))) return rc;
+    CK(report, cudaMemcpy(&status, c->tl_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status == 0) return DOSE_OK;
+    c->have_plan = false;
+    const char *why = status == 1 ? "sampled delivery breaks the progress conditions"
+                    : status == 2 ? "delivery makes no progress (fills deliver nothing)"
+                                  : "delivery clock overflow";
+    if (is_trial) return fail(report, DOSE_EINVAL, "trial %d: %s", trial, why);
+    return fail(report, DOSE_EINVAL, "%s", why);
+}
+
+}  // namespace
+
+int dose_add_spots(dose_ctx *c, const dose_spot *spots, int64_t n, const dose_delivery *dl, void *stream)
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    int n_fields = 0, rc;
+    unsigned long long total = 0;
+    if ((rc = check_spots(c, spots, n, &n_fields, &total))) return rc;
+    if (dl && (rc = check_delivery(c, dl, n, total))) return rc;
+    cudaStream_t st = S(stream);
+    if ((rc = load_plan(c, spots, n, n_fields, st))) return rc;
     if (dl) {
-        TimelineArgs a;
-        a.protons = c->protons; a.layer = c->layer; a.field = c->field; a.n_spots = (int)n;
-        a.n_phases = P; a.start_phase = dl->start_phase; a.gated = dl->gated;
-        a.gate_first = dl->gate_first; a.gate_last = dl->gate_last; a.repaints = dl->repaints;
-        a.tph = dl->period_ns / P; a.spot_switch = dl->spot_switch_ns; a.layer_switch = dl->layer_switch_ns;
-        a.discard = dl->gated ? dl->discard_ns : 0; a.rate = dl->rate_protons_per_s; a.seed = dl->seed;
-        a.pp = c->pp; a.field_end = c->field_end; a.start_out = c->start_phase; a.n_fields = n_fields;
-        k_timeline<<<1, 64, 0, st>>>(a);
-        CK(c, cudaGetLastError());
+        if ((rc = launch_timelines(c, {timeline_args(c, *dl)}, st))) return rc;
+        c->have_plan = true;
+        c->have_delivery = true;
+        if (dl->synchrotron && (rc = timeline_status(c, c, 0, false, st))) return rc;
     } else {
         CK(c, cudaMemcpyAsync(c->pp, c->protons, n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
         CK(c, cudaMemsetAsync(c->start_phase, 0, n_fields * sizeof(int), st));
         CK(c, cudaMemsetAsync(c->field_end, 0, n_fields * sizeof(long long), st));
+        c->have_plan = true;
     }
-    c->have_plan = true;
+    return DOSE_OK;
+}
+
+int dose_add_spots_trials(dose_ctx *const *ctxs, int n_trials, const dose_spot *spots, int64_t n,
+                          const dose_delivery *mean, const dose_delivery_spread *spread, uint64_t first_trial,
+                          void *stream)
+{
+    if (!ctxs || n_trials <= 0 || !ctxs[0]) return fail(nullptr, DOSE_EINVAL, "no contexts");
+    dose_ctx *c0 = ctxs[0];
+    if (!mean || !spread) return fail(c0, DOSE_EINVAL, "mean delivery and spread are required");
+    for (int k = 0; k < n_trials; ++k) {
+        if (!ctxs[k]) return fail(c0, DOSE_EINVAL, "context %d is NULL", k);
+        if (ctxs[k]->g->device != c0->g->device) return fail(c0, DOSE_EINVAL, "context %d is on another GPU", k);
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == ctxs[k]) return fail(c0, DOSE_EINVAL, "context %d appears twice", k);
+    }
+    const dose_delivery_spread &sp = *spread;
+    const int64_t sig[6] = {sp.spot_switch_sigma_ns, sp.layer_switch_sigma_ns, sp.discard_sigma_ns,
+                            sp.rate_sigma, sp.fill_protons_sigma, sp.extraction_limit_sigma_ns};
+    for (int64_t v : sig)
+        if (v < 0 || v > (1ll << 38)) return fail(c0, DOSE_EINVAL, "spread sigmas must be in 0..2^38");
+    if (sp.period_max_ns > sp.period_min_ns && (sp.period_step_ns <= 0 || sp.period_min_ns <= 0))
+        return fail(c0, DOSE_EINVAL, "period range needs a positive minimum and step");
+    int n_fields = 0, rc;
+    unsigned long long total = 0;
+    if ((rc = check_spots(c0, spots, n, &n_fields, &total))) return rc;
+    // the mean must be sound; sampled trials are checked in the kernel
+    dose_delivery worst = *mean;
+    if (sp.period_max_ns > sp.period_min_ns) worst.period_ns = sp.period_min_ns;
+    if ((rc = check_delivery(c0, &worst, n, total))) return rc;
+    cudaStream_t st = S(stream);
+    std::vector<TimelineArgs> args;
+    for (int k = 0; k < n_trials; ++k) {
+        dose_ctx *c = ctxs[k];
+        if (c->g->n_phases != c0->g->n_phases) return fail(c0, DOSE_EINVAL, "context %d has another phase count", k);
+        if ((rc = load_plan(c, spots, n, n_fields, st))) return rc;
+        args.push_back(timeline_args(c, *mean));
+    }
+    if (!c0->tl_spread && (rc = dalloc_t(c0, &c0->tl_spread, 1))) return rc;
+    CK(c0, cudaMemcpyAsync(c0->tl_spread, spread, sizeof(dose_delivery_spread), cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < n_trials; ++k) {
+        args[k].spread = c0->tl_spread;
+        args[k].trial = first_trial + (uint64_t)k;
+    }
+    if ((rc = launch_timelines(c0, args, st))) return rc;
+    for (int k = 0; k < n_trials; ++k) {
+        ctxs[k]->have_plan = true;
+        ctxs[k]->have_delivery = true;
+    }
+    for (int k = 0; k < n_trials; ++k)
+        if ((rc = timeline_status(ctxs[k], c0, (int)(first_trial + k), true, st))) return rc;
     return DOSE_OK;
 }
 
@@ -974,6 +1086,9 @@ int dose_read(dose_ctx *c, int what, int phase, void *dst, size_t bytes, int dst
     case DOSE_EMTM_STATS:
         if (!c->have_accum || c->accum_method != 0) return fail(c, DOSE_ESTATE, "no energy/mass-transfer accumulation");
         src = c->emtm_stats; need = 4 * sizeof(unsigned long long); break;
+    case DOSE_DELIVERY:
+        if (!c->have_plan || !c->have_delivery) return fail(c, DOSE_ESTATE, "no delivery simulation ran");
+        src = c->tl_used; need = sizeof(dose_delivery); break;
     case DOSE_HIST_PREFIX:
         if (!phase_ok()) return fail(c, DOSE_EINVAL, "phase out of range");
         if (!c->ph[phase].allocated || !c->ph[phase].prefix) return fail(c, DOSE_ESTATE, "phase %d was not run", phase);

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "dose.h"
 #include "engine.cuh"
 
 namespace dose {
@@ -28,20 +29,47 @@ __global__ void k_normalise(const NormJob *jobs);
 __global__ void k_debug_philox(const uint4 *ctr, const uint2 *key, uint4 *out, float *uni, int n);
 __global__ void k_debug_tables(const Tables *tab, float inv_ds, const float *e, int n, float *out);
 
-struct TimelineArgs {
+// Delivery parameters that keep the clock moving: every fill and every gate
+// window delivers at least one proton (shortest cycle mu - 6 sigma, the
+// Irwin-Hall bound, at least N ns).  Shared by the host checks and the
+// kernel's check of sampled trial deliveries.
+__host__ __device__ inline bool delivery_ok(const dose_delivery &d)
+{
+    if (d.n_phases <= 0 || d.repaints <= 0 || d.period_ns <= 0 || d.rate_protons_per_s == 0 ||
+        d.period_sigma_ns < 0 || d.period_sigma_ns > (1ll << 38) || d.spot_switch_ns < 0 ||
+        d.layer_switch_ns < 0 || d.discard_ns < 0 || d.start_phase >= d.n_phases || d.extraction_limit_ns < 0)
+        return false;
+    if (d.max_protons_per_paint > 0 && d.repaints != 1) return false;
+    if (d.synchrotron != 0 && d.synchrotron != 1) return false;
+    const long long tmin = d.period_ns - 6 * d.period_sigma_ns;
+    if (tmin < d.n_phases) return false;
+    const long long tph_min = tmin / d.n_phases;
+    const long long proton_ns = (long long)((1000000000ull + d.rate_protons_per_s - 1) / d.rate_protons_per_s);
+    if (d.gated) {
+        if (d.gate_first < 0 || d.gate_last >= d.n_phases || d.gate_first > d.gate_last) return false;
+        const long long window = (long long)(d.gate_last - d.gate_first + 1) * tph_min;
+        if (d.discard_ns >= window) return false;
+        if (d.synchrotron && window - d.discard_ns < proton_ns) return false;
+    }
+    if (d.synchrotron && d.extraction_limit_ns > 0 && d.extraction_limit_ns < proton_ns) return false;
+    return true;
+}
+
+struct TimelineArgs {                // one trial (or the single delivery) of a plan
     const unsigned long long *protons;
     const int *layer;
     const int *field;
-    int n_spots;
-    int n_phases, start_phase, gated, gate_first, gate_last, repaints;
-    long long tph, spot_switch, layer_switch, discard;
-    unsigned long long rate, seed;
+    int n_spots, n_fields;
+    dose_delivery d;                 // the delivery, or the mean of the trials
+    const dose_delivery_spread *spread;   // device; null: d as given
+    unsigned long long trial;
     unsigned long long *pp;          // n_phases x n_spots, zeroed by the caller
     long long *field_end;            // n_fields
     int *start_out;                  // n_fields
-    int n_fields;
+    dose_delivery *used;             // the delivery the clock ran (sampled for trials)
+    int *status;                     // 0; 1 sampled delivery invalid; 2 no progress; 3 clock overflow
 };
-__global__ void k_timeline(TimelineArgs a);
+__global__ void k_timeline(const TimelineArgs *args);
 
 struct EmtmArgs {
     const float *dose;               // n_phases x nvox

@@ -22,7 +22,8 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "lib
 DOSE_OK, DOSE_EINVAL, DOSE_ENOMEM, DOSE_ECUDA, DOSE_ETIMEOUT, DOSE_ESTEPLIMIT, DOSE_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
 (DOSE_PHASE_DOSE, DOSE_DENSITY, DOSE_ACCUM, DOSE_TALLY_I64, DOSE_SUBPLAN, DOSE_ENERGY_LEDGER,
- DOSE_STATUS, DOSE_START_PHASE, DOSE_FIELD_END_NS, DOSE_EMTM_STATS, DOSE_HIST_PREFIX) = range(11)
+ DOSE_STATUS, DOSE_START_PHASE, DOSE_FIELD_END_NS, DOSE_EMTM_STATS, DOSE_HIST_PREFIX,
+ DOSE_DELIVERY) = range(12)
 DOSE_PHYS_STRAGGLING, DOSE_PHYS_MCS, DOSE_PHYS_NUCLEAR, DOSE_PHYS_ALL = 1, 2, 4, 7
 (DOSE_OPT_PHYSICS, DOSE_OPT_MAX_STEPS, DOSE_OPT_BLOCK, DOSE_OPT_BLOCKS_PER_SM, DOSE_OPT_CHUNK,
  DOSE_OPT_TIMEOUT_MS, DOSE_OPT_FAIL_ALLOC_AFTER, DOSE_OPT_REGISTERS) = range(8)
@@ -47,7 +48,16 @@ class dose_delivery(C.Structure):
                 ("gate_first", C.c_int32), ("gate_last", C.c_int32), ("repaints", C.c_int32),
                 ("period_ns", C.c_int64), ("period_sigma_ns", C.c_int64),
                 ("spot_switch_ns", C.c_int64), ("layer_switch_ns", C.c_int64),
-                ("discard_ns", C.c_int64), ("rate_protons_per_s", C.c_uint64), ("seed", C.c_uint64)]
+                ("discard_ns", C.c_int64), ("rate_protons_per_s", C.c_uint64), ("seed", C.c_uint64),
+                ("synchrotron", C.c_int32), ("reserved", C.c_int32), ("fill_protons", C.c_uint64),
+                ("extraction_limit_ns", C.c_int64), ("max_protons_per_paint", C.c_uint64)]
+
+
+class dose_delivery_spread(C.Structure):
+    _fields_ = [("period_min_ns", C.c_int64), ("period_max_ns", C.c_int64), ("period_step_ns", C.c_int64),
+                ("spot_switch_sigma_ns", C.c_int64), ("layer_switch_sigma_ns", C.c_int64),
+                ("discard_sigma_ns", C.c_int64), ("rate_sigma", C.c_int64), ("fill_protons_sigma", C.c_int64),
+                ("extraction_limit_sigma_ns", C.c_int64)]
 
 
 class dose_job(C.Structure):
@@ -73,7 +83,7 @@ class dose_dvf_grid(C.Structure):
                 ("post", C.c_float * 16)]
 
 
-assert C.sizeof(dose_spot) == 32 and C.sizeof(dose_job) == 64
+assert C.sizeof(dose_spot) == 32 and C.sizeof(dose_job) == 64 and C.sizeof(dose_delivery) == 112
 assert C.sizeof(dose_server_config) == 56 and C.sizeof(dose_request) == 32
 
 
@@ -109,6 +119,7 @@ def _load():
         "dose_run_phase_noalloc": ([P, I, I, I, F, F, F, P, P, P, I, U64, U64, P, P, P], I),
         "dose_debug_tables": ([P, I, P, P], I),
         "dose_decode_dvf": ([P, P, P, I, P, P, P], I),
+        "dose_add_spots_trials": ([P, I, P, I64, P, P, U64, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -423,8 +434,31 @@ def spots_array(plan):
 def delivery_struct(d):
     s = dose_delivery()
     for name, _ in dose_delivery._fields_:
-        setattr(s, name, int(getattr(d, name)))
+        setattr(s, name, int(getattr(d, name, 0)))
     return s
+
+
+def spread_struct(d):
+    s = dose_delivery_spread()
+    for name, _ in dose_delivery_spread._fields_:
+        setattr(s, name, int(getattr(d, name, 0)))
+    return s
+
+
+def dose_add_spots_trials(ctxs, spots, mean, spread, first_trial=0, stream=None):
+    """Load ``spots`` into every context of ``ctxs`` and run the delivery
+    simulation of trials first_trial.. (one per context) in one launch."""
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    _check(_lib.dose_add_spots_trials(arr, len(ctxs), C.cast(spots, C.c_void_p), len(spots), C.byref(mean),
+                                      C.byref(spread), int(first_trial), _stream(stream)), ctxs[0])
+
+
+def read_delivery(ctx):
+    """The delivery the context's timeline ran, as a dict."""
+    buf = np.zeros(C.sizeof(dose_delivery), np.uint8)
+    dose_read(ctx, DOSE_DELIVERY, 0, buf)
+    d = dose_delivery.from_buffer_copy(buf.tobytes())
+    return {name: getattr(d, name) for name, _ in dose_delivery._fields_}
 
 
 def make_jobs(specs):

@@ -52,12 +52,17 @@ def test_argument_validation_without_device(libdose):
     assert lib.dose_add_spots(None, None, 0, None, None) == D.DOSE_EINVAL
     assert lib.dose_accumulate_subvoxel(None, 0, None, None, 0, None, 0, 0, None) == D.DOSE_EINVAL
     assert lib.dose_debug_philox(None, None, None, 0, None) == D.DOSE_EINVAL
+    assert lib.dose_add_spots_trials(None, 0, None, 0, None, None, 0, None) == D.DOSE_EINVAL
+    assert lib.dose_decode_dvf(None, None, None, 0, None, None, None) == D.DOSE_EINVAL
     lib.dose_destroy(None)
 
 
 def test_structs_match_the_header(libdose):
     D = libdose
     assert C.sizeof(D.dose_spot) == 32
-    assert C.sizeof(D.dose_delivery) == 6 * 4 + 5 * 8 + 2 * 8
+    assert C.sizeof(D.dose_delivery) == 6 * 4 + 5 * 8 + 2 * 8 + 2 * 4 + 3 * 8
+    assert D.dose_delivery.max_protons_per_paint.offset == 104
+    assert C.sizeof(D.dose_delivery_spread) == 9 * 8
+    assert C.sizeof(D.dose_dvf_grid) == 3 * 4 + 4 * 3 * 4 + 2 * 16 * 4
     assert C.sizeof(D.dose_job) == 64
     assert D.dose_job.shift_mm.offset == 52
