@@ -49,6 +49,9 @@ def _args():
     p.add_argument("--no-4d", action="store_true", help="skip the 4D-plan measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement")
+    p.add_argument("--no-trials", action="store_true", help="skip the uncertainty-trials measurement")
+    p.add_argument("--histories-trial", type=int, default=4_000_000,
+                   help="histories per phase of each uncertainty trial")
     p.add_argument("--serve-window", type=float, default=5.0, help="seconds of Poisson arrivals")
     p.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
     p.add_argument("--serve-budget-gb", type=float, default=150.0, help="device memory for request slots")
@@ -278,6 +281,78 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
             "workload": "synthetic 4DCT 10 x 256x256x160 at 1x1x2.5 mm, 3000 spots / 20 layers 70-180 MeV, "
                         f"{n_per_phase:.0e} histories per phase, EMTM 2x2x5 onto phase 0",
             "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}}
+
+
+# ------------------------------------------------------------------ uncertainty trials
+def _bench_trials(D, torch, stream, n_per_phase, n_trials=25, seed=SEED):
+    """The uncertainty study of Sec. 2.B on the synthetic 4DCT: 25 trials,
+    each drawing its start phase (random), breathing period (3-7 s, whole
+    seconds) and synchrotron parameters (App. A fill model: 1.25e10 protons
+    (2 nC) per fill, 8 s extraction limit, 70 ms discard, 2 s reset, 2 ms
+    spot switch, 1e9 p/s, each with a Gaussian spread) as one launch of the
+    timeline, then every trial's phase subplans transported in ONE ragged
+    persistent launch (n_per_phase histories per phase with protons), then
+    each trial's EMTM onto phase 0.  Reported: seconds for the whole study
+    and the transport's histories/s."""
+    from paper_1809_03927_gb300 import workloads as W
+    ph, dvf, geo = W.phantom_4dct()
+    plan = W.tumour_plan(geo, ph.origin)
+    nx, ny, nz = ph.n
+    S_ = 1_000_000_000
+    mean = W.Delivery(seed=seed, start_phase=-1, synchrotron=1, fill_protons=12_500_000_000,
+                      extraction_limit_ns=8 * S_, discard_ns=70_000_000, layer_switch_ns=2 * S_,
+                      spot_switch_ns=2_000_000, rate_protons_per_s=1_000_000_000)
+    spread = W.DeliverySpread(period_min_ns=3 * S_, period_max_ns=7 * S_, period_step_ns=S_,
+                              spot_switch_sigma_ns=200_000, layer_switch_sigma_ns=100_000_000,
+                              discard_sigma_ns=5_000_000, rate_sigma=50_000_000,
+                              fill_protons_sigma=500_000_000, extraction_limit_sigma_ns=300_000_000)
+    hu_dev = torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda()
+    dvf_dev = torch.from_numpy(dvf).cuda()
+    del dvf
+    base = D.dose_create_grid(nx, ny, nz, *ph.d, ph.origin, ph.n_phases, hu_dev, ph.beam_dir, stream)
+    views = []
+    spots = D.spots_array(plan)
+    try:
+        views = [D.dose_create_view(base) for _ in range(n_trials)]
+
+        def study():
+            D.dose_add_spots_trials(views, spots, D.delivery_struct(mean), D.spread_struct(spread), 0, stream)
+            jobs = []
+            for k, v in enumerate(views):
+                pp = D.dose_read(v, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64))
+                for p in range(ph.n_phases):
+                    if pp[p].sum():
+                        jobs.append(dict(ctx=v, phase=p, n_histories=n_per_phase, seed=seed + k))
+                    else:
+                        D.dose_set_phase_dose(v, p, torch.zeros(nx * ny * nz, dtype=torch.float32, device="cuda"),
+                                              stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            D.dose_run_batch(D.make_jobs(jobs), stream)
+            e1.record(stream)
+            for v in views:
+                D.dose_accumulate_subvoxel(v, 0, (2, 2, 5), dvf=dvf_dev, stream=stream)
+            torch.cuda.synchronize()
+            return len(jobs), e0.elapsed_time(e1) / 1e3
+
+        D.dose_add_spots_trials(views, spots, D.delivery_struct(mean), D.spread_struct(spread), 0, stream)
+        pp0 = D.dose_read(views[0], D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
+        tune = D.dose_autotune(views[0], int(np.argmax(pp0)), n_per_phase, 2_000_000, seed, stream)
+        study()                                    # warm-up (and first allocation of the views)
+        t0 = time.perf_counter()
+        n_jobs, mc_s = study()
+        wall = time.perf_counter() - t0
+        periods = sorted({int(D.read_delivery(v)["period_ns"]) // S_ for v in views})
+    finally:
+        for v in views:
+            D.dose_destroy(v)
+        D.dose_destroy(base)
+    return {"s_per_study": wall, "trials": n_trials, "phase_jobs": n_jobs, "transport_s": mc_s,
+            "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]},
+            "transport_histories_per_s": n_jobs * n_per_phase / mc_s, "periods_s_drawn": periods,
+            "workload": f"{n_trials} uncertainty trials of the synthetic 4DCT plan (synchrotron fills, "
+                        f"period U{{3..7}} s, Gaussian machine parameters), {n_per_phase:.0e} histories per "
+                        "phase with protons, all trials' phases in one ragged launch, EMTM 2x2x5 per trial"}
 
 
 # ------------------------------------------------------------------ ragged batch
@@ -598,6 +673,8 @@ def run_engine(args):
         line["four_d"] = _bench_4d(D, torch, stream, args.histories_4d, 2, SEED)
     if not args.no_ragged:
         line["ragged_batch"] = _bench_ragged(D, torch, stream)
+    if not args.no_trials:
+        line["uncertainty_trials"] = _bench_trials(D, torch, stream, args.histories_trial)
     if not args.no_serve:
         line["serving"] = _bench_serving(D, torch, stream, args.serve_window, args.serve_rate,
                                          int(args.serve_budget_gb * 1e9))

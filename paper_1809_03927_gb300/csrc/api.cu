@@ -740,24 +740,30 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
     if (work) {
         CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
         CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
-        const size_t smem = kSmemTransport;
         auto kern = c0->regs ? k_transport_r64 : k_transport;
         if (!c0->regs && c0->block > 512)
             return fail(c0, DOSE_EINVAL, "block %d needs the 64-register variant (DOSE_OPT_REGISTERS 1)", c0->block);
-        CK(c0, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CK(c0, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransportMax));
         int sms = 0;
         CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->g->device));
+        // stage the job table in shared memory unless that costs resident blocks
+        const size_t smem_plain = transport_smem(kMaxStagedJobs + 1);
+        int fit_plain = 0, fit_staged = 0;
+        CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_plain, kern, c0->block, smem_plain));
+        if ((int)tj.size() <= kMaxStagedJobs)
+            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_staged, kern, c0->block,
+                                                                 transport_smem((int)tj.size())));
+        const int stage = fit_staged > 0 && fit_staged >= fit_plain ? 1 : 0;
+        const size_t smem = stage ? transport_smem((int)tj.size()) : smem_plain;
         int per_sm = c0->blocks_per_sm;
-        if (per_sm <= 0) {
-            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c0->block, smem));
-            if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
-        }
+        if (per_sm <= 0) per_sm = stage ? fit_staged : fit_plain;
+        if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
         const unsigned long long warps = (unsigned long long)sms * per_sm * (c0->block / 32);
         unsigned chunk = c0->chunk;
         // keep at least ~4 pulls per warp so the tail stays short
         while (chunk > 32 && (unsigned long long)chunk * warps * 4 > work) chunk >>= 1;
         kern<<<sms * per_sm, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
-                                                    tab.dev, tab.inv_ds, chunk);
+                                                    tab.dev, tab.inv_ds, chunk, stage);
         CK(c0, cudaGetLastError());
     }
     if (!nj.empty()) {
@@ -806,8 +812,8 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
     j.shift_mm[0] = j.shift_mm[1] = j.shift_mm[2] = 0.0f;
     c->blocks_per_sm = 0;
     // the occupancy query needs the kernels' dynamic shared-memory limit set
-    CK(c, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransport));
-    CK(c, cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransport));
+    CK(c, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransportMax));
+    CK(c, cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransportMax));
     // allocate the phase's histories once; each trial then only transports
     j.flags = DOSE_JOB_CLEAR; j.hist_begin = 0; j.hist_end = 0;
     if ((rc = dose_run_batch(&j, 1, stream))) goto done;
@@ -816,7 +822,7 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
             if (!regs && b > 512) continue;
             int fits = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, regs ? k_transport_r64 : k_transport, b,
-                                                              kSmemTransport) != cudaSuccess || fits <= 0) {
+                                                              transport_smem(1)) != cudaSuccess || fits <= 0) {
                 cudaGetLastError();
                 continue;
             }

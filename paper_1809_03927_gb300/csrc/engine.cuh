@@ -72,11 +72,19 @@ struct TJob {
     unsigned long long work_begin;      // offset in the launch's work index
 };
 
-// A transport launch with at most kSmemJobs jobs stages their descriptors
-// and per-job counters (escaped, removed, steps, flags) in shared memory
-// after the tables; larger launches read them from global memory.
-constexpr int kSmemJobs = 32;
-constexpr size_t kSmemTransport = kSmemTables + kSmemJobs * sizeof(TJob) + kSmemJobs * 4 * sizeof(unsigned long long);
+// A transport launch may stage the descriptors and per-job counters
+// (escaped, removed, steps, flags) of up to kMaxStagedJobs jobs in shared
+// memory after the tables; transport_smem(n) is then its dynamic shared
+// memory.  The launcher stages only where that costs no resident blocks,
+// else passes transport_smem(kMaxStagedJobs + 1) (the tables alone) and
+// the kernel reads the jobs from global memory.
+constexpr int kMaxStagedJobs = 256;
+static_assert(sizeof(TJob) % 8 == 0, "job counters follow the descriptors 8-byte aligned");
+__host__ __device__ constexpr size_t transport_smem(int n_jobs)
+{
+    return kSmemTables + (n_jobs <= kMaxStagedJobs ? (size_t)n_jobs * (sizeof(TJob) + 4 * sizeof(unsigned long long)) : 0);
+}
+constexpr size_t kSmemTransportMax = transport_smem(kMaxStagedJobs);
 
 struct AllocJob {
     const unsigned long long *protons;  // n_spots, this phase's subplan

@@ -19,12 +19,15 @@ int set_phase_zero(dose_ctx *c, int phase, void *stream);
 
 __global__ void k_density(const int16_t *hu, float *rho, long long n, const Tables *tab);
 __global__ void k_alloc(const AllocJob *jobs);
+// stage != 0: the launch gives transport_smem(n_jobs) bytes and the job
+// table is staged in shared memory; 0: transport_smem(kMaxStagedJobs + 1)
+// (tables only) and the jobs are read from global memory.
 __global__ void k_transport(const TJob *jobs, int n_jobs, unsigned long long total,
                             unsigned long long *counter, const Tables *gtab, float inv_ds,
-                            unsigned chunk);
+                            unsigned chunk, int stage);
 __global__ void k_transport_r64(const TJob *jobs, int n_jobs, unsigned long long total,
                                 unsigned long long *counter, const Tables *gtab, float inv_ds,
-                                unsigned chunk);
+                                unsigned chunk, int stage);
 __global__ void k_normalise(const NormJob *jobs);
 __global__ void k_debug_philox(const uint4 *ctr, const uint2 *key, uint4 *out, float *uni, int n);
 __global__ void k_debug_tables(const Tables *tab, float inv_ds, const float *e, int n, float *out);

@@ -179,13 +179,13 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                                                unsigned long long total,
                                                unsigned long long *__restrict__ counter,
                                                const Tables *__restrict__ gtab, float inv_ds,
-                                               unsigned chunk)
+                                               unsigned chunk, int stage)
 {
     extern __shared__ int4 smem[];
     TJob *s_jobs = reinterpret_cast<TJob *>(reinterpret_cast<char *>(smem) + kSmemTables);
+    const bool staged = stage != 0;                   // the launch gave transport_smem(n_jobs)
     unsigned long long *s_led = reinterpret_cast<unsigned long long *>(
-        reinterpret_cast<char *>(smem) + kSmemTables + kSmemJobs * sizeof(TJob));
-    const bool staged = n_jobs <= kSmemJobs;
+        reinterpret_cast<char *>(smem) + kSmemTables + (staged ? n_jobs : 0) * sizeof(TJob));
     {
         const int4 *src = reinterpret_cast<const int4 *>(gtab);
         for (int i = threadIdx.x; i < (int)(kSmemTables / 16); i += blockDim.x) smem[i] = src[i];
@@ -477,17 +477,17 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
 __global__ void __launch_bounds__(512, 1)
 k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
             unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
-            unsigned chunk)
+            unsigned chunk, int stage)
 {
-    transport_body(jobs, n_jobs, total, counter, gtab, inv_ds, chunk);
+    transport_body(jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
 }
 
 __global__ void __launch_bounds__(1024, 1)
 k_transport_r64(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
                 unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab,
-                float inv_ds, unsigned chunk)
+                float inv_ds, unsigned chunk, int stage)
 {
-    transport_body(jobs, n_jobs, total, counter, gtab, inv_ds, chunk);
+    transport_body(jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
 }
 
 // ------------------------------------------------------------- self-tests
