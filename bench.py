@@ -459,13 +459,6 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
     nx, ny, nz = ph.n
     hu_dev = torch.from_numpy(np.ascontiguousarray(ph.hu)).cuda()
     dvf_dev = torch.from_numpy(dvf).cuda()
-    pull_dev = torch.from_numpy(W.reference_to_phase_field(dvf)).cuda()
-    # the registrations as a DIR system would store them: each phase's
-    # field on a grid of every other CT voxel centre (2 x 2 x 5 mm)
-    reg_grid = dict(n=(nx // 2, ny // 2, nz // 2), start_mm=tuple(ph.origin[k] + 0.5 * ph.d[k] for k in range(3)),
-                    spacing_mm=tuple(2.0 * v for v in ph.d), row_cos=(1, 0, 0), col_cos=(0, 1, 0))
-    reg_delta = [torch.from_numpy(np.ascontiguousarray(np.moveaxis(dvf[p][:, ::2, ::2, ::2], 0, -1))).cuda()
-                 for p in range(ph.n_phases)]
     del dvf
     reqs = _requests(window_s, rate)
     base = D.dose_create_grid(nx, ny, nz, *ph.d, ph.origin, ph.n_phases, hu_dev, ph.beam_dir, stream)
