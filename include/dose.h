@@ -187,6 +187,16 @@ int dose_create_grid(dose_ctx **out, int nx, int ny, int nz, float dx_mm, float 
  * many dose requests over one resident 4DCT need one copy of the CT.        */
 int dose_create_view(dose_ctx *base, dose_ctx **out);
 
+/* Beam direction of one field of the plan (multi-field plans): the field's
+ * spots enter along beam_dir (a unit grid-axis vector, like the grid's own
+ * beam_dir) through the grid face it points into, and their x_mm, y_mm are
+ * on that field's two lateral axes, lower axis first.  beam_dir = NULL
+ * restores the grid's beam.  Applies to the loaded plan and to later ones;
+ * views start with their base's settings.  The histories of a phase are
+ * still allocated over all its spots together (each history keeps its
+ * Philox stream), so a multi-field dose is the sum of its fields' parts.  */
+int dose_set_field_beam(dose_ctx *c, int field, const float beam_dir[3]);
+
 /* Load the plan (host array of n spots) and run the delivery simulation on
  * the device (Sec. 2.B): the per-phase subplans (protons per phase and
  * spot).  delivery = NULL puts every spot wholly on phase 0 (a static, 3D

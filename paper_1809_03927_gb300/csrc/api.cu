@@ -80,6 +80,8 @@ struct dose_ctx {
     long long *field_end = nullptr;
     bool have_plan = false;
     bool have_delivery = false;              // the plan ran through the timeline
+    signed char field_dir[64];               // per field: 2 axis + (sign > 0), -1 = the grid's beam
+    unsigned char *spot_dir = nullptr;       // per spot beam code, null when every field uses the grid's
     TimelineArgs *tl_args = nullptr;         // device timeline arguments, cap_tl entries
     int cap_tl = 0;
     dose_delivery_spread *tl_spread = nullptr;
@@ -255,7 +257,8 @@ int ensure_workspace(dose_ctx *c, int n_jobs)
 void free_plan(dose_ctx *c)
 {
     dfree(c, c->spot); dfree(c, c->protons); dfree(c, c->layer); dfree(c, c->field);
-    dfree(c, c->pp); dfree(c, c->start_phase); dfree(c, c->field_end);
+    dfree(c, c->pp); dfree(c, c->start_phase); dfree(c, c->field_end); dfree(c, c->spot_dir);
+    c->spot_dir = nullptr;
     c->spot = nullptr; c->protons = nullptr; c->layer = nullptr; c->field = nullptr;
     c->pp = nullptr; c->start_phase = nullptr; c->field_end = nullptr;
     for (auto &P : c->ph) {
@@ -351,6 +354,7 @@ int dose_create_grid(dose_ctx **out, int nx, int ny, int nz, float dx_mm, float 
     if (nz_count != 1) return fail(nullptr, DOSE_EINVAL, "beam_dir must be a unit axis vector");
 
     dose_ctx *c = new dose_ctx;
+    std::memset(c->field_dir, -1, sizeof c->field_dir);
     c->g = new Grid;
     Grid &g = *c->g;
     g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
@@ -405,6 +409,7 @@ int dose_create_view(dose_ctx *base, dose_ctx **out)
     dose_ctx *c = new dose_ctx;
     c->g = base->g;
     c->g->refs.fetch_add(1);
+    std::memcpy(c->field_dir, base->field_dir, sizeof c->field_dir);
     c->ph.resize(c->g->n_phases);
     c->physics = base->physics;
     c->max_steps = base->max_steps;
@@ -492,6 +497,26 @@ int check_delivery(dose_ctx *c, const dose_delivery *dl, int64_t n, unsigned lon
     return DOSE_OK;
 }
 
+// Per-spot beam codes from the fields' directions (none when every field of
+// the plan enters along the grid's beam).
+int upload_spot_dirs(dose_ctx *c, const int *field, cudaStream_t st)
+{
+    bool any = false;
+    for (int s = 0; s < c->n_spots; ++s) any |= c->field_dir[field[s]] >= 0;
+    dfree(c, c->spot_dir);
+    c->spot_dir = nullptr;
+    if (!any) return DOSE_OK;
+    const unsigned char grid_code = (unsigned char)(2 * c->g->beam_axis + (c->g->beam_sign > 0 ? 1 : 0));
+    std::vector<unsigned char> code(c->n_spots);
+    for (int s = 0; s < c->n_spots; ++s)
+        code[s] = c->field_dir[field[s]] >= 0 ? (unsigned char)c->field_dir[field[s]] : grid_code;
+    int rc;
+    if ((rc = dalloc_t(c, &c->spot_dir, (size_t)c->n_spots))) return rc;
+    // from pageable memory: returns once the bytes are staged
+    CK(c, cudaMemcpyAsync(c->spot_dir, code.data(), code.size(), cudaMemcpyHostToDevice, st));
+    return DOSE_OK;
+}
+
 // Replace the plan of c and upload the spots.
 int load_plan(dose_ctx *c, const dose_spot *spots, int64_t n, int n_fields, cudaStream_t st)
 {
@@ -524,7 +549,7 @@ int load_plan(dose_ctx *c, const dose_spot *spots, int64_t n, int n_fields, cuda
     CK(c, cudaMemcpyAsync(c->field, fi.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(c, cudaMemsetAsync(c->pp, 0, (size_t)n * P * sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(c->tl_status, 0, sizeof(int), st));
-    return DOSE_OK;
+    return upload_spot_dirs(c, fi.data(), st);
 }
 
 TimelineArgs timeline_args(dose_ctx *c, const dose_delivery &d)
@@ -569,6 +594,30 @@ int timeline_status(dose_ctx *c, dose_ctx *report, int trial, bool is_trial, cud
 }
 
 }  // namespace
+
+int dose_set_field_beam(dose_ctx *c, int field, const float beam_dir[3])
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (field < 0 || field >= kMaxFields) return fail(c, DOSE_EINVAL, "field %d outside 0..%d", field, kMaxFields - 1);
+    signed char code = -1;
+    if (beam_dir) {
+        int axis = -1, n = 0, sign = 1;
+        for (int k = 0; k < 3; ++k) {
+            if (beam_dir[k] == 1.0f || beam_dir[k] == -1.0f) { axis = k; sign = beam_dir[k] > 0 ? 1 : -1; ++n; }
+            else if (beam_dir[k] != 0.0f) return fail(c, DOSE_EINVAL, "beam_dir must be a unit axis vector");
+        }
+        if (n != 1) return fail(c, DOSE_EINVAL, "beam_dir must be a unit axis vector");
+        code = (signed char)(2 * axis + (sign > 0 ? 1 : 0));
+    }
+    c->field_dir[field] = code;
+    if (!c->have_plan) return DOSE_OK;
+    // re-derive the loaded plan's spot codes
+    std::vector<int> fi(c->n_spots);
+    int rc;
+    if ((rc = use_device(c))) return rc;
+    CK(c, cudaMemcpy(fi.data(), c->field, fi.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    return upload_spot_dirs(c, fi.data(), nullptr);
+}
 
 int dose_add_spots(dose_ctx *c, const dose_spot *spots, int64_t n, const dose_delivery *dl, void *stream)
 {
@@ -710,10 +759,9 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
             t.nx = g.n[0]; t.ny = g.n[1]; t.nz = g.n[2];
             t.dx = g.d[0]; t.dy = g.d[1]; t.dz = g.d[2];
             t.idx = 1.0f / g.d[0]; t.idy = 1.0f / g.d[1]; t.idz = 1.0f / g.d[2];
-            const int a = g.beam_axis, b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
-            t.ob = g.origin[b] + J.shift_mm[b];
-            t.oc = g.origin[cc] + J.shift_mm[cc];
-            t.beam_axis = a; t.beam_sign = g.beam_sign;
+            for (int k = 0; k < 3; ++k) t.o[k] = g.origin[k] + J.shift_mm[k];
+            t.spot_dir = c->spot_dir;
+            t.beam_axis = g.beam_axis; t.beam_sign = g.beam_sign;
             t.spr_scale = J.spr_scale; t.physics = c->physics; t.max_steps = c->max_steps;
             t.key0 = (unsigned)J.seed; t.key1 = (unsigned)(J.seed >> 32); t.stream = (unsigned)J.phase;
             t.hist_begin = J.hist_begin; t.work_begin = work;

@@ -62,7 +62,8 @@ struct TJob {
     int nx, ny, nz;
     float dx, dy, dz;
     float idx, idy, idz;                // 1 / voxel sizes
-    float ob, oc;                       // lateral patient->grid offsets (origin + shift)
+    float o[3];                         // patient->grid offsets per axis (origin + shift)
+    const unsigned char *spot_dir;      // per spot: 2 axis + (sign > 0), or null: beam_axis/sign
     int beam_axis, beam_sign;
     float spr_scale;
     unsigned physics;

@@ -196,8 +196,8 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
     t.spot = d_spot; t.wh = a.wh; t.prefix = a.prefix; t.n_spots = n_spots;
     t.nx = nx; t.ny = ny; t.nz = nz; t.dx = dx_mm; t.dy = dy_mm; t.dz = dz_mm;
     t.idx = 1.0f / dx_mm; t.idy = 1.0f / dy_mm; t.idz = 1.0f / dz_mm;
-    const int b = axis == 0 ? 1 : 0, c = axis == 2 ? 1 : 2;
-    t.ob = origin_mm[b]; t.oc = origin_mm[c];
+    t.o[0] = origin_mm[0]; t.o[1] = origin_mm[1]; t.o[2] = origin_mm[2];
+    t.spot_dir = nullptr;
     t.beam_axis = axis; t.beam_sign = sign;
     t.spr_scale = 1.0f; t.physics = DOSE_PHYS_ALL; t.max_steps = 20000;
     t.key0 = (unsigned)seed; t.key1 = (unsigned)(seed >> 32); t.stream = 0;

@@ -269,9 +269,15 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                         make_uint4(0u, (unsigned)h, (unsigned)(h >> 32), J.stream), J.key0, J.key1));
                     const float2 z = box_muller(u.u[0], u.u[1]);
                     eta = -__logf(u.u[2]);
-                    const float lb = sp.x - J.ob + sp.w * z.x;
-                    const float lc = sp.y - J.oc + sp.w * z.y;
-                    const int ax = J.beam_axis, sg = J.beam_sign;
+                    // the spot's field may enter along its own grid axis
+                    int ax = J.beam_axis, sg = J.beam_sign;
+                    if (J.spot_dir) {
+                        const unsigned code = J.spot_dir[a];
+                        ax = (int)(code >> 1);
+                        sg = (code & 1u) ? 1 : -1;
+                    }
+                    const float lb = sp.x - J.o[ax == 0 ? 1 : 0] + sp.w * z.x;
+                    const float lc = sp.y - J.o[ax == 2 ? 1 : 2] + sp.w * z.y;
                     const int nx = J.nx, ny = J.ny, nz = J.nz;
                     const float dx = J.dx, dy = J.dy, dz = J.dz;
                     bool inside;

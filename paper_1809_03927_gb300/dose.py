@@ -120,6 +120,7 @@ def _load():
         "dose_debug_tables": ([P, I, P, P], I),
         "dose_decode_dvf": ([P, P, P, I, P, P, P], I),
         "dose_add_spots_trials": ([P, I, P, I64, P, P, U64, P], I),
+        "dose_set_field_beam": ([P, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -222,6 +223,13 @@ def dose_add_spots(ctx, spots, delivery=None, stream=None):
     """``spots``: a ``dose_spot`` ctypes array; ``delivery``: ``dose_delivery`` or None."""
     dl = C.byref(delivery) if delivery is not None else None
     _check(_lib.dose_add_spots(ctx, C.cast(spots, C.c_void_p), len(spots), dl, _stream(stream)), ctx)
+
+
+def dose_set_field_beam(ctx, field, beam_dir):
+    """Field ``field`` enters along the grid-axis vector ``beam_dir`` (None:
+    the grid's beam)."""
+    d = _f3(beam_dir) if beam_dir is not None else None
+    _check(_lib.dose_set_field_beam(ctx, int(field), d), ctx)
 
 
 def dose_run_phase(ctx, phase, n_histories, seed, spr_scale=1.0, shift_mm=None, stream=None):
