@@ -167,8 +167,11 @@ enum {
     DOSE_OPT_TIMEOUT_MS = 5,      /* host wait bound for dose_read (default 600000) */
     DOSE_OPT_FAIL_ALLOC_AFTER = 6,/* test hook: the n-th later device allocation
                                      of this context fails (-1 = off)            */
-    DOSE_OPT_REGISTERS = 7        /* transport register budget: 0 = up to 128 per
+    DOSE_OPT_REGISTERS = 7,       /* transport register budget: 0 = up to 128 per
                                      thread (blocks <= 512), 1 = 64 (blocks <= 1024) */
+    DOSE_OPT_MATERIAL_GRID = 8    /* 1: the transport reads a per-voxel (density, SPR)
+                                     grid (8 B per voxel per phase, built once per grid
+                                     on first use) instead of HU + table; same results */
 };
 
 /* Create a context holding a voxel grid of `n_phases` HU volumes (Sec. 2.A:
@@ -379,8 +382,9 @@ int dose_read(dose_ctx *c, int what, int phase, void *dst, size_t bytes, int dst
  * n_histories-history run of `phase` under each launch shape -- register
  * budget (DOSE_OPT_REGISTERS 0 or 1) x threads per block in {128, 256, 512,
  * 1024} (the shapes that fit) x histories a warp takes per queue pull in
- * {32, 64, 128, 256} -- and keep the fastest on the context.  Launch shapes
- * change speed only: the tallies are bit-identical for every shape.  The
+ * {32, 64, 128, 256} -- then, for the fastest, the material source
+ * (DOSE_OPT_MATERIAL_GRID 0 or 1), and keep the winners on the context.
+ * Launch shapes change speed only: the tallies are bit-identical.  The
  * phase's tally and dose are overwritten.  best (host, may be NULL)
  * receives {registers option, block, chunk, elapsed microseconds of the best
  * shape}.  Waits for the stream.  The step-length rule is part of the

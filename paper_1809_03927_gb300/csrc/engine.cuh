@@ -53,6 +53,7 @@ enum { FLAG_STEPLIMIT = 1 };
 // ---- one transport job of a persistent launch ---------------------------
 struct TJob {
     const int16_t *hu;                  // this phase's grid
+    const float2 *matg;                 // this phase's (rho, SPR) per voxel, or null: hu + table
     unsigned long long *tally;          // nvox
     unsigned long long *ledger;         // LED_WORDS
     const float4 *spot;                 // (x, y, E, sigma) patient mm / MeV

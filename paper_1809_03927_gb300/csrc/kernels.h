@@ -18,6 +18,7 @@ void grid_info(const dose_ctx *c, int dims[4]);
 int set_phase_zero(dose_ctx *c, int phase, void *stream);
 
 __global__ void k_density(const int16_t *hu, float *rho, long long n, const Tables *tab);
+__global__ void k_material(const int16_t *hu, float2 *m, long long n, const Tables *tab);
 __global__ void k_alloc(const AllocJob *jobs);
 // stage != 0: the launch gives transport_smem(n_jobs) bytes and the job
 // table is staged in shared memory; 0: transport_smem(kMaxStagedJobs + 1)

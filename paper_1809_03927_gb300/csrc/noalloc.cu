@@ -192,7 +192,7 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
     a.n_spots = n_spots;
     a.n_hist = n_histories;
     TJob t;
-    t.hu = hu; t.tally = tally; t.ledger = d_ledger;
+    t.hu = hu; t.matg = nullptr; t.tally = tally; t.ledger = d_ledger;
     t.spot = d_spot; t.wh = a.wh; t.prefix = a.prefix; t.n_spots = n_spots;
     t.nx = nx; t.ny = ny; t.nz = nz; t.dx = dx_mm; t.dy = dy_mm; t.dz = dz_mm;
     t.idx = 1.0f / dx_mm; t.idy = 1.0f / dy_mm; t.idz = 1.0f / dz_mm;

@@ -82,6 +82,18 @@ __global__ void k_density(const int16_t *__restrict__ hu, float *__restrict__ rh
     }
 }
 
+// HU -> (density, SPR) of every voxel: the table's values, for launches that
+// read the material per voxel instead of HU + table.
+__global__ void k_material(const int16_t *__restrict__ hu, float2 *__restrict__ m, long long n,
+                           const Tables *__restrict__ tab)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int h = min(max((int)hu[i], kHuMin), kHuMax);
+        m[i] = tab->mat[h - kHuMin];
+    }
+}
+
 // --------------------------------------------------------------- allocation
 // One block per job.  n_s = floor(N p_s / W) for every spot, then the
 // N - sum n_s spots with the largest remainders (ties: lower index) get one
@@ -323,8 +335,13 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         }
         const int nx = J.nx, ny = J.ny;
         const int vox = (iz * ny + iy) * nx + ix;
-        const int hv = min(max((int)__ldg(J.hu + vox), kHuMin), kHuMax);
-        const float2 m = __ldg(mat + (hv - kHuMin));
+        float2 m;
+        if (J.matg) {
+            m = __ldg(J.matg + vox);
+        } else {
+            const int hv = min(max((int)__ldg(J.hu + vox), kHuMin), kHuMax);
+            m = __ldg(mat + (hv - kHuMin));
+        }
         const float rho = m.x;
         const float spr = m.y * J.spr_scale;
         const float inv_spr = __fdividef(1.0f, spr);

@@ -26,7 +26,7 @@ DOSE_OK, DOSE_EINVAL, DOSE_ENOMEM, DOSE_ECUDA, DOSE_ETIMEOUT, DOSE_ESTEPLIMIT, D
  DOSE_DELIVERY) = range(12)
 DOSE_PHYS_STRAGGLING, DOSE_PHYS_MCS, DOSE_PHYS_NUCLEAR, DOSE_PHYS_ALL = 1, 2, 4, 7
 (DOSE_OPT_PHYSICS, DOSE_OPT_MAX_STEPS, DOSE_OPT_BLOCK, DOSE_OPT_BLOCKS_PER_SM, DOSE_OPT_CHUNK,
- DOSE_OPT_TIMEOUT_MS, DOSE_OPT_FAIL_ALLOC_AFTER, DOSE_OPT_REGISTERS) = range(8)
+ DOSE_OPT_TIMEOUT_MS, DOSE_OPT_FAIL_ALLOC_AFTER, DOSE_OPT_REGISTERS, DOSE_OPT_MATERIAL_GRID) = range(9)
 DOSE_JOB_CLEAR, DOSE_JOB_FINISH = 1, 2
 LEDGER = ("deposited", "escaped", "removed", "incident", "steps", "histories", "flags", "protons")
 

@@ -463,3 +463,24 @@ def test_autotune_keeps_results(gpu):
     finally:
         gpu.dose_destroy(ctx)
     np.testing.assert_array_equal(t, ref)
+
+
+def test_material_grid_gives_the_same_tallies(gpu):
+    """The per-voxel (density, SPR) grid holds the table's values, so the
+    transport's results do not depend on DOSE_OPT_MATERIAL_GRID (checked on
+    phase 2 of a 4DCT so the phase offset of the grid is exercised)."""
+    ph, _, geo = H.small_4dct(n_phases=3, nx=40, ny=40, nz=24)
+    plan = W.tumour_plan(geo, ph.origin, n_layers=3, per_layer=10, e_lo=70.0, e_hi=100.0)
+    dlv = H.whole_plan_on(2, 3)
+    out = []
+    for mat in (0, 1):
+        ctx = H.make_ctx(gpu, ph)
+        try:
+            gpu.dose_set_option(ctx, gpu.DOSE_OPT_MATERIAL_GRID, mat)
+            gpu.dose_add_spots(ctx, gpu.spots_array(plan), gpu.delivery_struct(dlv))
+            gpu.dose_run_phase(ctx, 2, 200_000, 6)
+            out.append(gpu.dose_read(ctx, gpu.DOSE_TALLY_I64, 2, np.zeros(ph.hu.shape[1:], np.uint64)))
+        finally:
+            gpu.dose_destroy(ctx)
+    assert out[0].sum() > 0
+    np.testing.assert_array_equal(out[0], out[1])
