@@ -1277,8 +1277,10 @@ int64_t or_breathing_deviate(uint64_t seed, int32_t f, uint64_t c)
 /* + sum_S D_i^S (Eq. 2), zero outside the mask.                           */
 /*                                                                         */
 /* The target voxel is an integer decided by floating point; it is taken  */
-/* in single precision with the operation order written below, the same   */
-/* precision the GPU kernel decides it in.  Sums and ratios are FP64.      */
+/* in single precision with the operation order written below (the        */
+/* displacement goes to voxel units through the single-precision          */
+/* reciprocal of the voxel size), the precision the GPU kernel decides it */
+/* in.  Sums and ratios are FP64.                                          */
 /* ======================================================================= */
 static float or_f_lerp(float a, float b, float t)
 {
@@ -1359,7 +1361,8 @@ int or_emtm(const int32_t n[3], const float dmm[3], int32_t n_phases,
                     float disp = 0.0f;
                     if (dvf) disp = or_f_sample(dvf + ((size_t)S * 3 + a) * nvox, n, q[0], q[1], q[2]);
                     volatile float base = q[a] + 0.5f;
-                    volatile float off = disp / dmm[a];
+                    volatile float inv = 1.0f / dmm[a];
+                    volatile float off = disp * inv;
                     volatile float r = base + off;
                     t[a] = r;
                 }

@@ -95,6 +95,7 @@ struct dose_ctx {
     unsigned long long *ledger_all = nullptr;// n_phases x LED_WORDS
     unsigned long long *em = nullptr;        // E then M, n_phases x nvox each
     float *dvf_buf = nullptr;                // staging for host DVFs
+    float4 *dvf4 = nullptr;                  // one phase's field, interleaved (EMTM)
     uint8_t *mask_buf = nullptr;             // staging for a host mask
     float *dvfgrid_e = nullptr;              // decoded registration grid (r_f - r0), 3 x cap
     float *dvfgrid_delta = nullptr;          // staging for host translations, 3 x cap
@@ -1059,7 +1060,7 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
     CK(c, cudaMemsetAsync(c->maxbits, 0, P * sizeof(unsigned), st));
     CK(c, cudaMemsetAsync(c->emtm_stats, 0, 4 * sizeof(unsigned long long), st));
     EmtmArgs a;
-    a.dose = c->dose_all; a.rho = g.rho; a.dvf = dvf_dev; a.mask = mask_dev;
+    a.dose = c->dose_all; a.rho = g.rho; a.mask = mask_dev;
     a.E = c->em; a.M = c->em + P * nvox; a.maxbits = c->maxbits; a.stats = c->emtm_stats;
     a.accum = c->accum;
     a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
@@ -1068,8 +1069,21 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
     a.ref = ref_phase; a.n_phases = (int)P;
     k_emtm_max<<<dim3(304, (unsigned)P), 256, 0, st>>>(a);
     CK(c, cudaGetLastError());
-    k_emtm<<<dim3((unsigned)((nvox + 255) / 256), (unsigned)P), 256, 0, st>>>(a);
-    CK(c, cudaGetLastError());
+    a.dvf4 = nullptr; a.phase = 0;
+    a.idx = 1.0f / g.d[0]; a.idy = 1.0f / g.d[1]; a.idz = 1.0f / g.d[2];
+    if (dvf_dev) {
+        if (!c->dvf4 && (rc = dalloc_t(c, &c->dvf4, nvox))) return rc;
+        for (int S = 0; S < (int)P; ++S) {
+            if (S == ref_phase) continue;
+            k_dvf4<<<1216, 256, 0, st>>>(dvf_dev + (size_t)S * 3 * nvox, c->dvf4, (long long)nvox);
+            a.dvf4 = c->dvf4; a.phase = S;
+            k_emtm<<<dim3((unsigned)((nvox + 255) / 256), 1), 256, 0, st>>>(a);
+            CK(c, cudaGetLastError());
+        }
+    } else {
+        k_emtm<<<dim3((unsigned)((nvox + 255) / 256), (unsigned)P), 256, 0, st>>>(a);
+        CK(c, cudaGetLastError());
+    }
     k_emtm_sum<<<1216, 256, 0, st>>>(a);
     CK(c, cudaGetLastError());
     c->have_accum = true;

@@ -78,7 +78,6 @@ __global__ void k_timeline(const TimelineArgs *args);
 struct EmtmArgs {
     const float *dose;               // n_phases x nvox
     const float *rho;                // n_phases x nvox
-    const float *dvf;                // n_phases x 3 x nvox, or null
     const uint8_t *mask;             // nvox or null
     unsigned long long *E, *M;       // n_phases x nvox each (slot of the reference unused)
     unsigned *maxbits;               // n_phases: bits of max(rho D) per phase
@@ -88,8 +87,12 @@ struct EmtmArgs {
     float dx, dy, dz;
     int nsx, nsy, nsz;
     int ref, n_phases;
+    const float4 *dvf4;              // one source phase's field, interleaved, or null (identity)
+    int phase;                       // that source phase (grid.y is the phase when dvf4 is null)
+    float idx, idy, idz;             // 1 / voxel size, rounded to FP32
 };
 __global__ void k_emtm_max(EmtmArgs a);
+__global__ void k_dvf4(const float *src, float4 *dst, long long nvox);
 __global__ void k_emtm(EmtmArgs a);
 __global__ void k_emtm_sum(EmtmArgs a);
 
