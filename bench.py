@@ -36,6 +36,12 @@ SEED = 2
 WORKLOAD = "slab phantom 128^3 at 2 mm (water/lung/bone), 400 spots on 10 layers 70-200 MeV, 1e7 histories"
 # algorithmic thread-operations of one condensed-history step
 OPS_PER_STEP = 230
+# DRAM bytes (read + write) of one transport launch on the slab workload
+# (1e7 histories; 64-register variant, 1024-thread blocks, chunk 32, HU +
+# table): ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the
+# full-size launch, 2.71 MB read, 0 written (the grid is read once, the
+# tally stays in L2)
+TRANSPORT_DRAM = {"bytes": 2.71e6, "shape": (1, 1024, 32, 0)}
 
 
 def _args():
@@ -637,6 +643,11 @@ def run_engine(args):
         return
     value = ws * n_hist / (t_step / 1e3)
     peaks = _peaks()
+    material = D.dose_get_option(ctx, D.DOSE_OPT_MATERIAL_GRID)
+    shape = (int(tune[0]), int(tune[1]), int(tune[2]), material)
+    # DRAM traffic of the transport launch, from an ncu capture of this
+    # workload in this launch shape (null for any other shape or size)
+    traffic = TRANSPORT_DRAM["bytes"] if (shape == TRANSPORT_DRAM["shape"] and n_hist == N_HIST) else None
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12          # Top/s: 128 FP32/INT32 lanes per SM
@@ -649,10 +660,10 @@ def run_engine(args):
                    "histories_per_step": n_hist, "steps_per_history": round(steps_per_hist, 2),
                    "l2": "256 MB buffer written between timed steps, outside the step events",
                    "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2],
-                              "autotune_sample_us": tune[3]},
+                              "material_grid": material, "autotune_sample_us": tune[3]},
                    "parallelism": f"{ws} independent replica(s), one per GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
-                     "frac": achieved / peak_ops, "traffic": None,
+                     "frac": achieved / peak_ops, "traffic": traffic,
                      "kernel": "k_transport", "kernel_ms": t_kernel,
                      "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (median sampled SM clock)",
                      "ops_per_step": OPS_PER_STEP},

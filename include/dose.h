@@ -395,6 +395,10 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
 /* Set an option (DOSE_OPT_*).                                              */
 int dose_set_option(dose_ctx *c, int option, int64_t value);
 
+/* Read an option's current value (e.g. the launch shape the autotuner
+ * kept).  value: host pointer.  DOSE_EINVAL for an unknown option.        */
+int dose_get_option(const dose_ctx *c, int option, int64_t *value);
+
 /* Free the context (waits for its device work).  NULL is a no-op.          */
 void dose_destroy(dose_ctx *c);
 

@@ -427,6 +427,23 @@ int dose_create_view(dose_ctx *base, dose_ctx **out)
     return DOSE_OK;
 }
 
+int dose_get_option(const dose_ctx *c, int option, int64_t *value)
+{
+    if (!c || !value) return fail(nullptr, DOSE_EINVAL, "ctx and value are required");
+    switch (option) {
+    case DOSE_OPT_PHYSICS: *value = c->physics; return DOSE_OK;
+    case DOSE_OPT_MAX_STEPS: *value = c->max_steps; return DOSE_OK;
+    case DOSE_OPT_BLOCK: *value = c->block; return DOSE_OK;
+    case DOSE_OPT_BLOCKS_PER_SM: *value = c->blocks_per_sm; return DOSE_OK;
+    case DOSE_OPT_CHUNK: *value = c->chunk; return DOSE_OK;
+    case DOSE_OPT_TIMEOUT_MS: *value = c->timeout_ms; return DOSE_OK;
+    case DOSE_OPT_FAIL_ALLOC_AFTER: *value = c->fail_alloc_after; return DOSE_OK;
+    case DOSE_OPT_REGISTERS: *value = c->regs; return DOSE_OK;
+    case DOSE_OPT_MATERIAL_GRID: *value = c->material_grid; return DOSE_OK;
+    default: return fail(nullptr, DOSE_EINVAL, "unknown option %d", option);
+    }
+}
+
 int dose_set_option(dose_ctx *c, int option, int64_t value)
 {
     if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");

@@ -121,6 +121,7 @@ def _load():
         "dose_decode_dvf": ([P, P, P, I, P, P, P], I),
         "dose_add_spots_trials": ([P, I, P, I64, P, P, U64, P], I),
         "dose_set_field_beam": ([P, I, P], I),
+        "dose_get_option": ([P, I, C.POINTER(I64)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -223,6 +224,12 @@ def dose_add_spots(ctx, spots, delivery=None, stream=None):
     """``spots``: a ``dose_spot`` ctypes array; ``delivery``: ``dose_delivery`` or None."""
     dl = C.byref(delivery) if delivery is not None else None
     _check(_lib.dose_add_spots(ctx, C.cast(spots, C.c_void_p), len(spots), dl, _stream(stream)), ctx)
+
+
+def dose_get_option(ctx, option):
+    v = C.c_int64()
+    _check(_lib.dose_get_option(ctx, int(option), C.byref(v)), ctx)
+    return int(v.value)
 
 
 def dose_set_field_beam(ctx, field, beam_dir):

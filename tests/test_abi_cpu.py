@@ -54,6 +54,8 @@ def test_argument_validation_without_device(libdose):
     assert lib.dose_debug_philox(None, None, None, 0, None) == D.DOSE_EINVAL
     assert lib.dose_add_spots_trials(None, 0, None, 0, None, None, 0, None) == D.DOSE_EINVAL
     assert lib.dose_decode_dvf(None, None, None, 0, None, None, None) == D.DOSE_EINVAL
+    assert lib.dose_get_option(None, 0, None) == D.DOSE_EINVAL
+    assert lib.dose_set_field_beam(None, 0, None) == D.DOSE_EINVAL
     lib.dose_destroy(None)
 
 
