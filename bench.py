@@ -62,6 +62,8 @@ def _args():
     p.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
     p.add_argument("--serve-budget-gb", type=float, default=150.0, help="device memory for request slots")
     p.add_argument("--histories-4d", type=int, default=100_000_000, help="histories per phase of the 4D plan")
+    p.add_argument("--small-4d", action="store_true",
+                   help="4D leg on a 128x128x80 grid at 2x2x5 mm (profiler captures), not the 4DCT workload")
     p.add_argument("--histories", type=int, default=N_HIST,
                    help="histories per step (smaller cases for profiling; the metric's workload is 1e7)")
     return p.parse_args()
@@ -183,16 +185,17 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ 4D plan
-def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
+def _bench_4d(D, torch, stream, n_per_phase, reps, seed, small=False):
     """Seconds per 4D dose of the synthetic 4DCT: 10 phases of 256x256x160
     at 1x1x2.5 mm, 3000 spots on 20 layers (70-180 MeV), delivery timeline
     (1e9 p/s, 2 ms spot switch, 1 s layer switch, 4 s period, random start),
     n_per_phase histories per phase in one launch, EMTM accumulation onto
     phase 0 with 2x2x5 subvoxels (0.5 mm) and the Eq. 2 sum.  Grids, DVFs
     and plan are resident; the timed plan runs the timeline, all phases'
-    transport and the accumulation."""
+    transport and the accumulation.  small: the same phantom on a 128x128x80
+    grid at 2x2x5 mm (for profiler captures of the accumulation kernels)."""
     from paper_1809_03927_gb300 import workloads as W
-    ph, dvf, geo = W.phantom_4dct()
+    ph, dvf, geo = W.phantom_4dct(128, 128, 80, (2.0, 2.0, 5.0)) if small else W.phantom_4dct()
     plan = W.tumour_plan(geo, ph.origin)
     dlv = D.delivery_struct(W.Delivery(seed=3))
     nx, ny, nz = ph.n
@@ -211,7 +214,7 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
     try:
         D.dose_add_spots(ctx, spots, dlv, stream)
         phase_p = D.dose_read(ctx, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
-        tune = D.dose_autotune(ctx, int(np.argmax(phase_p)), n_per_phase, 2_000_000, seed, stream)
+        tune = D.dose_autotune(ctx, int(np.argmax(phase_p)), n_per_phase, min(n_per_phase, 2_000_000), seed, stream)
 
         def plan_once():
             D.dose_add_spots(ctx, spots, dlv, stream)
@@ -284,7 +287,8 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed):
             "dvf_decode_s": decode_s,
             "dvf_decode": f"{ph.n_phases - 1} registrations on {nx // 2}x{ny // 2}x{nz // 2} grids "
                           "(every other CT voxel centre) decoded onto the CT grid with the report mask",
-            "workload": "synthetic 4DCT 10 x 256x256x160 at 1x1x2.5 mm, 3000 spots / 20 layers 70-180 MeV, "
+            "workload": ("synthetic 4DCT 10 x 128x128x80 at 2x2x5 mm (small, for profiling)" if small else
+                         "synthetic 4DCT 10 x 256x256x160 at 1x1x2.5 mm") + ", 3000 spots / 20 layers 70-180 MeV, "
                         f"{n_per_phase:.0e} histories per phase, EMTM 2x2x5 onto phase 0",
             "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}}
 
@@ -343,7 +347,7 @@ def _bench_trials(D, torch, stream, n_per_phase, n_trials=25, seed=SEED):
 
         D.dose_add_spots_trials(views, spots, D.delivery_struct(mean), D.spread_struct(spread), 0, stream)
         pp0 = D.dose_read(views[0], D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
-        tune = D.dose_autotune(views[0], int(np.argmax(pp0)), n_per_phase, 2_000_000, seed, stream)
+        tune = D.dose_autotune(views[0], int(np.argmax(pp0)), n_per_phase, min(n_per_phase, 2_000_000), seed, stream)
         study()                                    # warm-up (and first allocation of the views)
         t0 = time.perf_counter()
         n_jobs, mc_s = study()
@@ -674,7 +678,7 @@ def run_engine(args):
         "clocks": clocks,
     }
     if not args.no_4d:
-        line["four_d"] = _bench_4d(D, torch, stream, args.histories_4d, 2, SEED)
+        line["four_d"] = _bench_4d(D, torch, stream, args.histories_4d, 2, SEED, small=args.small_4d)
     if not args.no_ragged:
         line["ragged_batch"] = _bench_ragged(D, torch, stream)
     if not args.no_trials:
