@@ -169,8 +169,9 @@ def _lateral_sigma(d, axis_sum, spacing):
     p = d.sum(axis=axis_sum)
     x = (np.arange(p.shape[-1]) + 0.5) * spacing
     w = p.sum(axis=-1)
-    m = (p * x).sum(axis=-1) / w
-    return np.sqrt((p * (x - m[:, None]) ** 2).sum(axis=-1) / w), m
+    safe = np.where(w > 0, w, 1.0)                 # depths the beam never reaches: nan
+    m = np.where(w > 0, (p * x).sum(axis=-1) / safe, np.nan)
+    return np.where(w > 0, np.sqrt((p * (x - m[:, None]) ** 2).sum(axis=-1) / safe), np.nan), m
 
 
 def _comb(sg, so):
