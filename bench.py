@@ -34,7 +34,10 @@ METRIC = "proton histories/s"
 N_HIST = 10_000_000
 SEED = 2
 WORKLOAD = "slab phantom 128^3 at 2 mm (water/lung/bone), 400 spots on 10 layers 70-200 MeV, 1e7 histories"
-# algorithmic thread-operations of one condensed-history step
+# algorithmic thread-operations of one condensed-history step: Philox4x32-10
+# 80, three Box-Muller pairs 30, five table lerps 30, voxel-face distances
+# 20, energy loss and straggling 15, scattering, frame and move 40, tally
+# quantisation 5, bookkeeping 10
 OPS_PER_STEP = 230
 # DRAM bytes (read + write) of one transport launch on the slab workload
 # (1e7 histories; 64-register variant, 1024-thread blocks, chunk 32, HU +
@@ -64,9 +67,29 @@ def _args():
     p.add_argument("--histories-4d", type=int, default=100_000_000, help="histories per phase of the 4D plan")
     p.add_argument("--small-4d", action="store_true",
                    help="4D leg on a 128x128x80 grid at 2x2x5 mm (profiler captures), not the 4DCT workload")
+    p.add_argument("--reference-seconds", type=float, default=10.0,
+                   help="CPU seconds of each timed oracle step of the reference arm")
     p.add_argument("--histories", type=int, default=N_HIST,
                    help="histories per step (smaller cases for profiling; the metric's workload is 1e7)")
     return p.parse_args()
+
+
+def reduce_max_over_ranks(values, ws, device="cpu"):
+    """Per-rank times -> the maximum over the ranks (all ranks get it); the
+    process group (nccl for the engine, any backend in tests) is already
+    initialised when ws > 1."""
+    import torch
+    vals = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    return [float(v) for v in vals.cpu()]
+
+
+def job_throughput(ws, units_per_rank, step_ms):
+    """Whole-job throughput: the units every rank processed in one step over
+    the slowest rank's step time (weak scaling: each rank has its own)."""
+    return ws * units_per_rank / (step_ms / 1e3)
 
 
 def _dist():
@@ -167,7 +190,8 @@ def run_reference(args):
     phantom, plan = _workload()
     times, counts = [], []
     for i in range(args.warmup + args.steps):
-        r = _oracle_sample(phantom, plan, seconds_target=4.0 if i < args.warmup else 10.0)
+        r = _oracle_sample(phantom, plan, seconds_target=min(4.0, args.reference_seconds) if i < args.warmup
+                           else args.reference_seconds)
         if i >= args.warmup:
             n = float(r["sample"].split("(")[1].split(" ")[0])
             counts.append(n)
@@ -633,21 +657,18 @@ def run_engine(args):
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
+    material = D.dose_get_option(ctx, D.DOSE_OPT_MATERIAL_GRID)
     D.dose_destroy(ctx)
 
-    # reduce over ranks: max time
-    t_step = total_ms / args.steps
-    vals = torch.tensor([t_step, e2e_s, sum(tk) / len(tk)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    t_step, e2e_s, t_kernel = [float(v) for v in vals.cpu()]
+    # whole-job time: the slowest rank
+    t_step, e2e_s, t_kernel = reduce_max_over_ranks([total_ms / args.steps, e2e_s, sum(tk) / len(tk)], ws,
+                                                    device="cuda")
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
-    value = ws * n_hist / (t_step / 1e3)
+    value = job_throughput(ws, n_hist, t_step)
     peaks = _peaks()
-    material = D.dose_get_option(ctx, D.DOSE_OPT_MATERIAL_GRID)
     shape = (int(tune[0]), int(tune[1]), int(tune[2]), material)
     # DRAM traffic of the transport launch, from an ncu capture of this
     # workload in this launch shape (null for any other shape or size)
