@@ -70,6 +70,7 @@ struct TJob {
     unsigned physics;
     unsigned max_steps;
     unsigned key0, key1, stream;
+    uint2 rk[10];                       // round keys (key + r x Weyl increments)
     unsigned long long hist_begin;      // first history of this slice
     unsigned long long work_begin;      // offset in the launch's work index
 };
@@ -119,6 +120,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
         const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
         const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Philox4x32-10 with the ten round keys given (the key schedule of the
+// definition, precomputed per job).
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint2 *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint2 k = rk[r];
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
     }
     return c;
 }

@@ -350,8 +350,8 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         ++step;
         // this step's random numbers: independent of the geometry below, so
         // the generator's rounds can interleave with the table lookups
-        const U6 u = uniforms6(philox4x32_10(
-            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), J.stream), J.key0, J.key1));
+        const U6 u = uniforms6(philox_rk(
+            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), J.stream), J.rk));
         if (R0 * inv_spr <= kSmin) {                   // residual range below s_min
             const unsigned long long eu = to_units(E * wh);
             atomicAdd(J.tally + vox, eu);
