@@ -636,12 +636,17 @@ def run_engine(args):
 
     # end to end through the C ABI with host buffers: upload grid + plan,
     # run, read the dose back to host memory, every step
+    launch_opts = {o: D.dose_get_option(ctx, o) for o in (D.DOSE_OPT_REGISTERS, D.DOSE_OPT_BLOCK, D.DOSE_OPT_CHUNK,
+                                                         D.DOSE_OPT_MATERIAL_GRID)}
     dose_host = torch.empty((nz, ny, nx), dtype=torch.float32).pin_memory()
     hu_pinned = torch.from_numpy(hu_host).pin_memory()
 
     def e2e_step():
         c = D.dose_create_grid(nx, ny, nz, *phantom.d, phantom.origin, 1, hu_pinned, phantom.beam_dir, stream)
         try:
+            # the launch shape tuned once above, as a user would reuse it
+            for opt, v in launch_opts.items():
+                D.dose_set_option(c, opt, v)
             D.dose_add_spots(c, spots, None, stream)
             D.dose_run_phase(c, 0, n_hist, seed, 1.0, None, stream)
             D.dose_read(c, D.DOSE_PHASE_DOSE, 0, dose_host, stream)

@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -120,7 +121,7 @@ struct dose_ctx {
     int material_grid = 0;                   // DOSE_OPT_MATERIAL_GRID
     long long timeout_ms = 600000;
     long long fail_alloc_after = -1;
-    std::vector<void *> owned;
+    std::vector<std::pair<void *, size_t>> owned;   // device blocks and their sizes
     std::string err;
 };
 
@@ -146,6 +147,72 @@ int fail(dose_ctx *c, int code, const char *fmt, ...)
 
 cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Device blocks released by destroyed contexts, kept per (device, size) for
+// the next context (cudaMalloc/cudaFree cost ~0.1 ms each and cudaFree
+// synchronises the device).  Blocks enter the cache only after
+// dose_destroy has synchronised the device, so no kernel still uses them;
+// at most kBlockCacheBytes are kept, and an allocation that fails empties
+// the cache and tries again.
+std::mutex g_cache_mutex;
+std::map<std::pair<int, size_t>, std::vector<void *>> g_cache;
+size_t g_cache_bytes = 0;
+constexpr size_t kBlockCacheBytes = size_t(8) << 30;
+
+size_t block_size(size_t bytes) { return (std::max<size_t>(bytes, 16) + 255) & ~size_t(255); }
+
+void cache_flush(int dev)
+{
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    for (auto it = g_cache.begin(); it != g_cache.end();) {
+        if (it->first.first != dev) { ++it; continue; }
+        for (void *q : it->second) { cudaFree(q); g_cache_bytes -= it->first.second; }
+        it = g_cache.erase(it);
+    }
+}
+
+// A device block of block_size(bytes) on the current device.
+cudaError_t block_alloc(void **p, size_t bytes)
+{
+    const size_t sz = block_size(bytes);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mutex);
+        auto it = g_cache.find({dev, sz});
+        if (it != g_cache.end() && !it->second.empty()) {
+            *p = it->second.back();
+            it->second.pop_back();
+            g_cache_bytes -= sz;
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, sz);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        cache_flush(dev);
+        e = cudaMalloc(p, sz);
+    }
+    return e;
+}
+
+// Give back a block no kernel uses any more (the device was synchronised).
+void block_release(void *p, size_t bytes)
+{
+    if (!p) return;
+    const size_t sz = block_size(bytes);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mutex);
+        if (g_cache_bytes + sz <= kBlockCacheBytes) {
+            g_cache[{dev, sz}].push_back(p);
+            g_cache_bytes += sz;
+            return;
+        }
+    }
+    cudaFree(p);
+}
+
 int dalloc(dose_ctx *c, void **p, size_t bytes)
 {
     if (c->fail_alloc_after >= 0) {
@@ -155,20 +222,21 @@ int dalloc(dose_ctx *c, void **p, size_t bytes)
         }
         --c->fail_alloc_after;
     }
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    cudaError_t e = block_alloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return fail(c, DOSE_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
-    c->owned.push_back(*p);
+    c->owned.emplace_back(*p, bytes);
     return DOSE_OK;
 }
 
+// Free one block while the context lives: cudaFree (it waits for the device).
 void dfree(dose_ctx *c, void *p)
 {
     if (!p) return;
-    auto it = std::find(c->owned.begin(), c->owned.end(), p);
+    auto it = std::find_if(c->owned.begin(), c->owned.end(), [p](const std::pair<void *, size_t> &o) { return o.first == p; });
     if (it != c->owned.end()) c->owned.erase(it);
     cudaFree(p);
 }
@@ -382,8 +450,8 @@ int dose_create_grid(dose_ctx **out, int nx, int ny, int nz, float dx_mm, float 
         dose_destroy(c);
         return rc;
     }
-    e = cudaMalloc(&g.hu, n_all * sizeof(int16_t));
-    if (e == cudaSuccess) e = cudaMalloc(&g.rho, n_all * sizeof(float));
+    e = block_alloc(reinterpret_cast<void **>(&g.hu), n_all * sizeof(int16_t));
+    if (e == cudaSuccess) e = block_alloc(reinterpret_cast<void **>(&g.rho), n_all * sizeof(float));
     if (e != cudaSuccess) {
         cudaGetLastError();
         rc = fail(nullptr, DOSE_ENOMEM, "grid allocation (%zu voxels): %s", n_all, cudaGetErrorString(e));
@@ -1303,12 +1371,13 @@ void dose_destroy(dose_ctx *c)
 {
     if (!c) return;
     if (c->g) cudaSetDevice(c->g->device);
-    cudaDeviceSynchronize();
-    for (void *p : c->owned) cudaFree(p);
+    cudaDeviceSynchronize();                 // nothing in flight uses the blocks below
+    for (auto &o : c->owned) block_release(o.first, o.second);
     c->owned.clear();
     if (c->g && c->g->refs.fetch_sub(1) == 1) {
-        if (c->g->hu) cudaFree(c->g->hu);
-        if (c->g->rho) cudaFree(c->g->rho);
+        const size_t n_all = (size_t)c->g->nvox * c->g->n_phases;
+        block_release(c->g->hu, n_all * sizeof(int16_t));
+        block_release(c->g->rho, n_all * sizeof(float));
         if (c->g->mat) cudaFree(c->g->mat);
         delete c->g;
     }
