@@ -93,3 +93,13 @@ def test_4d_gated_skips_empty_phases(gpu, orc):
     assert doses[0].max() == 0.0 and doses[3].max() == 0.0
     assert doses[1].max() > 0.0 and doses[2].max() > 0.0
     assert acc.max() > 0.0
+
+
+def test_readme_example_runs(gpu):
+    """The usage example of the README, as written."""
+    import re
+    readme = open(__import__("os").path.join(__import__("os").path.dirname(__file__), "..", "README.md")).read()
+    code = re.search(r"```python\n(.*?)```", readme, re.S).group(1)
+    scope = {}
+    exec(compile(code, "README.md", "exec"), scope)
+    assert scope["acc"].max() > 0
