@@ -883,8 +883,9 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
             t.beam_axis = g.beam_axis; t.beam_sign = g.beam_sign;
             t.spr_scale = J.spr_scale; t.physics = c->physics; t.max_steps = c->max_steps;
             t.key0 = (unsigned)J.seed; t.key1 = (unsigned)(J.seed >> 32);
-            for (int r = 0; r < 10; ++r)   // Philox round keys: key + r x the Weyl increments
-                t.rk[r] = make_uint2(t.key0 + (unsigned)r * 0x9E3779B9u, t.key1 + (unsigned)r * 0xBB67AE85u);
+            for (int r = 0; r < 10; r += 2)   // Philox round keys: key + r x the Weyl increments
+                t.rk[r >> 1] = make_uint4(t.key0 + (unsigned)r * 0x9E3779B9u, t.key1 + (unsigned)r * 0xBB67AE85u,
+                                          t.key0 + (unsigned)(r + 1) * 0x9E3779B9u, t.key1 + (unsigned)(r + 1) * 0xBB67AE85u);
             t.stream = (unsigned)J.phase;
             t.hist_begin = J.hist_begin; t.work_begin = work;
             tj.push_back(t);

@@ -51,26 +51,28 @@ enum { LED_DEP = 0, LED_ESC = 1, LED_REM = 2, LED_INC = 3, LED_STEPS = 4, LED_HI
 enum { FLAG_STEPLIMIT = 1 };
 
 // ---- one transport job of a persistent launch ---------------------------
-struct TJob {
+struct alignas(16) TJob {
+    // read every step, grouped in 16-byte words for vector loads
+    int nx, ny, nz;
+    unsigned max_steps;
+    float dx, dy, dz;
+    float spr_scale;
+    float idx, idy, idz;                // 1 / voxel sizes
+    unsigned physics;
+    uint4 rk[5];                        // Philox round keys: (k0, k1) of rounds 2i and 2i+1
     const int16_t *hu;                  // this phase's grid
     const float2 *matg;                 // this phase's (rho, SPR) per voxel, or null: hu + table
     unsigned long long *tally;          // nvox
     unsigned long long *ledger;         // LED_WORDS
+    // read at history birth
     const float4 *spot;                 // (x, y, E, sigma) patient mm / MeV
     const float *wh;                    // history weight per spot
     const unsigned long long *prefix;   // n_spots + 1 (first history of each spot)
-    int n_spots;
-    int nx, ny, nz;
-    float dx, dy, dz;
-    float idx, idy, idz;                // 1 / voxel sizes
-    float o[3];                         // patient->grid offsets per axis (origin + shift)
     const unsigned char *spot_dir;      // per spot: 2 axis + (sign > 0), or null: beam_axis/sign
+    int n_spots;
+    float o[3];                         // patient->grid offsets per axis (origin + shift)
     int beam_axis, beam_sign;
-    float spr_scale;
-    unsigned physics;
-    unsigned max_steps;
     unsigned key0, key1, stream;
-    uint2 rk[10];                       // round keys (key + r x Weyl increments)
     unsigned long long hist_begin;      // first history of this slice
     unsigned long long work_begin;      // offset in the launch's work index
 };
@@ -125,15 +127,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
 }
 
 // Philox4x32-10 with the ten round keys given (the key schedule of the
-// definition, precomputed per job).
-__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint2 *rk)
+// definition, precomputed per job, two rounds per 16-byte word).
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint4 *rk)
 {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint2 k = rk[r];
-        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    for (int r = 0; r < 10; r += 2) {
+        const uint4 k = rk[r >> 1];
+        unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
         c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        hi0 = __umulhi(0xD2511F53u, c.x); lo0 = 0xD2511F53u * c.x;
+        hi1 = __umulhi(0xCD9E8D57u, c.z); lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.z, lo1, hi0 ^ c.w ^ k.w, lo0);
     }
     return c;
 }

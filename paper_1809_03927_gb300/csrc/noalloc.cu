@@ -201,8 +201,9 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
     t.beam_axis = axis; t.beam_sign = sign;
     t.spr_scale = 1.0f; t.physics = DOSE_PHYS_ALL; t.max_steps = 20000;
     t.key0 = (unsigned)seed; t.key1 = (unsigned)(seed >> 32);
-    for (int r = 0; r < 10; ++r)   // Philox round keys: key + r x the Weyl increments
-        t.rk[r] = make_uint2(t.key0 + (unsigned)r * 0x9E3779B9u, t.key1 + (unsigned)r * 0xBB67AE85u);
+    for (int r = 0; r < 10; r += 2)   // Philox round keys: key + r x the Weyl increments
+        t.rk[r >> 1] = make_uint4(t.key0 + (unsigned)r * 0x9E3779B9u, t.key1 + (unsigned)r * 0xBB67AE85u,
+                                  t.key0 + (unsigned)(r + 1) * 0x9E3779B9u, t.key1 + (unsigned)(r + 1) * 0xBB67AE85u);
     t.stream = 0;
     t.hist_begin = 0; t.work_begin = 0;
     AllocJob *d_a = reinterpret_cast<AllocJob *>(base + kOffAlloc);
