@@ -290,6 +290,10 @@ typedef struct dose_request {
     uint64_t seed;
     float spr_scale;
     float shift_mm[3];
+    /* the request's own delivery (a gating or repainting variant, Sec. 2.B),
+     * copied at submission; NULL = the server's.  A request whose delivery
+     * puts no protons on any phase finishes with zero dose.               */
+    const dose_delivery *delivery;
 } dose_request;
 int dose_server_create(dose_ctx *base, const dose_server_config *cfg, const dose_spot *spots,
                        int64_t n_spots, const dose_delivery *delivery, dose_server **out);

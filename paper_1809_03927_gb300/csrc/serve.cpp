@@ -25,14 +25,23 @@
 #include "kernels.h"
 
 struct dose_server {
+    struct Queued {
+        int64_t id;
+        dose_request req;
+        bool own_delivery;             // req.delivery was given (copied into dlv)
+        dose_delivery dlv;
+    };
     struct Slot {
         dose_ctx *view = nullptr;
         int64_t request = -1;          // -1: free
+        bool loaded_own = false;       // the plan is loaded with loaded_dlv, not the server's
+        dose_delivery loaded_dlv{};
     };
     struct Active {
         int64_t id;
         dose_request req;
         int slot;
+        std::vector<int> phases;       // phases the request's delivery reaches
         uint64_t per_phase;            // histories per phase with protons
         uint64_t next;                 // next history index (same for every phase)
     };
@@ -44,7 +53,7 @@ struct dose_server {
     std::vector<int> phases;           // phases whose subplan has protons
     size_t slot_bytes = 0;
     std::vector<Slot> slots;
-    std::deque<std::pair<int64_t, dose_request>> queue;
+    std::deque<Queued> queue;
     std::vector<Active> active;
     std::vector<int64_t> done;         // finished, result not yet released
     std::vector<std::pair<int64_t, int>> finished_slot;  // id -> slot
@@ -127,7 +136,13 @@ int dose_server_submit(dose_server *s, const dose_request *req, int64_t *id)
     if (!s || !req) return sfail(s, DOSE_EINVAL, "server and request are required");
     if (req->n_histories == 0) return sfail(s, DOSE_EINVAL, "request has no histories");
     const int64_t rid = s->next_id++;
-    s->queue.emplace_back(rid, *req);
+    dose_server::Queued q;
+    q.id = rid;
+    q.req = *req;
+    q.own_delivery = req->delivery != nullptr;
+    if (q.own_delivery) q.dlv = *req->delivery;
+    q.req.delivery = nullptr;                      // the copy in q.dlv is used
+    s->queue.push_back(q);
     if (id) *id = rid;
     return DOSE_OK;
 }
@@ -143,6 +158,7 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
         int slot = -1;
         for (size_t k = 0; k < s->slots.size(); ++k)
             if (s->slots[k].request < 0) { slot = (int)k; break; }
+        const dose_server::Queued &q = s->queue.front();
         if (slot < 0 && s->slots.size() < cap) {
             dose_server::Slot sl;
             int rc = dose_create_view(s->base, &sl.view);
@@ -157,28 +173,61 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
             slot = (int)s->slots.size() - 1;
         }
         if (slot < 0) break;
-        auto q = s->queue.front();
-        s->queue.pop_front();
+        dose_server::Slot &sl = s->slots[slot];
         dose_server::Active a;
-        a.id = q.first;
-        a.req = q.second;
+        a.id = q.id;
+        a.req = q.req;
         a.slot = slot;
-        a.per_phase = std::max<uint64_t>(1, q.second.n_histories / s->phases.size());
+        a.phases = s->phases;
+        // a request with its own delivery reloads the slot's plan with it
+        // (the slot keeps it for the next request with the same delivery)
+        const bool want_own = q.own_delivery;
+        const bool same = want_own ? (sl.loaded_own && std::memcmp(&sl.loaded_dlv, &q.dlv, sizeof q.dlv) == 0)
+                                   : !sl.loaded_own;
+        if (!same) {
+            const dose_delivery *d = want_own ? &q.dlv : (s->has_delivery ? &s->delivery : nullptr);
+            int rc = dose_add_spots(sl.view, s->spots.data(), (int64_t)s->spots.size(), d, stream);
+            if (rc) return rc;
+            sl.loaded_own = want_own;
+            if (want_own) sl.loaded_dlv = q.dlv;
+        }
+        if (want_own) {
+            int dims[4] = {0, 0, 0, 0};
+            dose::grid_info(sl.view, dims);
+            const int64_t S = (int64_t)s->spots.size();
+            std::vector<uint64_t> pp((size_t)dims[3] * S);
+            int rc = dose_read(sl.view, DOSE_SUBPLAN, 0, pp.data(), pp.size() * 8, 0, stream);
+            if (rc) return rc;
+            a.phases.clear();
+            for (int p = 0; p < dims[3]; ++p) {
+                uint64_t w = 0;
+                for (int64_t k = 0; k < S; ++k) w += pp[(size_t)p * S + k];
+                if (w) a.phases.push_back(p);
+            }
+        }
+        a.per_phase = a.phases.empty() ? 0 : std::max<uint64_t>(1, a.req.n_histories / a.phases.size());
         a.next = 0;
-        s->slots[slot].request = a.id;
+        sl.request = a.id;
+        s->queue.pop_front();
         s->active.push_back(a);
     }
     if (s->active.empty()) return DOSE_OK;
     // every active request gets an equal share of the step's histories
+    size_t phase_jobs = 0;
+    for (const auto &a : s->active) phase_jobs += a.phases.size();
     const uint64_t share = std::max<uint64_t>(
         s->cfg.min_slice ? s->cfg.min_slice : 1,
-        s->cfg.step_histories / (s->active.size() * s->phases.size()));
+        s->cfg.step_histories / std::max<size_t>(1, phase_jobs));
     std::vector<dose_job> jobs;
     std::vector<int> finishing;
     for (size_t i = 0; i < s->active.size(); ++i) {
         auto &a = s->active[i];
+        if (a.phases.empty()) {                      // nothing delivered: a zero dose
+            finishing.push_back((int)i);
+            continue;
+        }
         const uint64_t end = std::min(a.per_phase, a.next + share);
-        for (int p : s->phases) {
+        for (int p : a.phases) {
             dose_job j;
             j.ctx = s->slots[a.slot].view;
             j.phase = p;
@@ -191,20 +240,20 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
             for (int k = 0; k < 3; ++k) j.shift_mm[k] = a.req.shift_mm[k];
             jobs.push_back(j);
         }
-        s->histories_done += (end - a.next) * s->phases.size();
+        s->histories_done += (end - a.next) * a.phases.size();
         a.next = end;
         if (end == a.per_phase) finishing.push_back((int)i);
     }
-    int rc = dose_run_batch(jobs.data(), (int)jobs.size(), stream);
+    int rc = jobs.empty() ? DOSE_OK : dose_run_batch(jobs.data(), (int)jobs.size(), stream);
     if (rc) return rc;
     for (int i : finishing) {
         auto &a = s->active[i];
         dose_ctx *v = s->slots[a.slot].view;
         int dims[4];
         dose::grid_info(v, dims);
-        // phases the plan does not reach carry zero dose
+        // phases the request's delivery does not reach carry zero dose
         for (int p = 0; p < dims[3]; ++p)
-            if (std::find(s->phases.begin(), s->phases.end(), p) == s->phases.end())
+            if (std::find(a.phases.begin(), a.phases.end(), p) == a.phases.end())
                 if ((rc = dose::set_phase_zero(v, p, stream))) return rc;
         if (s->cfg.accumulate &&
             (rc = dose_accumulate_subvoxel(v, s->cfg.ref_phase, s->cfg.nsub, s->cfg.dvf, 1, nullptr, 0, 0, stream)))

@@ -74,7 +74,7 @@ class dose_server_config(C.Structure):
 
 class dose_request(C.Structure):
     _fields_ = [("n_histories", C.c_uint64), ("seed", C.c_uint64), ("spr_scale", C.c_float),
-                ("shift_mm", C.c_float * 3)]
+                ("shift_mm", C.c_float * 3), ("delivery", C.c_void_p)]
 
 
 class dose_dvf_grid(C.Structure):
@@ -84,7 +84,7 @@ class dose_dvf_grid(C.Structure):
 
 
 assert C.sizeof(dose_spot) == 32 and C.sizeof(dose_job) == 64 and C.sizeof(dose_delivery) == 112
-assert C.sizeof(dose_server_config) == 56 and C.sizeof(dose_request) == 32
+assert C.sizeof(dose_server_config) == 56 and C.sizeof(dose_request) == 40
 
 
 def _load():
@@ -368,8 +368,11 @@ def dose_server_create(base, memory_budget_bytes, step_histories, spots, deliver
     return out.value
 
 
-def dose_server_submit(server, n_histories, seed, spr_scale=1.0, shift_mm=(0.0, 0.0, 0.0)):
-    r = dose_request(int(n_histories), int(seed), float(spr_scale), _f3(shift_mm))
+def dose_server_submit(server, n_histories, seed, spr_scale=1.0, shift_mm=(0.0, 0.0, 0.0), delivery=None):
+    """``delivery``: a ``dose_delivery`` for this request (copied), or None
+    for the server's."""
+    r = dose_request(int(n_histories), int(seed), float(spr_scale), _f3(shift_mm),
+                     C.cast(C.pointer(delivery), C.c_void_p) if delivery is not None else None)
     rid = C.c_int64()
     _check(_lib.dose_server_submit(server, C.byref(r), C.byref(rid)), None)
     return rid.value

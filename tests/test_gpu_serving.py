@@ -113,3 +113,46 @@ def test_server_rejects_bad_input(gpu):
             D.dose_server_destroy(srv)
     finally:
         D.dose_destroy(base)
+
+
+def test_requests_with_their_own_delivery(gpu):
+    """Gating and repainting variants served next to nominal requests: each
+    request's result equals that request computed alone with its delivery
+    (the even split over the phases its delivery reaches)."""
+    D = gpu
+    ph, dvf, spots, dlv, base = _setup(D)
+    shape = ph.hu.shape[1:]
+    common = dict(n_phases=4, start_phase=-1, seed=21, period_ns=20_000_000, spot_switch_ns=200_000,
+                  layer_switch_ns=3_000_000)
+    gated = D.delivery_struct(W.Delivery(**dict(common, gated=1, gate_first=1, gate_last=2, start_phase=0)))
+    repaint = D.delivery_struct(W.Delivery(**dict(common, max_protons_per_paint=300_000)))
+    late = D.delivery_struct(W.Delivery(**dict(common, gated=1, gate_first=3, gate_last=3, start_phase=0)))
+    reqs = [(30_000, 11, None), (20_000, 12, gated), (24_000, 13, repaint), (10_000, 14, None),
+            (16_000, 15, gated), (8_000, 16, late)]
+    srv = D.dose_server_create(base, 1 << 34, 25_000, spots, dlv, min_slice=50, max_active=3, nsub=NSUB, dvf=dvf)
+    out, ids = {}, {}
+    try:
+        for k, (n, seed, d) in enumerate(reqs):
+            ids[D.dose_server_submit(srv, n, seed, delivery=d)] = k
+        steps = 0
+        while len(out) < len(reqs):
+            for rid in D.dose_server_step(srv):
+                out[ids[rid]] = D.dose_server_result(srv, rid, D.DOSE_ACCUM, 0, np.zeros(shape, np.float32))
+                D.dose_server_release(srv, rid)
+            steps += 1
+            assert steps < 10_000
+    finally:
+        D.dose_server_destroy(srv)
+    view = D.dose_create_view(base)
+    try:
+        for k, (n, seed, d) in enumerate(reqs):
+            D.dose_add_spots(view, spots, d if d is not None else dlv)
+            pp = D.dose_read(view, D.DOSE_SUBPLAN, 0, np.zeros((4, len(spots)), np.uint64)).sum(axis=1)
+            reached = int(np.count_nonzero(pp))
+            D.dose_run_4d(view, max(1, n // reached), seed, 0, NSUB, dvf=dvf)
+            alone = D.dose_read(view, D.DOSE_ACCUM, 0, np.zeros(shape, np.float32))
+            np.testing.assert_array_equal(out[k], alone)
+            assert alone.max() > 0
+    finally:
+        D.dose_destroy(view)
+        D.dose_destroy(base)
