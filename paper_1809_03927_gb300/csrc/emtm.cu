@@ -179,8 +179,11 @@ __global__ void k_emtm_sum(EmtmArgs a)
             if (S == a.ref) continue;
             const unsigned long long m = a.M[(size_t)S * nvox + i];
             if (m == 0) continue;
-            const int es = energy_shift(a.maxbits[S]);
-            acc += ldexp((double)a.E[(size_t)S * nvox + i] / (double)m, kMassShift - es);
+            // E / M back to Gy: times 2^(mass shift - energy shift), an exact
+            // power of two built from its exponent bits
+            const int k = kMassShift - energy_shift(a.maxbits[S]);
+            const double q = div64((double)a.E[(size_t)S * nvox + i], (double)m);
+            acc += (k > -1000 && k < 1000) ? q * __longlong_as_double((long long)(1023 + k) << 52) : ldexp(q, k);
         }
         if (a.mask && !a.mask[i]) acc = 0.0;
         a.accum[i] = (float)acc;

@@ -194,6 +194,19 @@ __device__ __forceinline__ float box_muller_first(float ua, float ub)
     return -r * __cosf(a);
 }
 
+// a / b in FP64 for b > 0 without the library's double division (slow on
+// this part's FP64 units): the FP32 reciprocal refined by one Newton-Raphson
+// step y <- y + y (1 - b y) (24 -> ~48 correct bits), then one residual
+// correction of the quotient, q <- q + y (a - b q), which brings it within
+// an ulp of the correctly rounded quotient.
+__device__ __forceinline__ double div64(double a, double b)
+{
+    double y = (double)__frcp_rn((float)b);
+    y = fma(y, fma(-b, y, 1.0), y);
+    const double q = a * y;
+    return fma(y, fma(-b, q, a), q);
+}
+
 __device__ __forceinline__ unsigned long long to_units(float e)
 {
     return __float2ull_rn(e * kQuantum);

@@ -550,7 +550,7 @@ __global__ void k_normalise(const NormJob *__restrict__ jobs)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < J.nvox; i += stride) {
         const unsigned long long t = J.tally[i];
         dep += t;
-        J.dose[i] = (float)((double)t * factor / (double)J.rho[i]);
+        J.dose[i] = (float)div64((double)t * factor, (double)J.rho[i]);
     }
     dep = warp_sum_u64(dep);
     if ((threadIdx.x & 31) == 0 && dep) atomicAdd(J.ledger + LED_DEP, dep);

@@ -485,3 +485,27 @@ def test_material_grid_gives_the_same_tallies(gpu):
             gpu.dose_destroy(ctx)
     assert out[0].sum() > 0
     np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_normalisation_matches_fp64_division(gpu):
+    """D_i = tally_i x (W/N) x 1.602176634e-10 / (2^24 V) / rho_i in FP64,
+    rounded once to FP32: the device's Newton-Raphson quotient gives the
+    correctly rounded FP64 division's float in every voxel (at most 1 ulp
+    off, and only in a vanishing fraction)."""
+    ph = W.slab_phantom(n=64)
+    pl = W.slab_plan(n_layers=4, nx=3, ny=2)
+    r = H.gpu_run(gpu, ph, pl, 400_000, 12)
+    ctx = H.make_ctx(gpu, ph)
+    try:
+        rho = gpu.dose_read(ctx, gpu.DOSE_DENSITY, 0, np.zeros(ph.hu.shape, np.float32))
+    finally:
+        gpu.dose_destroy(ctx)
+    W_, N = int(r["ledger"][7]), int(r["ledger"][5])
+    v = float(np.float32(ph.d[0])) * float(np.float32(ph.d[1])) * float(np.float32(ph.d[2])) / 1000.0
+    factor = W_ / N * 1.602176634e-10 / (16777216.0 * v)
+    want = (r["tally"].astype(np.float64) * factor / rho.astype(np.float64)).astype(np.float32)
+    got = r["dose"]
+    ulp = np.abs(got.view(np.int32).astype(np.int64) - want.view(np.int32).astype(np.int64))
+    assert ulp.max() <= 1
+    assert (ulp > 0).mean() <= 1e-4
+    assert np.count_nonzero(want) > 1000
