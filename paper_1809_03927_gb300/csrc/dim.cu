@@ -16,10 +16,13 @@
 // (i, i+1) otherwise.  The subvoxels are therefore visited by octant: the
 // eight field nodes of an octant's cell are loaded once (24 values) and
 // every subvoxel of the octant is interpolated from registers.  The dose
-// taps of the carried points are arbitrary and go through the L1 cache.
+// taps of the carried points are arbitrary and go through the L1 cache; the
+// eight taps of the last cell are kept, since neighbouring subvoxels mostly
+// land in the same cell of the source dose.
 // Each phase's subvoxel sum is FP32 and the phase sum FP64; the pull needs
 // no atomics, so the result does not depend on the launch.
 #include <cuda_runtime.h>
+#include <climits>
 #include "engine.cuh"
 #include "kernels.h"
 
@@ -29,28 +32,9 @@ namespace {
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
-// Trilinear sample of one FP32 field at index-space point (x, y, z), edge-clamped.
-__device__ __forceinline__ float sample_clamped(const float *__restrict__ c, int nx, int ny, int nz,
-                                                float x, float y, float z)
-{
-    const float fx0 = floorf(x), fy0 = floorf(y), fz0 = floorf(z);
-    const float fx = x - fx0, fy = y - fy0, fz = z - fz0;
-    const int kx = (int)fx0, ky = (int)fy0, kz = (int)fz0;
-    const int x0 = min(max(kx, 0), nx - 1), x1 = min(max(kx + 1, 0), nx - 1);
-    const int y0 = min(max(ky, 0), ny - 1), y1 = min(max(ky + 1, 0), ny - 1);
-    const int z0 = min(max(kz, 0), nz - 1), z1 = min(max(kz + 1, 0), nz - 1);
-    const size_t r00 = ((size_t)z0 * ny + y0) * nx, r10 = ((size_t)z0 * ny + y1) * nx;
-    const size_t r01 = ((size_t)z1 * ny + y0) * nx, r11 = ((size_t)z1 * ny + y1) * nx;
-    const float c00 = lerpf(__ldg(c + r00 + x0), __ldg(c + r00 + x1), fx);
-    const float c10 = lerpf(__ldg(c + r10 + x0), __ldg(c + r10 + x1), fx);
-    const float c01 = lerpf(__ldg(c + r01 + x0), __ldg(c + r01 + x1), fx);
-    const float c11 = lerpf(__ldg(c + r11 + x0), __ldg(c + r11 + x1), fx);
-    return lerpf(lerpf(c00, c10, fy), lerpf(c01, c11, fy), fz);
-}
-
 }  // namespace
 
-__global__ void __launch_bounds__(256, 3) k_dim(DimArgs a)
+__global__ void __launch_bounds__(256, 2) k_dim(DimArgs a)
 {
     const long long nvox = (long long)a.nx * a.ny * a.nz;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,6 +55,8 @@ __global__ void __launch_bounds__(256, 3) k_dim(DimArgs a)
         const float *ds = a.dose + (size_t)S * nvox;
         const float *dv = a.dvf ? a.dvf + (size_t)S * 3 * nvox : nullptr;
         float sum = 0.0f;
+        int ck[3] = {INT_MIN, INT_MIN, INT_MIN};      // cell of the cached dose taps
+        float cv[8];
         for (int oct = 0; oct < 8; ++oct) {
             // this octant's subvoxel index range and field cell, per axis
             int k0[3], k1[3], c0[3], c1[3];
@@ -126,7 +112,24 @@ __global__ void __launch_bounds__(256, 3) k_dim(DimArgs a)
                             ty += lerpf(lerpf(uz[1][0], uz[1][1], fx), lerpf(uz[1][2], uz[1][3], fx), fy);
                             tz += lerpf(lerpf(uz[2][0], uz[2][1], fx), lerpf(uz[2][2], uz[2][3], fx), fy);
                         }
-                        sum += sample_clamped(ds, a.nx, a.ny, a.nz, tx, ty, tz);
+                        // neighbouring subvoxels usually land in the same cell: reuse its taps
+                        const float gx = floorf(tx), gy = floorf(ty), gz = floorf(tz);
+                        const int cx = (int)gx, cy = (int)gy, cz = (int)gz;
+                        if (cx != ck[0] || cy != ck[1] || cz != ck[2]) {
+                            ck[0] = cx; ck[1] = cy; ck[2] = cz;
+                            const int x0 = min(max(cx, 0), a.nx - 1), x1 = min(max(cx + 1, 0), a.nx - 1);
+                            const int y0 = min(max(cy, 0), a.ny - 1), y1 = min(max(cy + 1, 0), a.ny - 1);
+                            const int z0 = min(max(cz, 0), a.nz - 1), z1 = min(max(cz + 1, 0), a.nz - 1);
+                            const size_t r00 = ((size_t)z0 * a.ny + y0) * a.nx, r10 = ((size_t)z0 * a.ny + y1) * a.nx;
+                            const size_t r01 = ((size_t)z1 * a.ny + y0) * a.nx, r11 = ((size_t)z1 * a.ny + y1) * a.nx;
+                            cv[0] = __ldg(ds + r00 + x0); cv[1] = __ldg(ds + r00 + x1);
+                            cv[2] = __ldg(ds + r10 + x0); cv[3] = __ldg(ds + r10 + x1);
+                            cv[4] = __ldg(ds + r01 + x0); cv[5] = __ldg(ds + r01 + x1);
+                            cv[6] = __ldg(ds + r11 + x0); cv[7] = __ldg(ds + r11 + x1);
+                        }
+                        const float hx = tx - gx, hy = ty - gy, hz = tz - gz;
+                        sum += lerpf(lerpf(lerpf(cv[0], cv[1], hx), lerpf(cv[2], cv[3], hx), hy),
+                                     lerpf(lerpf(cv[4], cv[5], hx), lerpf(cv[6], cv[7], hx), hy), hz);
                     }
                 }
             }
