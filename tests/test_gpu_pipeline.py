@@ -103,3 +103,42 @@ def test_readme_example_runs(gpu):
     scope = {}
     exec(compile(code, "README.md", "exec"), scope)
     assert scope["acc"].max() > 0
+
+
+def test_emtm_full_size_properties(gpu):
+    """The EMTM on the 10-phase 256 x 256 x 160 4DCT with (2, 2, 5)
+    subvoxels, properties that hold at any size: with no field the
+    accumulation is the phase sum; with the breathing field, voxels whose
+    whole neighbourhood stays still in every phase keep the phase sum, every
+    subvoxel is pushed once, and the moving region changes the dose."""
+    import torch
+    ph, dvf, geo = W.phantom_4dct()
+    P = ph.n_phases
+    nx, ny, nz = ph.n
+    rng = np.random.default_rng(3)
+    doses = rng.gamma(2.0, 0.5, size=(P, nz, ny, nx)).astype(np.float32)
+    total = doses.astype(np.float64).sum(axis=0)
+    ctx = H.make_ctx(gpu, ph)
+    try:
+        for p in range(P):
+            gpu.dose_set_phase_dose(ctx, p, np.ascontiguousarray(doses[p]))
+        gpu.dose_accumulate_subvoxel(ctx, 0, NSUB)
+        ident = gpu.dose_read(ctx, gpu.DOSE_ACCUM, 0, np.zeros((nz, ny, nx), np.float32))
+        gpu.dose_accumulate_subvoxel(ctx, 0, NSUB, dvf=torch.from_numpy(dvf).cuda())
+        moved = gpu.dose_read(ctx, gpu.DOSE_ACCUM, 0, np.zeros((nz, ny, nx), np.float32))
+        stats = gpu.dose_read(ctx, gpu.DOSE_EMTM_STATS, 0, np.zeros(4, np.uint64))
+    finally:
+        gpu.dose_destroy(ctx)
+    np.testing.assert_allclose(ident, total, rtol=2e-6)
+    still = np.abs(dvf).max(axis=(0, 1)) == 0.0
+    # a voxel is safe when it and its 26 neighbours never move
+    pad = np.pad(still, 1, constant_values=True)
+    safe = np.ones_like(still)
+    for dz in (0, 1, 2):
+        for dy in (0, 1, 2):
+            for dx in (0, 1, 2):
+                safe &= pad[dz:dz + nz, dy:dy + ny, dx:dx + nx]
+    assert safe.mean() > 0.5 and (~safe).sum() > 10_000
+    np.testing.assert_allclose(moved[safe], total[safe], rtol=2e-6)
+    assert not np.allclose(moved[~safe], total[~safe], rtol=1e-3)
+    assert int(stats[0]) == (P - 1) * nx * ny * nz * 20
