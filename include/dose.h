@@ -145,7 +145,8 @@ enum {
     DOSE_STATUS = 6,         /* int32[1]: DOSE_OK or DOSE_ESTEPLIMIT for `phase`     */
     DOSE_START_PHASE = 7,    /* int32[n_fields]  start phase of each field          */
     DOSE_FIELD_END_NS = 8,   /* int64[n_fields]  delivery clock at each field's end */
-    DOSE_EMTM_STATS = 9,     /* uint64[4]: subvoxels pushed, dropped (mapped outside),
+    DOSE_EMTM_STATS = 9,     /* uint64[4]: subvoxels pushed (of the source voxels
+                                within reach of dose), dropped (mapped outside),
                                 atomic pairs issued, reserved                       */
     DOSE_HIST_PREFIX = 10,   /* uint64[n_spots + 1] of phase `phase`: first history of
                                 each spot (histories of spot s = p[s+1] - p[s])      */
@@ -371,7 +372,13 @@ int dose_decode_dvf(dose_ctx *c, const dose_dvf_grid *grid, const float *transla
  * displacement (mm) carrying a reference point to S, given at the reference
  * voxel centres -- the opposite direction to method 0, as the paper notes.
  * Every phase must have a dose.  DOSE_EMTM_STATS is only readable after
- * method 0.                                                                */
+ * method 0.
+ * Both methods visit only what a phase's dose can reach: the box of the
+ * voxels carrying dose (method 0: rho > 0 and D > 0; method 1: D != 0),
+ * grown per axis by m (ceil(max|u| / d) + 2) voxels, u the phase's field,
+ * m = 2 for method 0 (source voxels) and 1 for method 1 (reference voxels).
+ * What lies outside adds exactly zero, so the result is that of visiting
+ * every voxel; DOSE_EMTM_STATS counts the subvoxels within reach.          */
 int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], const float *dvf,
                              int dvf_on_device, const uint8_t *mask, int mask_on_device,
                              int method, void *stream);

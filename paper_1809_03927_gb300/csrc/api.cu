@@ -97,6 +97,7 @@ struct dose_ctx {
     unsigned long long *em = nullptr;        // E then M, n_phases x nvox each
     float *dvf_buf = nullptr;                // staging for host DVFs
     float4 *dvf4 = nullptr;                  // one phase's field, interleaved (EMTM)
+    unsigned *reach = nullptr;               // n_phases x kReachWords (accumulations)
     uint8_t *mask_buf = nullptr;             // staging for a host mask
     float *dvfgrid_e = nullptr;              // decoded registration grid (r_f - r0), 3 x cap
     float *dvfgrid_delta = nullptr;          // staging for host translations, 3 x cap
@@ -1132,13 +1133,24 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
         CK(c, cudaMemcpyAsync(c->mask_buf, mask, nvox, cudaMemcpyHostToDevice, st));
         mask_dev = c->mask_buf;
     }
+    if (!c->reach && (rc = dalloc_t(c, &c->reach, P * kReachWords))) return rc;
+    int sms = 0;
+    CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g.device));
+    CK(c, cudaMemsetAsync(c->reach, 0, P * kReachWords * sizeof(unsigned), st));
+    ReachArgs ra;
+    ra.dose = c->dose_all; ra.rho = method == 0 ? g.rho : nullptr; ra.dvf = dvf_dev;
+    ra.reach = c->reach; ra.maxbits = nullptr;
+    ra.nx = g.n[0]; ra.ny = g.n[1]; ra.nz = g.n[2]; ra.ref = ref_phase;
     if (method == 1) {
+        k_reach<<<dim3((unsigned)(2 * sms), (unsigned)P), 256, 0, st>>>(ra);
+        CK(c, cudaGetLastError());
         DimArgs a;
         a.dose = c->dose_all; a.dvf = dvf_dev; a.mask = mask_dev; a.accum = c->accum;
         a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
         a.idx = 1.0f / g.d[0]; a.idy = 1.0f / g.d[1]; a.idz = 1.0f / g.d[2];
         a.nsx = nsub[0]; a.nsy = nsub[1]; a.nsz = nsub[2];
         a.ref = ref_phase; a.n_phases = (int)P;
+        a.reach = c->reach;
         k_dim<<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(a);
         CK(c, cudaGetLastError());
         c->have_accum = true;
@@ -1150,27 +1162,33 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
     CK(c, cudaMemsetAsync(c->emtm_stats, 0, 4 * sizeof(unsigned long long), st));
     EmtmArgs a;
     a.dose = c->dose_all; a.rho = g.rho; a.mask = mask_dev;
-    a.E = c->em; a.M = c->em + P * nvox; a.maxbits = c->maxbits; a.stats = c->emtm_stats;
+    a.E = c->em; a.M = c->em + P * nvox; a.maxbits = c->maxbits; a.reach = c->reach; a.stats = c->emtm_stats;
     a.accum = c->accum;
     a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
     a.dx = g.d[0]; a.dy = g.d[1]; a.dz = g.d[2];
     a.nsx = nsub[0]; a.nsy = nsub[1]; a.nsz = nsub[2];
     a.ref = ref_phase; a.n_phases = (int)P;
-    k_emtm_max<<<dim3(304, (unsigned)P), 256, 0, st>>>(a);
+    ra.maxbits = c->maxbits;
+    k_reach<<<dim3((unsigned)(2 * sms), (unsigned)P), 256, 0, st>>>(ra);
     CK(c, cudaGetLastError());
     a.dvf4 = nullptr; a.phase = 0;
     a.idx = 1.0f / g.d[0]; a.idy = 1.0f / g.d[1]; a.idz = 1.0f / g.d[2];
+    // grid-stride launches: the voxels within reach are not known on the host
+    int per_sm = 0;
+    CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emtm, 256, 0));
+    const unsigned grid = (unsigned)std::min<size_t>((nvox + 255) / 256, (size_t)sms * std::max(per_sm, 1));
     if (dvf_dev) {
         if (!c->dvf4 && (rc = dalloc_t(c, &c->dvf4, nvox))) return rc;
         for (int S = 0; S < (int)P; ++S) {
             if (S == ref_phase) continue;
-            k_dvf4<<<1216, 256, 0, st>>>(dvf_dev + (size_t)S * 3 * nvox, c->dvf4, (long long)nvox);
+            k_dvf4<<<grid, 256, 0, st>>>(dvf_dev + (size_t)S * 3 * nvox, c->dvf4, c->reach + (size_t)S * kReachWords,
+                                         a.nx, a.ny, a.nz, a.idx, a.idy, a.idz);
             a.dvf4 = c->dvf4; a.phase = S;
-            k_emtm<<<dim3((unsigned)((nvox + 255) / 256), 1), 256, 0, st>>>(a);
+            k_emtm<<<dim3(grid, 1), 256, 0, st>>>(a);
             CK(c, cudaGetLastError());
         }
     } else {
-        k_emtm<<<dim3((unsigned)((nvox + 255) / 256), (unsigned)P), 256, 0, st>>>(a);
+        k_emtm<<<dim3(grid, (unsigned)P), 256, 0, st>>>(a);
         CK(c, cudaGetLastError());
     }
     k_emtm_sum<<<1216, 256, 0, st>>>(a);

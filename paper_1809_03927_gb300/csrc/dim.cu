@@ -20,7 +20,9 @@
 // eight taps of the last cell are kept, since neighbouring subvoxels mostly
 // land in the same cell of the source dose.
 // Each phase's subvoxel sum is FP32 and the phase sum FP64; the pull needs
-// no atomics, so the result does not depend on the launch.
+// no atomics, so the result does not depend on the launch.  A phase adds
+// nothing to the reference voxels out of its reach (reach_box with mult 1,
+// from k_reach over D != 0), which skip it.
 #include <cuda_runtime.h>
 #include <climits>
 #include "engine.cuh"
@@ -52,6 +54,9 @@ __global__ void __launch_bounds__(256, 2) k_dim(DimArgs a)
     double acc = (double)a.dose[(size_t)a.ref * nvox + i];
     for (int S = 0; S < a.n_phases; ++S) {
         if (S == a.ref) continue;
+        // out of reach of the phase's dose: every tap is zero
+        const VoxBox b = reach_box(a.reach + (size_t)S * kReachWords, 1, a.nx, a.ny, a.nz, a.idx, a.idy, a.idz);
+        if (ix < b.lo[0] || ix > b.hi[0] || iy < b.lo[1] || iy > b.hi[1] || iz < b.lo[2] || iz > b.hi[2]) continue;
         const float *ds = a.dose + (size_t)S * nvox;
         const float *dv = a.dvf ? a.dvf + (size_t)S * 3 * nvox : nullptr;
         float sum = 0.0f;

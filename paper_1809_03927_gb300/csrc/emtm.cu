@@ -1,9 +1,12 @@
 // Energy/mass-transfer accumulation (Sec. 2.D.2, Eqs. 4-6 of Pepin et al.)
 // and the phase sum of Eq. 2.
 //
-//   k_emtm_max  largest rho_j D_j of each source phase (fixed-point scale)
-//   k_dvf4      one source phase's field, x/y/z planes -> one float4 per voxel
-//   k_emtm      one thread per source voxel j of that phase: split j into
+//   k_reach     per source phase: the largest rho_j D_j (fixed-point
+//               scale), the box of the voxels that carry dose and the largest
+//               displacement per axis (also run before the DIM)
+//   k_dvf4      one source phase's field, x/y/z planes -> one float4 per
+//               voxel, over the nodes its reach reads
+//   k_emtm      a thread per source voxel j within reach of dose: split j into
 //               nsx x nsy x nsz subvoxels, move each centre by the phase's DVF
 //               (trilinear between voxel centres, edge-clamped; one 16-byte
 //               load per node) and add the subvoxel's mass rho_j and energy
@@ -14,11 +17,18 @@
 //               sums are exact and order-free.
 //   k_emtm_sum  D_i = D_i^R + sum_S E_i^S / M_i^S (0 where M = 0), masked.
 //
+// Source voxels out of reach (reach_box with mult 2) are not pushed: every
+// voxel they can reach receives no energy, so E_i^S = 0 and the term adds
+// exactly zero whatever M_i^S holds.  The result is the same as pushing
+// every voxel; only the counters of pushed and dropped subvoxels count
+// the voxels within reach.
+//
 // The target voxel is decided in single precision with the rounding order
 // written out below (no contraction; the displacement goes to voxel units
 // through the FP32 reciprocal of the voxel size), so it is reproducible bit
 // for bit.
 #include <cuda_runtime.h>
+#include <climits>
 #include <cmath>
 #include "engine.cuh"
 #include "kernels.h"
@@ -50,26 +60,79 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
 }
 }  // namespace
 
-__global__ void k_emtm_max(EmtmArgs a)
+// A warp per row (y, z) of the grid, its lanes along x (coalesced).
+__global__ void k_reach(ReachArgs a)
 {
     const int p = blockIdx.y;
     if (p == a.ref) return;
-    const long long nvox = (long long)a.nx * a.ny * a.nz;
+    const size_t nvox = (size_t)a.nx * a.ny * a.nz;
     const float *d = a.dose + (size_t)p * nvox;
-    const float *r = a.rho + (size_t)p * nvox;
-    float m = 0.0f;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride)
-        m = fmaxf(m, fmaxf(r[i] * d[i], 0.0f));
+    const float *r = a.rho ? a.rho + (size_t)p * nvox : nullptr;
+    const float *u = a.dvf ? a.dvf + (size_t)p * 3 * nvox : nullptr;
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    const unsigned rows = (unsigned)a.ny * (unsigned)a.nz;
+    unsigned lo[3] = {UINT_MAX, UINT_MAX, UINT_MAX}, hi[3] = {0u, 0u, 0u};   // hi: index + 1
+    unsigned um[3] = {0u, 0u, 0u}, mb = 0u;
+    for (unsigned row = blockIdx.x * warps + (threadIdx.x >> 5); row < rows; row += gridDim.x * warps) {
+        const size_t base = (size_t)row * a.nx;
+        bool hit = false;
+        for (int x = lane; x < a.nx; x += 32) {
+            const float dv = d[base + x];
+            bool carries;
+            if (r) {
+                const float rv = r[base + x];
+                mb = max(mb, __float_as_uint(fmaxf(rv * dv, 0.0f)));   // non-negative: bits order as values
+                carries = rv > 0.0f && dv > 0.0f;
+            } else {
+                carries = dv != 0.0f;
+            }
+            if (carries) {
+                lo[0] = min(lo[0], (unsigned)x);
+                hi[0] = max(hi[0], (unsigned)x + 1u);
+                hit = true;
+            }
+            if (u) {
+                um[0] = max(um[0], __float_as_uint(fabsf(u[base + x])));
+                um[1] = max(um[1], __float_as_uint(fabsf(u[nvox + base + x])));
+                um[2] = max(um[2], __float_as_uint(fabsf(u[2 * nvox + base + x])));
+            }
+        }
+        if (hit) {
+            const unsigned y = row % (unsigned)a.ny, z = row / (unsigned)a.ny;
+            lo[1] = min(lo[1], y); hi[1] = max(hi[1], y + 1u);
+            lo[2] = min(lo[2], z); hi[2] = max(hi[2], z + 1u);
+        }
+    }
+    unsigned *w = a.reach + (size_t)p * kReachWords;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(a.maxbits + p, __float_as_uint(m));
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
+        hi[k] = __reduce_max_sync(0xffffffffu, hi[k]);
+        um[k] = __reduce_max_sync(0xffffffffu, um[k]);
+    }
+    mb = __reduce_max_sync(0xffffffffu, mb);
+    if (lane == 0) {
+        if (hi[0]) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                atomicMax(w + k, ~lo[k]);
+                atomicMax(w + 3 + k, hi[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (um[k]) atomicMax(w + 6 + k, um[k]);
+        if (a.maxbits && mb) atomicMax(a.maxbits + p, mb);
+    }
 }
 
+// A grid-stride loop over the source voxels within reach (x fastest).
 __global__ void k_emtm(EmtmArgs a)
 {
     const int S = a.dvf4 ? a.phase : (int)blockIdx.y;
     if (S == a.ref) return;
+    const VoxBox b = reach_box(a.reach + (size_t)S * kReachWords, 2, a.nx, a.ny, a.nz, a.idx, a.idy, a.idz);
+    if (b.lo[0] > b.hi[0]) return;                                   // no dose in this phase
     // the subvoxel-centre fractions (k + 1/2) / n of each axis, once per block
     __shared__ float s_frac[3][64];
     for (int t = threadIdx.x; t < 3 * 64; t += blockDim.x) {
@@ -79,16 +142,18 @@ __global__ void k_emtm(EmtmArgs a)
     }
     __syncthreads();
     const long long nvox = (long long)a.nx * a.ny * a.nz;
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned bx = (unsigned)(b.hi[0] - b.lo[0] + 1), by = (unsigned)(b.hi[1] - b.lo[1] + 1);
+    const unsigned nbox = bx * by * (unsigned)(b.hi[2] - b.lo[2] + 1);   // <= nvox < 2^31
+    const int es = energy_shift(a.maxbits[S]);
     unsigned long long pushed = 0, dropped = 0, pairs = 0;
-    if (j < nvox) {
-        const unsigned ju = (unsigned)j, row = ju / (unsigned)a.nx;      // nvox < 2^31
-        const int jx = (int)(ju - row * (unsigned)a.nx);
-        const int jy = (int)(row % (unsigned)a.ny);
-        const int jz = (int)(row / (unsigned)a.ny);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nbox; k += gridDim.x * blockDim.x) {
+        const unsigned row = k / bx;
+        const int jx = b.lo[0] + (int)(k - row * bx);
+        const int jy = b.lo[1] + (int)(row % by);
+        const int jz = b.lo[2] + (int)(row / by);
+        const long long j = ((long long)jz * a.ny + jy) * a.nx + jx;
         const float rho = a.rho[(size_t)S * nvox + j];
         const float dj = a.dose[(size_t)S * nvox + j];
-        const int es = energy_shift(a.maxbits[S]);
         const double prod = fmax((double)rho * (double)dj, 0.0);
         const unsigned long long eu = __double2ull_rn(ldexp(prod, es));
         const unsigned long long mu = __double2ull_rn(ldexp((double)rho, kMassShift));
@@ -162,11 +227,26 @@ __global__ void k_emtm(EmtmArgs a)
     }
 }
 
-__global__ void k_dvf4(const float *__restrict__ src, float4 *__restrict__ dst, long long nvox)
+__global__ void k_dvf4(const float *__restrict__ src, float4 *__restrict__ dst, const unsigned *reach, int nx,
+                       int ny, int nz, float idx, float idy, float idz)
 {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride)
+    VoxBox b = reach_box(reach, 2, nx, ny, nz, idx, idy, idz);
+    if (b.lo[0] > b.hi[0]) return;
+    const int n[3] = {nx, ny, nz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {                 // the trilinear nodes of the box's subvoxels
+        b.lo[ax] = max(b.lo[ax] - 1, 0);
+        b.hi[ax] = min(b.hi[ax] + 1, n[ax] - 1);
+    }
+    const size_t nvox = (size_t)nx * ny * nz;
+    const unsigned bx = (unsigned)(b.hi[0] - b.lo[0] + 1), by = (unsigned)(b.hi[1] - b.lo[1] + 1);
+    const unsigned nbox = bx * by * (unsigned)(b.hi[2] - b.lo[2] + 1);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nbox; k += gridDim.x * blockDim.x) {
+        const unsigned row = k / bx;
+        const size_t i = ((size_t)(b.lo[2] + (int)(row / by)) * ny + (b.lo[1] + (int)(row % by))) * nx +
+                         (b.lo[0] + (int)(k - row * bx));
         dst[i] = make_float4(src[i], src[nvox + i], src[2 * nvox + i], 0.0f);
+    }
 }
 
 __global__ void k_emtm_sum(EmtmArgs a)

@@ -237,6 +237,36 @@ __device__ __forceinline__ float energy_at_range(const float *er, float r, float
     const float f = x - (float)i;
     return fmaf(f, er[i + 1] - er[i], er[i]);
 }
+
+// The voxels an accumulation of one source phase has to visit: the box of
+// the voxels that carry dose (a reach record, words as k_reach writes them)
+// grown on every axis by `mult` x r voxels, r = ceil(max|u| / d) + 2, and
+// clipped to the grid; empty (lo > hi) when no voxel carries dose.  A point
+// carried by the field moves at most max|u| / d voxels (a trilinear blend
+// of node values cannot exceed their largest magnitude; the FP32 roundings
+// add far less than the one voxel of slack in r), so
+//   DIM  (mult 1): a reference voxel outside the box interpolates only zero
+//        dose taps of the phase;
+//   EMTM (mult 2): a source voxel outside the box can push only to voxels
+//        that receive no energy, whose dose is zero with or without its mass.
+// A non-finite or grid-sized displacement gives the whole axis.
+struct VoxBox { int lo[3], hi[3]; };
+__device__ __forceinline__ VoxBox reach_box(const unsigned *w, int mult, int nx, int ny, int nz,
+                                            float idx, float idy, float idz)
+{
+    VoxBox b;
+    const int n[3] = {nx, ny, nz};
+    const float id[3] = {idx, idy, idz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (w[3] == 0) { b.lo[ax] = 0; b.hi[ax] = -1; continue; }
+        const float dm = __uint_as_float(w[6 + ax]) * id[ax];
+        const int r = dm < (float)n[ax] ? (int)ceilf(dm) + 2 : n[ax];
+        b.lo[ax] = max((int)~w[ax] - mult * r, 0);
+        b.hi[ax] = min((int)w[3 + ax] - 1 + mult * r, n[ax] - 1);
+    }
+    return b;
+}
 #endif  // __CUDACC__
 
 }  // namespace dose

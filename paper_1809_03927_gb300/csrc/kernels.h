@@ -75,12 +75,32 @@ struct TimelineArgs {                // one trial (or the single delivery) of a 
 };
 __global__ void k_timeline(const TimelineArgs *args);
 
+// What an accumulation can reach, per source phase: a record of
+// kReachWords words, zeroed before k_reach fills it.  Words 0-2 hold the
+// bitwise NOT of the lowest x, y, z index of a voxel that carries dose
+// (rho > 0 and D > 0 for the EMTM, D != 0 for the DIM), words 3-5 one past
+// the highest (0: no such voxel), words 6-8 the bits of max |u| per axis
+// (mm) of the phase's field (0 without a field).  reach_box grows it into
+// the voxels the accumulation has to visit.
+constexpr int kReachWords = 12;
+struct ReachArgs {
+    const float *dose;               // n_phases x nvox
+    const float *rho;                // n_phases x nvox (EMTM), or null: the DIM's D != 0
+    const float *dvf;                // n_phases x 3 x nvox (mm), or null
+    unsigned *reach;                 // n_phases x kReachWords, zeroed
+    unsigned *maxbits;               // n_phases: bits of max(rho D) (EMTM), or null
+    int nx, ny, nz;
+    int ref;
+};
+__global__ void k_reach(ReachArgs a);
+
 struct EmtmArgs {
     const float *dose;               // n_phases x nvox
     const float *rho;                // n_phases x nvox
     const uint8_t *mask;             // nvox or null
     unsigned long long *E, *M;       // n_phases x nvox each (slot of the reference unused)
     unsigned *maxbits;               // n_phases: bits of max(rho D) per phase
+    const unsigned *reach;           // n_phases x kReachWords (k_reach)
     unsigned long long *stats;       // 4: pushed, dropped, atomic pairs, reserved
     float *accum;                    // nvox
     int nx, ny, nz;
@@ -91,8 +111,10 @@ struct EmtmArgs {
     int phase;                       // that source phase (grid.y is the phase when dvf4 is null)
     float idx, idy, idz;             // 1 / voxel size, rounded to FP32
 };
-__global__ void k_emtm_max(EmtmArgs a);
-__global__ void k_dvf4(const float *src, float4 *dst, long long nvox);
+// The field nodes the source voxels of reach_box(reach, 2) read (that box
+// grown by one voxel), interleaved; every other node of dst is left as is.
+__global__ void k_dvf4(const float *src, float4 *dst, const unsigned *reach, int nx, int ny, int nz,
+                       float idx, float idy, float idz);
 __global__ void k_emtm(EmtmArgs a);
 __global__ void k_emtm_sum(EmtmArgs a);
 
@@ -105,6 +127,7 @@ struct DimArgs {
     float idx, idy, idz;             // 1 / voxel sizes (mm -> voxels)
     int nsx, nsy, nsz;
     int ref, n_phases;
+    const unsigned *reach;           // n_phases x kReachWords (k_reach over D != 0)
 };
 __global__ void k_dim(DimArgs a);
 

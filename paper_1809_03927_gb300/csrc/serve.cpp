@@ -78,7 +78,7 @@ size_t slot_footprint(int nx, int ny, int nz, int n_phases, int64_t n_spots, boo
 {
     const size_t nvox = (size_t)nx * ny * nz, P = (size_t)n_phases;
     size_t b = P * nvox * (8 + 4) + P * 64;
-    if (accumulate) b += 2 * P * nvox * 8 + nvox * 4 + P * 4 + 64 + nvox * 4 + nvox * 16;
+    if (accumulate) b += 2 * P * nvox * 8 + nvox * 4 + P * 4 + 64 + nvox * 4 + nvox * 16 + P * 48;
     b += P * (size_t)(n_spots + 1) * (8 + 4 + 8) + (size_t)n_spots * (16 + 8 + 4 + 4 + 8 * P) + (1 << 20);
     return b;
 }

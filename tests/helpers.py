@@ -154,3 +154,27 @@ def gamma_pass(ref, evl, spacing, dd=0.01, dta=1.0, threshold=0.1, step=0.25):
 def small_4dct(n_phases=4, nx=64, ny=64, nz=40, motion_pp=15.0):
     ph, dvf, geo = W.phantom_4dct(nx, ny, nz, (1.0, 1.0, 2.5), n_phases=n_phases, motion_pp=motion_pp)
     return ph, dvf, geo
+
+
+def reach_box(carries, field, d, mult):
+    """The voxel box an accumulation of one source phase visits, as the
+    engine's header defines it: the (x, y, z) box of the voxels that carry
+    dose grown by mult x (ceil(max|u| / d) + 2) per axis in FP32, clipped to
+    the grid; None when no voxel carries dose.  carries is (nz, ny, nx)
+    bool, field (3, nz, ny, nx) mm or None."""
+    if not carries.any():
+        return None
+    n = carries.shape[::-1]
+    box = []
+    for ax in range(3):
+        other = tuple(a for a in range(3) if a != 2 - ax)
+        idx = np.nonzero(carries.any(axis=other))[0]
+        v = np.float32(np.abs(field[ax]).max()) if field is not None else np.float32(0.0)
+        dm = np.float32(v * (np.float32(1.0) / np.float32(d[ax])))
+        r = int(np.ceil(dm)) + 2 if dm < n[ax] else n[ax]
+        box.append((max(int(idx[0]) - mult * r, 0), min(int(idx[-1]) + mult * r, n[ax] - 1)))
+    return box
+
+
+def box_voxels(box):
+    return 0 if box is None else int(np.prod([hi - lo + 1 for lo, hi in box]))

@@ -83,6 +83,31 @@ def test_dim_parity(gpu, orc, case, nsub):
         assert np.all(acc[mask == 0] == 0.0)
 
 
+@pytest.mark.parametrize("case", ["blob", "corner", "empty_phase", "far_field"])
+def test_dim_sparse_dose_reach(gpu, orc, case):
+    """Doses with compact support: reference voxels out of a phase's reach
+    skip it, and the pull still matches the oracle's DIM of every voxel."""
+    rng = np.random.default_rng(sum(map(ord, case)))
+    P = 4
+    doses = rng.gamma(2.0, 0.5, size=(P,) + SHAPE).astype(np.float32)
+    keep = np.zeros(doses.shape, bool)
+    if case == "corner":
+        keep[:, -3:, :4, -2:] = True
+    elif case == "empty_phase":
+        keep[:, 5:12, 8:16, 10:20] = True
+        keep[3] = False
+    else:
+        keep[:, 5:12, 8:16, 10:20] = True
+    doses = np.where(keep, doses, np.float32(0.0)).astype(np.float32)
+    dvf = _smooth_field(rng, P, SHAPE, D3, 30.0 if case == "far_field" else 1.5)
+    acc = _gpu_dim(gpu, doses, 0, (2, 2, 5), dvf=dvf)
+    want = orc.dim(doses, D3, 0, (2, 2, 5), dvf=dvf)
+    _close(acc, want)
+    assert acc.max() > 0
+    # the phase sum reaches beyond the reference phase's own dose
+    assert np.count_nonzero(acc) > np.count_nonzero(doses[0])
+
+
 def test_dim_identity_n1_is_the_exact_phase_sum(gpu):
     """At n = 1 with no field every subvoxel centre is a voxel centre, so
     the interpolation returns the voxel value exactly and the accumulated

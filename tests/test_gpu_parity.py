@@ -450,6 +450,49 @@ def test_emtm_parity(gpu, orc, case):
         np.testing.assert_allclose(acc, doses.astype(np.float64).sum(axis=0), rtol=2e-6)
 
 
+@pytest.mark.parametrize("case", ["blob", "corner", "empty_phase", "far_field", "identity"])
+def test_emtm_sparse_dose_reach(gpu, orc, case):
+    """Doses with compact support, as a Monte Carlo gives them: the kernel
+    pushes only the source voxels within reach of dose (the header's reach
+    box), and the accumulated dose is still the oracle's push of every
+    voxel; the pushed count is the reach boxes' volume times the subvoxels."""
+    ph, dvf, doses, rho = _emtm_inputs(orc)
+    P = doses.shape[0]
+    keep = np.zeros(doses.shape, bool)                       # (phase, z, y, x)
+    if case == "corner":
+        keep[:, :3, -4:, :2] = True
+    elif case == "empty_phase":
+        keep[:, 15:22, 30:40, 5:12] = True
+        keep[2] = False
+    else:
+        keep[:, 10:20, 20:35, 25:40] = True
+    doses = np.where(keep, doses, np.float32(0.0)).astype(np.float32)
+    field = None if case == "identity" else (dvf * np.float32(12.0) if case == "far_field" else dvf)
+    nsub = (2, 2, 5)
+    ctx = H.make_ctx(gpu, ph)
+    try:
+        for p in range(P):
+            gpu.dose_set_phase_dose(ctx, p, np.ascontiguousarray(doses[p]))
+        gpu.dose_accumulate_subvoxel(ctx, 0, nsub, dvf=field)
+        acc = gpu.dose_read(ctx, gpu.DOSE_ACCUM, 0, np.zeros(doses.shape[1:], np.float32))
+        stats = gpu.dose_read(ctx, gpu.DOSE_EMTM_STATS, 0, np.zeros(4, np.uint64))
+    finally:
+        gpu.dose_destroy(ctx)
+    want, dropped = orc.emtm(doses, rho, ph.d, 0, nsub, dvf=field)
+    np.testing.assert_allclose(acc, want, rtol=2e-6, atol=1e-9)
+    assert acc.max() > 0 and int(stats[1]) <= dropped
+    boxes = [H.reach_box((rho[p] > 0) & (doses[p] > 0), None if field is None else field[p], ph.d, 2)
+             for p in range(1, P)]
+    assert int(stats[0]) == 20 * sum(H.box_voxels(b) for b in boxes)
+    nvox = doses[0].size
+    if case == "far_field":                                 # motion past the grid: the whole z axis
+        assert all(b[2] == (0, doses.shape[1] - 1) for b in boxes)
+    else:
+        assert int(stats[0]) < (P - 1) * nvox * 20 // 2
+    if case == "empty_phase":
+        assert boxes[1] is None
+
+
 def test_autotune_keeps_results(gpu):
     """The autotuner only picks a launch shape: tallies are bit-identical."""
     ph = W.slab_phantom(n=48)
