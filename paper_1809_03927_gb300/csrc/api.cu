@@ -1157,7 +1157,6 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
         c->accum_method = 1;
         return DOSE_OK;
     }
-    CK(c, cudaMemsetAsync(c->em, 0, 2 * P * nvox * sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(c->maxbits, 0, P * sizeof(unsigned), st));
     CK(c, cudaMemsetAsync(c->emtm_stats, 0, 4 * sizeof(unsigned long long), st));
     EmtmArgs a;
@@ -1177,6 +1176,8 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
     int per_sm = 0;
     CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emtm, 256, 0));
     const unsigned grid = (unsigned)std::min<size_t>((nvox + 255) / 256, (size_t)sms * std::max(per_sm, 1));
+    k_emtm_zero<<<dim3((unsigned)(4 * sms), (unsigned)P), 256, 0, st>>>(a);
+    CK(c, cudaGetLastError());
     if (dvf_dev) {
         if (!c->dvf4 && (rc = dalloc_t(c, &c->dvf4, nvox))) return rc;
         for (int S = 0; S < (int)P; ++S) {
@@ -1191,7 +1192,10 @@ int dose_accumulate_subvoxel(dose_ctx *c, int ref_phase, const int nsub[3], cons
         k_emtm<<<dim3(grid, (unsigned)P), 256, 0, st>>>(a);
         CK(c, cudaGetLastError());
     }
-    k_emtm_sum<<<1216, 256, 0, st>>>(a);
+    const size_t sum_smem = P * 8 * sizeof(int);
+    if (sum_smem > 48 * 1024)
+        CK(c, cudaFuncSetAttribute(k_emtm_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sum_smem));
+    k_emtm_sum<<<1216, 256, sum_smem, st>>>(a);
     CK(c, cudaGetLastError());
     c->have_accum = true;
     c->accum_method = 0;

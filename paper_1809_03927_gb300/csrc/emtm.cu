@@ -15,6 +15,7 @@
 //               subvoxels landing in the same voxel are summed in registers
 //               and pushed with one pair of 64-bit integer atomics, so the
 //               sums are exact and order-free.
+//   k_emtm_zero E and M cleared where the sum reads them
 //   k_emtm_sum  D_i = D_i^R + sum_S E_i^S / M_i^S (0 where M = 0), masked.
 //
 // Source voxels out of reach (reach_box with mult 2) are not pushed: every
@@ -249,14 +250,52 @@ __global__ void k_dvf4(const float *__restrict__ src, float4 *__restrict__ dst, 
     }
 }
 
+// Zeroes E and M of each source phase (grid.y) where mass can land: a
+// pushed source voxel lies in reach_box(mult 2) and moves at most r - 1
+// voxels, so every target is inside reach_box(mult 3).  Elsewhere the
+// arrays are neither written nor read.
+__global__ void k_emtm_zero(EmtmArgs a)
+{
+    const int S = blockIdx.y;
+    if (S == a.ref) return;
+    const VoxBox b = reach_box(a.reach + (size_t)S * kReachWords, 3, a.nx, a.ny, a.nz, a.idx, a.idy, a.idz);
+    if (b.lo[0] > b.hi[0]) return;
+    const size_t nvox = (size_t)a.nx * a.ny * a.nz;
+    unsigned long long *E = a.E + (size_t)S * nvox, *M = a.M + (size_t)S * nvox;
+    const unsigned bx = (unsigned)(b.hi[0] - b.lo[0] + 1), by = (unsigned)(b.hi[1] - b.lo[1] + 1);
+    const unsigned nbox = bx * by * (unsigned)(b.hi[2] - b.lo[2] + 1);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nbox; k += gridDim.x * blockDim.x) {
+        const unsigned row = k / bx;
+        const size_t i = ((size_t)(b.lo[2] + (int)(row / by)) * a.ny + (b.lo[1] + (int)(row % by))) * a.nx +
+                         (b.lo[0] + (int)(k - row * bx));
+        E[i] = 0ull;
+        M[i] = 0ull;
+    }
+}
+
+// Dynamic shared memory: 8 ints per phase (the mult-3 reach box of each
+// source phase, lo[3] and hi[3]; empty for the reference).
 __global__ void k_emtm_sum(EmtmArgs a)
 {
+    extern __shared__ int s_box[];
+    for (int S = threadIdx.x; S < a.n_phases; S += blockDim.x) {
+        VoxBox b = reach_box(a.reach + (size_t)S * kReachWords, 3, a.nx, a.ny, a.nz, a.idx, a.idy, a.idz);
+        if (S == a.ref) { b.lo[0] = 0; b.hi[0] = -1; }
+        for (int k = 0; k < 3; ++k) {
+            s_box[8 * S + k] = b.lo[k];
+            s_box[8 * S + 3 + k] = b.hi[k];
+        }
+    }
+    __syncthreads();
     const long long nvox = (long long)a.nx * a.ny * a.nz;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvox; i += stride) {
+        const unsigned iu = (unsigned)i, row = iu / (unsigned)a.nx;      // nvox < 2^31
+        const int x = (int)(iu - row * (unsigned)a.nx), y = (int)(row % (unsigned)a.ny), z = (int)(row / (unsigned)a.ny);
         double acc = (double)a.dose[(size_t)a.ref * nvox + i];
         for (int S = 0; S < a.n_phases; ++S) {
-            if (S == a.ref) continue;
+            const int *bb = s_box + 8 * S;
+            if (x < bb[0] || x > bb[3] || y < bb[1] || y > bb[4] || z < bb[2] || z > bb[5]) continue;
             const unsigned long long m = a.M[(size_t)S * nvox + i];
             if (m == 0) continue;
             // E / M back to Gy: times 2^(mass shift - energy shift), an exact

@@ -116,7 +116,8 @@ struct EmtmArgs {
 __global__ void k_dvf4(const float *src, float4 *dst, const unsigned *reach, int nx, int ny, int nz,
                        float idx, float idy, float idz);
 __global__ void k_emtm(EmtmArgs a);
-__global__ void k_emtm_sum(EmtmArgs a);
+__global__ void k_emtm_zero(EmtmArgs a);
+__global__ void k_emtm_sum(EmtmArgs a);        // dynamic shared memory: 32 B per phase
 
 struct DimArgs {
     const float *dose;               // n_phases x nvox

@@ -550,7 +550,9 @@ __global__ void k_normalise(const NormJob *__restrict__ jobs)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < J.nvox; i += stride) {
         const unsigned long long t = J.tally[i];
         dep += t;
-        J.dose[i] = (float)div64((double)t * factor, (double)J.rho[i]);
+        // most voxels of a beam's grid hold no energy: their dose is +0
+        // without the FP64 quotient (or the density read)
+        J.dose[i] = t ? (float)div64((double)t * factor, (double)J.rho[i]) : 0.0f;
     }
     dep = warp_sum_u64(dep);
     if ((threadIdx.x & 31) == 0 && dep) atomicAdd(J.ledger + LED_DEP, dep);

@@ -493,6 +493,30 @@ def test_emtm_sparse_dose_reach(gpu, orc, case):
         assert boxes[1] is None
 
 
+def test_emtm_after_a_dense_accumulation(gpu, orc):
+    """E and M are cleared only where a pushed subvoxel can land: a sparse
+    accumulation after a dense one on the same context (stale sums
+    everywhere) still equals the oracle, and so does the dense one again."""
+    ph, dvf, dense, rho = _emtm_inputs(orc)
+    keep = np.zeros(dense.shape, bool)
+    keep[:, 12:18, 25:33, 30:38] = True
+    sparse = np.where(keep, dense, np.float32(0.0)).astype(np.float32)
+    ctx = H.make_ctx(gpu, ph)
+    got = []
+    try:
+        for doses in (dense, sparse, dense):
+            for p in range(doses.shape[0]):
+                gpu.dose_set_phase_dose(ctx, p, np.ascontiguousarray(doses[p]))
+            gpu.dose_accumulate_subvoxel(ctx, 0, (2, 2, 5), dvf=dvf)
+            got.append(gpu.dose_read(ctx, gpu.DOSE_ACCUM, 0, np.zeros(dense.shape[1:], np.float32)))
+    finally:
+        gpu.dose_destroy(ctx)
+    for acc, doses in zip(got, (dense, sparse, dense)):
+        want, _ = orc.emtm(doses, rho, ph.d, 0, (2, 2, 5), dvf=dvf)
+        np.testing.assert_allclose(acc, want, rtol=2e-6, atol=1e-9)
+    np.testing.assert_array_equal(got[0], got[2])
+
+
 def test_autotune_keeps_results(gpu):
     """The autotuner only picks a launch shape: tallies are bit-identical."""
     ph = W.slab_phantom(n=48)
