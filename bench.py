@@ -40,11 +40,11 @@ WORKLOAD = "slab phantom 128^3 at 2 mm (water/lung/bone), 400 spots on 10 layers
 # quantisation 5, bookkeeping 10
 OPS_PER_STEP = 230
 # DRAM bytes (read + write) of one transport launch on the slab workload
-# (1e7 histories; 64-register variant, 1024-thread blocks, chunk 32, HU +
-# table): ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the
-# full-size launch, 2.70 MB read, 0 written (the grid is read once, the
-# tally stays in L2)
-TRANSPORT_DRAM = {"bytes": 2.70e6, "shape": (1, 1024, 32, 0)}
+# (1e7 histories) in the shape it was measured in (registers variant,
+# block, chunk, material grid): ncu --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum on the full-size launch, 2.71 MB read, 0 written
+# (the grid is read once, the tally stays in L2)
+TRANSPORT_DRAM = {"bytes": 2.71e6, "shape": (1, 1024, 32, 0)}
 
 
 def _args():

@@ -915,18 +915,18 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         auto kern = c0->regs ? k_transport_r64 : k_transport;
         if (!c0->regs && c0->block > 512)
             return fail(c0, DOSE_EINVAL, "block %d needs the 64-register variant (DOSE_OPT_REGISTERS 1)", c0->block);
-        CK(c0, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransportMax));
+        CK(c0, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemTransportMax + birth_smem(1024))));
         int sms = 0;
         CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->g->device));
         // stage the job table in shared memory unless that costs resident blocks
-        const size_t smem_plain = transport_smem(kMaxStagedJobs + 1);
+        const size_t smem_plain = transport_smem(kMaxStagedJobs + 1) + birth_smem(c0->block);
         int fit_plain = 0, fit_staged = 0;
         CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_plain, kern, c0->block, smem_plain));
         if ((int)tj.size() <= kMaxStagedJobs)
             CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_staged, kern, c0->block,
-                                                                 transport_smem((int)tj.size())));
+                                                                 transport_smem((int)tj.size()) + birth_smem(c0->block)));
         const int stage = fit_staged > 0 && fit_staged >= fit_plain ? 1 : 0;
-        const size_t smem = stage ? transport_smem((int)tj.size()) : smem_plain;
+        const size_t smem = stage ? transport_smem((int)tj.size()) + birth_smem(c0->block) : smem_plain;
         int per_sm = c0->blocks_per_sm;
         if (per_sm <= 0) per_sm = stage ? fit_staged : fit_plain;
         if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
@@ -986,8 +986,8 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
     j.shift_mm[0] = j.shift_mm[1] = j.shift_mm[2] = 0.0f;
     c->blocks_per_sm = 0;
     // the occupancy query needs the kernels' dynamic shared-memory limit set
-    CK(c, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransportMax));
-    CK(c, cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransportMax));
+    CK(c, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemTransportMax + birth_smem(1024))));
+    CK(c, cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemTransportMax + birth_smem(1024))));
     // allocate the phase's histories once; each trial then only transports
     j.flags = DOSE_JOB_CLEAR; j.hist_begin = 0; j.hist_end = 0;
     if ((rc = dose_run_batch(&j, 1, stream))) goto done;
@@ -996,7 +996,7 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
             if (!regs && b > 512) continue;
             int fits = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, regs ? k_transport_r64 : k_transport, b,
-                                                              transport_smem(1)) != cudaSuccess || fits <= 0) {
+                                                              transport_smem(1) + birth_smem(b)) != cudaSuccess || fits <= 0) {
                 cudaGetLastError();
                 continue;
             }

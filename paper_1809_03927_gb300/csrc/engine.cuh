@@ -77,12 +77,13 @@ struct alignas(16) TJob {
     unsigned long long work_begin;      // offset in the launch's work index
 };
 
-// A transport launch may stage the descriptors and per-job counters
-// (escaped, removed, steps, flags) of up to kMaxStagedJobs jobs in shared
-// memory after the tables; transport_smem(n) is then its dynamic shared
-// memory.  The launcher stages only where that costs no resident blocks,
-// else passes transport_smem(kMaxStagedJobs + 1) (the tables alone) and
-// the kernel reads the jobs from global memory.
+// A transport launch's dynamic shared memory holds the physics tables, the
+// warps' birth buffers (birth_smem(block)) and, when staged, the descriptors
+// and per-job counters (escaped, removed, steps, flags) of up to
+// kMaxStagedJobs jobs: transport_smem(n) + birth_smem(block).  The launcher
+// stages only where that costs no resident blocks, else passes
+// transport_smem(kMaxStagedJobs + 1) + birth_smem(block) (no jobs) and the
+// kernel reads the jobs from global memory.
 constexpr int kMaxStagedJobs = 256;
 static_assert(sizeof(TJob) % 8 == 0, "job counters follow the descriptors 8-byte aligned");
 __host__ __device__ constexpr size_t transport_smem(int n_jobs)
@@ -90,6 +91,14 @@ __host__ __device__ constexpr size_t transport_smem(int n_jobs)
     return kSmemTables + (n_jobs <= kMaxStagedJobs ? (size_t)n_jobs * (sizeof(TJob) + 4 * sizeof(unsigned long long)) : 0);
 }
 constexpr size_t kSmemTransportMax = transport_smem(kMaxStagedJobs);
+// Per warp, a buffer of 32 born histories between the tables and the staged
+// jobs: kBirthWords planes (position, direction, energy, nuclear path, weight,
+// voxel, job, history index) of 32 slots per warp.
+constexpr int kBirthWords = 15;
+__host__ __device__ constexpr size_t birth_smem(int block)
+{
+    return (size_t)(block / 32) * 32 * kBirthWords * sizeof(float);
+}
 
 struct AllocJob {
     const unsigned long long *protons;  // n_spots, this phase's subplan

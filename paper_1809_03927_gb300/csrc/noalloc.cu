@@ -79,7 +79,7 @@ int setup(int dev, unsigned char **base)
     if (e != cudaSuccess) return fail(DOSE_ECUDA, "cudaGetSymbolAddress", e);
     e = cudaMemcpy(p + kOffTables, &g_host_tab, sizeof(Tables), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(DOSE_ECUDA, "table upload", e);
-    e = cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTransportMax);
+    e = cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemTransportMax + birth_smem(1024)));
     if (e != cudaSuccess) return fail(DOSE_ECUDA, "cudaFuncSetAttribute", e);
     g_base[dev] = p;
     *base = p;
@@ -217,12 +217,12 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
     int sms = 0, per_sm = 0;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport_r64, 1024, transport_smem(1));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport_r64, 1024, transport_smem(1) + birth_smem(1024));
     if (e != cudaSuccess || per_sm <= 0) return fail(DOSE_ECUDA, "transport launch set-up", e);
     unsigned chunk = 256;
     const unsigned long long warps = (unsigned long long)sms * per_sm * 32;
     while (chunk > 32 && (unsigned long long)chunk * warps * 4 > n_histories) chunk >>= 1;
-    k_transport_r64<<<sms * per_sm, 1024, transport_smem(1), st>>>(d_t, 1, n_histories, d_counter, d_tab, g_inv_ds, chunk, 1);
+    k_transport_r64<<<sms * per_sm, 1024, transport_smem(1) + birth_smem(1024), st>>>(d_t, 1, n_histories, d_counter, d_tab, g_inv_ds, chunk, 1);
     k_normalise_hu<<<304, 256, 0, st>>>(tally, d_ledger, hu, d_tab, dose, nvox, n_histories,
                                         (double)dx_mm * dy_mm * dz_mm / 1000.0);
     e = cudaGetLastError();

@@ -14,7 +14,6 @@ namespace dose {
 
 namespace {
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRefillMin = 6;        // idle lanes that trigger a warp's refill
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 {
@@ -181,12 +180,16 @@ __device__ __forceinline__ float highland_g(float u)
 }  // namespace
 
 // Persistent kernel: every warp pulls `chunk` consecutive work items (one
-// history each) from a global counter and keeps its 32 lanes busy: when a
-// lane's history ends it takes the next unclaimed item of the warp's chunk
-// (ranked by ballot), so lanes are refilled as they die.  The loop ends when
-// the counter passes `total` and every lane of the warp is idle.  Every
-// history is a pure function of (seed, history index, stream), so results do
-// not depend on the launch shape, on the chunking or on the batching.
+// history each) from a global counter and keeps its 32 lanes busy.  Births
+// are made 32 at a time by the whole warp (every lane computes the birth of
+// one work item; those that start inside the grid go, ranked by ballot, into
+// the warp's buffer in shared memory), and a lane whose history ends takes
+// the next buffered birth at once.  A birth therefore runs with all lanes
+// active, and a dead lane idles only while its warp finishes the step.  The
+// loop ends when the counter passes `total`, the buffer is empty and every
+// lane of the warp is idle.  Every history is a pure function of (seed,
+// history index, stream), so results do not depend on the launch shape, on
+// the chunking, on the buffering or on the batching.
 __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, int n_jobs,
                                                unsigned long long total,
                                                unsigned long long *__restrict__ counter,
@@ -194,10 +197,13 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                                                unsigned chunk, int stage)
 {
     extern __shared__ int4 smem[];
-    TJob *s_jobs = reinterpret_cast<TJob *>(reinterpret_cast<char *>(smem) + kSmemTables);
+    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    const size_t birth_bytes = birth_smem(blockDim.x);
+    float *bbuf = reinterpret_cast<float *>(reinterpret_cast<char *>(smem) + kSmemTables);
+    TJob *s_jobs = reinterpret_cast<TJob *>(reinterpret_cast<char *>(smem) + kSmemTables + birth_bytes);
     const bool staged = stage != 0;                   // the launch gave transport_smem(n_jobs)
     unsigned long long *s_led = reinterpret_cast<unsigned long long *>(
-        reinterpret_cast<char *>(smem) + kSmemTables + (staged ? n_jobs : 0) * sizeof(TJob));
+        reinterpret_cast<char *>(smem) + kSmemTables + birth_bytes + (staged ? n_jobs : 0) * sizeof(TJob));
     {
         const int4 *src = reinterpret_cast<const int4 *>(gtab);
         for (int i = threadIdx.x; i < (int)(kSmemTables / 16); i += blockDim.x) smem[i] = src[i];
@@ -217,6 +223,9 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
     const TJob *jt = staged ? s_jobs : jobs;
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    // word f of buffer slot k of this warp
+    float *wb = bbuf + warp * 32;
+    const int plane = nwarps * 32;
 
     // Per-job counters: escaped and removed energy, steps, flags.  Staged
     // launches add them in shared memory and flush once per block.
@@ -237,88 +246,116 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
     // warp-uniform queue state
     unsigned long long pool_next = 0, pool_end = 0;
     bool queue_done = false;
+    int n_buf = 0;                                   // births waiting in this warp's buffer
 
     for (;;) {
-        // ---------------- refill idle lanes from the warp's chunk
-        // (a warp refills only once kRefillMin lanes are idle, or all are:
-        // the refill runs with the idle lanes only, so batching them
-        // amortises it over more histories)
-        unsigned need = __ballot_sync(kFull, !alive);
-        if (__popc(need) < kRefillMin && need != kFull) need = 0;
-        while (need && !queue_done) {
-            if (pool_next >= pool_end) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(counter, (unsigned long long)chunk);
-                base = __shfl_sync(kFull, base, 0);
-                if (base >= total) { queue_done = true; break; }
-                pool_next = base;
-                pool_end = min(base + (unsigned long long)chunk, total);
-            }
-            const unsigned rank = __popc(need & lt_mask);
-            const unsigned long long avail = pool_end - pool_next;
-            if (!alive && rank < avail) {
-                const unsigned long long w = pool_next + rank;
-                int lo = 0, hi = n_jobs;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (jt[mid].work_begin <= w) lo = mid; else hi = mid;
+        // ---------------- idle lanes take the next born histories; when the
+        // buffer is empty the whole warp births the next 32 work items
+        unsigned dead = __ballot_sync(kFull, !alive);
+        while (dead) {
+            if (n_buf == 0) {
+                if (queue_done) break;
+                if (pool_next >= pool_end) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(counter, (unsigned long long)chunk);
+                    base = __shfl_sync(kFull, base, 0);
+                    if (base >= total) { queue_done = true; break; }
+                    pool_next = base;
+                    pool_end = min(base + (unsigned long long)chunk, total);
                 }
-                const TJob &J = jt[lo];
-                job = lo;
-                h = J.hist_begin + (w - J.work_begin);
-                const int S = J.n_spots;
-                const unsigned long long *prefix = J.prefix;
-                if (h < prefix[S]) {
-                    int a = 0, b = S;
-                    while (b - a > 1) {
-                        const int m = (a + b) >> 1;
-                        if (prefix[m] <= h) a = m; else b = m;
+                const unsigned long long avail = pool_end - pool_next;
+                bool ok = false;
+                float bpx = 0, bpy = 0, bpz = 0, bux = 0, buy = 0, buz = 0, bE = 0, beta = 0, bwh = 0;
+                int bix = 0, biy = 0, biz = 0, bjob = 0;
+                unsigned long long bh = 0;
+                if (lane < avail) {
+                    const unsigned long long w = pool_next + lane;
+                    int lo = 0, hi = n_jobs;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (jt[mid].work_begin <= w) lo = mid; else hi = mid;
                     }
-                    const float4 sp = J.spot[a];
-                    wh = J.wh[a];
-                    E = sp.z;
-                    const U6 u = uniforms6(philox4x32_10(
-                        make_uint4(0u, (unsigned)h, (unsigned)(h >> 32), J.stream), J.key0, J.key1));
-                    const float2 z = box_muller(u.u[0], u.u[1]);
-                    eta = -__logf(u.u[2]);
-                    // the spot's field may enter along its own grid axis
-                    int ax = J.beam_axis, sg = J.beam_sign;
-                    if (J.spot_dir) {
-                        const unsigned code = J.spot_dir[a];
-                        ax = (int)(code >> 1);
-                        sg = (code & 1u) ? 1 : -1;
-                    }
-                    const float lb = sp.x - J.o[ax == 0 ? 1 : 0] + sp.w * z.x;
-                    const float lc = sp.y - J.o[ax == 2 ? 1 : 2] + sp.w * z.y;
-                    const int nx = J.nx, ny = J.ny, nz = J.nz;
-                    const float dx = J.dx, dy = J.dy, dz = J.dz;
-                    bool inside;
-                    ux = uy = uz = 0.0f;
-                    if (ax == 2) {
-                        inside = lb >= 0.0f && lb < nx * dx && lc >= 0.0f && lc < ny * dy;
-                        px = lb; py = lc; pz = sg > 0 ? 0.0f : nz * dz; uz = (float)sg;
-                        ix = (int)floorf(px * J.idx); iy = (int)floorf(py * J.idy); iz = sg > 0 ? 0 : nz - 1;
-                    } else if (ax == 1) {
-                        inside = lb >= 0.0f && lb < nx * dx && lc >= 0.0f && lc < nz * dz;
-                        px = lb; pz = lc; py = sg > 0 ? 0.0f : ny * dy; uy = (float)sg;
-                        ix = (int)floorf(px * J.idx); iz = (int)floorf(pz * J.idz); iy = sg > 0 ? 0 : ny - 1;
-                    } else {
-                        inside = lb >= 0.0f && lb < ny * dy && lc >= 0.0f && lc < nz * dz;
-                        py = lb; pz = lc; px = sg > 0 ? 0.0f : nx * dx; ux = (float)sg;
-                        iy = (int)floorf(py * J.idy); iz = (int)floorf(pz * J.idz); ix = sg > 0 ? 0 : nx - 1;
-                    }
-                    // guard the floor against rounding at the far faces
-                    ix = min(max(ix, 0), nx - 1); iy = min(max(iy, 0), ny - 1); iz = min(max(iz, 0), nz - 1);
-                    if (inside) {
-                        uth = 0.0f; gth = 0.0f; step = 0;
-                        alive = true;
-                    } else {
-                        led_add(job, 0, to_units(E * wh));
+                    const TJob &J = jt[lo];
+                    bjob = lo;
+                    bh = J.hist_begin + (w - J.work_begin);
+                    const int S = J.n_spots;
+                    const unsigned long long *prefix = J.prefix;
+                    if (bh < prefix[S]) {
+                        int a = 0, b = S;
+                        while (b - a > 1) {
+                            const int m = (a + b) >> 1;
+                            if (prefix[m] <= bh) a = m; else b = m;
+                        }
+                        const float4 sp = J.spot[a];
+                        bwh = J.wh[a];
+                        bE = sp.z;
+                        const U6 u = uniforms6(philox4x32_10(
+                            make_uint4(0u, (unsigned)bh, (unsigned)(bh >> 32), J.stream), J.key0, J.key1));
+                        const float2 z = box_muller(u.u[0], u.u[1]);
+                        beta = -__logf(u.u[2]);
+                        // the spot's field may enter along its own grid axis
+                        int ax = J.beam_axis, sg = J.beam_sign;
+                        if (J.spot_dir) {
+                            const unsigned code = J.spot_dir[a];
+                            ax = (int)(code >> 1);
+                            sg = (code & 1u) ? 1 : -1;
+                        }
+                        const float lb = sp.x - J.o[ax == 0 ? 1 : 0] + sp.w * z.x;
+                        const float lc = sp.y - J.o[ax == 2 ? 1 : 2] + sp.w * z.y;
+                        const int nx = J.nx, ny = J.ny, nz = J.nz;
+                        const float dx = J.dx, dy = J.dy, dz = J.dz;
+                        bool inside;
+                        if (ax == 2) {
+                            inside = lb >= 0.0f && lb < nx * dx && lc >= 0.0f && lc < ny * dy;
+                            bpx = lb; bpy = lc; bpz = sg > 0 ? 0.0f : nz * dz; buz = (float)sg;
+                            bix = (int)floorf(bpx * J.idx); biy = (int)floorf(bpy * J.idy); biz = sg > 0 ? 0 : nz - 1;
+                        } else if (ax == 1) {
+                            inside = lb >= 0.0f && lb < nx * dx && lc >= 0.0f && lc < nz * dz;
+                            bpx = lb; bpz = lc; bpy = sg > 0 ? 0.0f : ny * dy; buy = (float)sg;
+                            bix = (int)floorf(bpx * J.idx); biz = (int)floorf(bpz * J.idz); biy = sg > 0 ? 0 : ny - 1;
+                        } else {
+                            inside = lb >= 0.0f && lb < ny * dy && lc >= 0.0f && lc < nz * dz;
+                            bpy = lb; bpz = lc; bpx = sg > 0 ? 0.0f : nx * dx; bux = (float)sg;
+                            biy = (int)floorf(bpy * J.idy); biz = (int)floorf(bpz * J.idz); bix = sg > 0 ? 0 : nx - 1;
+                        }
+                        // guard the floor against rounding at the far faces
+                        bix = min(max(bix, 0), nx - 1); biy = min(max(biy, 0), ny - 1); biz = min(max(biz, 0), nz - 1);
+                        if (inside) ok = true;
+                        else led_add(bjob, 0, to_units(bE * bwh));
                     }
                 }
+                pool_next += min(32ull, avail);
+                const unsigned okm = __ballot_sync(kFull, ok);
+                if (ok) {
+                    float *e = wb + __popc(okm & lt_mask);
+                    e[0 * plane] = bpx; e[1 * plane] = bpy; e[2 * plane] = bpz;
+                    e[3 * plane] = bux; e[4 * plane] = buy; e[5 * plane] = buz;
+                    e[6 * plane] = bE; e[7 * plane] = beta; e[8 * plane] = bwh;
+                    e[9 * plane] = __int_as_float(bix); e[10 * plane] = __int_as_float(biy);
+                    e[11 * plane] = __int_as_float(biz); e[12 * plane] = __int_as_float(bjob);
+                    e[13 * plane] = __uint_as_float((unsigned)bh); e[14 * plane] = __uint_as_float((unsigned)(bh >> 32));
+                }
+                n_buf = __popc(okm);
+                __syncwarp();
+                continue;
             }
-            pool_next += min((unsigned long long)__popc(need), avail);
-            need = __ballot_sync(kFull, !alive);
+            const int take = min(__popc(dead), n_buf);
+            const int rank = __popc(dead & lt_mask);
+            if (!alive && rank < take) {
+                const float *e = wb + (n_buf - 1 - rank);
+                px = e[0 * plane]; py = e[1 * plane]; pz = e[2 * plane];
+                ux = e[3 * plane]; uy = e[4 * plane]; uz = e[5 * plane];
+                E = e[6 * plane]; eta = e[7 * plane]; wh = e[8 * plane];
+                ix = __float_as_int(e[9 * plane]); iy = __float_as_int(e[10 * plane]);
+                iz = __float_as_int(e[11 * plane]); job = __float_as_int(e[12 * plane]);
+                h = (unsigned long long)__float_as_uint(e[13 * plane]) |
+                    ((unsigned long long)__float_as_uint(e[14 * plane]) << 32);
+                uth = 0.0f; gth = 0.0f; step = 0;
+                alive = true;
+            }
+            n_buf -= take;
+            __syncwarp();
+            dead = __ballot_sync(kFull, !alive);
         }
         if (__ballot_sync(kFull, alive) == 0) break;
         if (!alive) continue;
