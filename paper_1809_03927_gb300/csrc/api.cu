@@ -940,7 +940,7 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
     }
     if (!nj.empty()) {
         CK(c0, cudaMemcpyAsync(c0->d_norm, nj.data(), nj.size() * sizeof(NormJob), cudaMemcpyHostToDevice, st));
-        dim3 grid(256, (unsigned)nj.size());
+        dim3 grid(608, (unsigned)nj.size());
         k_normalise<<<grid, 256, 0, st>>>(c0->d_norm);
         CK(c0, cudaGetLastError());
     }

@@ -36,7 +36,7 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 2) k_dim(DimArgs a)
+__global__ void __launch_bounds__(256, 3) k_dim(DimArgs a)
 {
     const long long nvox = (long long)a.nx * a.ny * a.nz;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

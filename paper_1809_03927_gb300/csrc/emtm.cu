@@ -298,10 +298,15 @@ __global__ void k_emtm_sum(EmtmArgs a)
             if (x < bb[0] || x > bb[3] || y < bb[1] || y > bb[4] || z < bb[2] || z > bb[5]) continue;
             const unsigned long long m = a.M[(size_t)S * nvox + i];
             if (m == 0) continue;
+            const unsigned long long e = a.E[(size_t)S * nvox + i];
+            if (e == 0) {                            // mass without energy: the quotient is +0
+                acc += 0.0;
+                continue;
+            }
             // E / M back to Gy: times 2^(mass shift - energy shift), an exact
             // power of two built from its exponent bits
             const int k = kMassShift - energy_shift(a.maxbits[S]);
-            const double q = div64((double)a.E[(size_t)S * nvox + i], (double)m);
+            const double q = div64((double)e, (double)m);
             acc += (k > -1000 && k < 1000) ? q * __longlong_as_double((long long)(1023 + k) << 52) : ldexp(q, k);
         }
         if (a.mask && !a.mask[i]) acc = 0.0;

@@ -357,7 +357,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
             __syncwarp();
             dead = __ballot_sync(kFull, !alive);
         }
-        if (__ballot_sync(kFull, alive) == 0) break;
+        if (dead == kFull) break;                    // the queue and the buffer are empty
         if (!alive) continue;
 
         // ---------------- one condensed-history step
@@ -584,12 +584,23 @@ __global__ void k_normalise(const NormJob *__restrict__ jobs)
         : (double)W / (double)J.n_hist * 1.602176634e-10 / (16777216.0 * J.voxel_cm3);
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned long long dep = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < J.nvox; i += stride) {
-        const unsigned long long t = J.tally[i];
-        dep += t;
-        // most voxels of a beam's grid hold no energy: their dose is +0
-        // without the FP64 quotient (or the density read)
-        J.dose[i] = t ? (float)div64((double)t * factor, (double)J.rho[i]) : 0.0f;
+    // four voxels per pass, their tallies loaded together
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < J.nvox; i0 += 4 * stride) {
+        unsigned long long t[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k * stride;
+            t[k] = i < J.nvox ? J.tally[i] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long i = i0 + k * stride;
+            if (i >= J.nvox) break;
+            dep += t[k];
+            // most voxels of a beam's grid hold no energy: their dose is +0
+            // without the FP64 quotient (or the density read)
+            J.dose[i] = t[k] ? (float)div64((double)t[k] * factor, (double)J.rho[i]) : 0.0f;
+        }
     }
     dep = warp_sum_u64(dep);
     if ((threadIdx.x & 31) == 0 && dep) atomicAdd(J.ledger + LED_DEP, dep);
