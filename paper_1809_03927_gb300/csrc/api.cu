@@ -392,6 +392,45 @@ int set_phase_zero(dose_ctx *c, int phase, void *stream)
     c->have_accum = false;
     return DOSE_OK;
 }
+
+int copy_plan(dose_ctx *dst, const dose_ctx *src, void *stream)
+{
+    if (!dst || !src) return fail(dst, DOSE_EINVAL, "contexts are required");
+    if (!src->have_plan) return fail(dst, DOSE_ESTATE, "no plan to copy");
+    if (dst->g != src->g) return fail(dst, DOSE_EINVAL, "a plan is copied between views of one grid only");
+    int rc;
+    if ((rc = use_device(dst))) return rc;
+    free_plan(dst);
+    const size_t n = (size_t)src->n_spots, P = (size_t)src->g->n_phases, F = (size_t)src->n_fields;
+    if ((rc = dalloc_t(dst, &dst->spot, n)) || (rc = dalloc_t(dst, &dst->protons, n)) ||
+        (rc = dalloc_t(dst, &dst->layer, n)) || (rc = dalloc_t(dst, &dst->field, n)) ||
+        (rc = dalloc_t(dst, &dst->pp, n * P)) || (rc = dalloc_t(dst, &dst->start_phase, F)) ||
+        (rc = dalloc_t(dst, &dst->field_end, F)) || (src->spot_dir && (rc = dalloc_t(dst, &dst->spot_dir, n)))) {
+        free_plan(dst);
+        return rc;
+    }
+    if (!dst->tl_used && ((rc = dalloc_t(dst, &dst->tl_used, 1)) || (rc = dalloc_t(dst, &dst->tl_status, 1)))) return rc;
+    cudaStream_t st = S(stream);
+    const auto d2d = [&](void *to, const void *from, size_t bytes) {
+        return cudaMemcpyAsync(to, from, bytes, cudaMemcpyDeviceToDevice, st);
+    };
+    CK(dst, d2d(dst->spot, src->spot, n * sizeof(float4)));
+    CK(dst, d2d(dst->protons, src->protons, n * sizeof(unsigned long long)));
+    CK(dst, d2d(dst->layer, src->layer, n * sizeof(int)));
+    CK(dst, d2d(dst->field, src->field, n * sizeof(int)));
+    CK(dst, d2d(dst->pp, src->pp, n * P * sizeof(unsigned long long)));
+    CK(dst, d2d(dst->start_phase, src->start_phase, F * sizeof(int)));
+    CK(dst, d2d(dst->field_end, src->field_end, F * sizeof(long long)));
+    if (src->spot_dir) CK(dst, d2d(dst->spot_dir, src->spot_dir, n));
+    if (src->have_delivery) CK(dst, d2d(dst->tl_used, src->tl_used, sizeof(dose_delivery)));
+    CK(dst, cudaMemsetAsync(dst->tl_status, 0, sizeof(int), st));
+    std::memcpy(dst->field_dir, src->field_dir, sizeof dst->field_dir);
+    dst->n_spots = src->n_spots;
+    dst->n_fields = src->n_fields;
+    dst->have_plan = true;
+    dst->have_delivery = src->have_delivery;
+    return DOSE_OK;
+}
 }  // namespace dose
 
 // ======================================================================== ABI
@@ -688,7 +727,11 @@ int launch_timelines(dose_ctx *c, const std::vector<TimelineArgs> &args, cudaStr
         c->cap_tl = (int)args.size();
     }
     CK(c, cudaMemcpyAsync(c->tl_args, args.data(), args.size() * sizeof(TimelineArgs), cudaMemcpyHostToDevice, st));
-    k_timeline<<<(unsigned)args.size(), kMaxFields, 0, st>>>(c->tl_args);
+    // the plan's protons, layers and fields are staged in shared memory
+    const size_t smem = (size_t)args[0].n_spots * (sizeof(unsigned long long) + sizeof(int) + 1);
+    if (smem > 48 * 1024)
+        CK(c, cudaFuncSetAttribute(k_timeline, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_timeline<<<(unsigned)args.size(), kMaxFields, smem, st>>>(c->tl_args);
     CK(c, cudaGetLastError());
     return DOSE_OK;
 }

@@ -16,6 +16,10 @@ namespace dose {
 void grid_info(const dose_ctx *c, int dims[4]);
 // Give a phase zero dose (a phase its plan does not reach).
 int set_phase_zero(dose_ctx *c, int phase, void *stream);
+// Give dst (a view of src's grid) src's plan and delivery result: the plan
+// arrays, the subplan, start phases, field ends and field beams are copied
+// on the stream, so the timeline does not run again.
+int copy_plan(dose_ctx *dst, const dose_ctx *src, void *stream);
 
 __global__ void k_density(const int16_t *hu, float *rho, long long n, const Tables *tab);
 __global__ void k_material(const int16_t *hu, float2 *m, long long n, const Tables *tab);
@@ -73,6 +77,8 @@ struct TimelineArgs {                // one trial (or the single delivery) of a 
     dose_delivery *used;             // the delivery the clock ran (sampled for trials)
     int *status;                     // 0; 1 sampled delivery invalid; 2 no progress; 3 clock overflow
 };
+// One block per trial, a thread per field; dynamic shared memory
+// 13 B per spot (the plan's protons, layers and fields).
 __global__ void k_timeline(const TimelineArgs *args);
 
 // What an accumulation can reach, per source phase: a record of

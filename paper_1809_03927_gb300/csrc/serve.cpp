@@ -3,7 +3,8 @@
 // Requests (robust scenarios of one plan over one resident 4DCT: seed,
 // history count, stopping-power scale, setup shift) wait in a FIFO queue.
 // Each step admits queued requests into free slots -- a slot is a view of
-// the resident grid with the plan loaded once, created while the memory
+// the resident grid with the plan loaded once (copied from a template view
+// whose delivery timeline ran at server creation), created while the memory
 // budget allows and reused afterwards -- then gives every active request a
 // share of the step's history budget over its phases and runs all those
 // slices in ONE persistent launch (dose_run_batch).  A request whose last
@@ -46,6 +47,7 @@ struct dose_server {
         uint64_t next;                 // next history index (same for every phase)
     };
     dose_ctx *base = nullptr;
+    dose_ctx *tmpl = nullptr;          // a view with the plan and the server's delivery loaded
     dose_server_config cfg{};
     std::vector<dose_spot> spots;
     dose_delivery delivery{};
@@ -101,29 +103,33 @@ int dose_server_create(dose_ctx *base, const dose_server_config *cfg, const dose
     s->cfg = *cfg;
     s->spots.assign(spots, spots + n_spots);
     if (delivery) { s->delivery = *delivery; s->has_delivery = true; }
-    // the base carries the grid; find the phases the plan reaches with a
-    // scratch view (its subplan is also the template every slot reproduces)
-    dose_ctx *probe = nullptr;
-    int rc = dose_create_view(base, &probe);
+    // the base carries the grid; a template view holds the plan with the
+    // server's delivery (the timeline runs once: slots copy its result) and
+    // gives the phases the plan reaches
+    int rc = dose_create_view(base, &s->tmpl);
     if (rc) { delete s; return rc; }
-    rc = dose_add_spots(probe, spots, n_spots, delivery, nullptr);
+    rc = dose_add_spots(s->tmpl, spots, n_spots, delivery, nullptr);
     int dims[4] = {0, 0, 0, 0};
-    if (!rc) dose::grid_info(probe, dims);
+    if (!rc) dose::grid_info(s->tmpl, dims);
     std::vector<uint64_t> pp;
     if (!rc) {
         pp.resize((size_t)dims[3] * n_spots);
-        rc = dose_read(probe, DOSE_SUBPLAN, 0, pp.data(), pp.size() * 8, 0, nullptr);
+        rc = dose_read(s->tmpl, DOSE_SUBPLAN, 0, pp.data(), pp.size() * 8, 0, nullptr);
     }
-    dose_destroy(probe);
-    if (rc) { delete s; return rc; }
+    if (rc) { dose_destroy(s->tmpl); delete s; return rc; }
     for (int p = 0; p < dims[3]; ++p) {
         uint64_t w = 0;
         for (int64_t k = 0; k < n_spots; ++k) w += pp[(size_t)p * n_spots + k];
         if (w) s->phases.push_back(p);
     }
-    if (s->phases.empty()) { delete s; return sfail(nullptr, DOSE_EINVAL, "the plan delivers no protons"); }
+    if (s->phases.empty()) {
+        dose_destroy(s->tmpl);
+        delete s;
+        return sfail(nullptr, DOSE_EINVAL, "the plan delivers no protons");
+    }
     s->slot_bytes = slot_footprint(dims[0], dims[1], dims[2], dims[3], n_spots, cfg->accumulate != 0);
     if (cfg->memory_budget_bytes < s->slot_bytes) {
+        dose_destroy(s->tmpl);
         delete s;
         return sfail(nullptr, DOSE_EINVAL, "memory budget is smaller than one request slot");
     }
@@ -162,8 +168,7 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
         if (slot < 0 && s->slots.size() < cap) {
             dose_server::Slot sl;
             int rc = dose_create_view(s->base, &sl.view);
-            if (!rc) rc = dose_add_spots(sl.view, s->spots.data(), (int64_t)s->spots.size(),
-                                         s->has_delivery ? &s->delivery : nullptr, stream);
+            if (!rc) rc = dose::copy_plan(sl.view, s->tmpl, stream);
             if (rc) {
                 if (sl.view) dose_destroy(sl.view);
                 if (rc == DOSE_ENOMEM) break;            // no room now; retry next step
@@ -185,8 +190,8 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
         const bool same = want_own ? (sl.loaded_own && std::memcmp(&sl.loaded_dlv, &q.dlv, sizeof q.dlv) == 0)
                                    : !sl.loaded_own;
         if (!same) {
-            const dose_delivery *d = want_own ? &q.dlv : (s->has_delivery ? &s->delivery : nullptr);
-            int rc = dose_add_spots(sl.view, s->spots.data(), (int64_t)s->spots.size(), d, stream);
+            int rc = want_own ? dose_add_spots(sl.view, s->spots.data(), (int64_t)s->spots.size(), &q.dlv, stream)
+                              : dose::copy_plan(sl.view, s->tmpl, stream);
             if (rc) return rc;
             sl.loaded_own = want_own;
             if (want_own) sl.loaded_dlv = q.dlv;
@@ -319,6 +324,7 @@ void dose_server_destroy(dose_server *s)
 {
     if (!s) return;
     for (auto &sl : s->slots) dose_destroy(sl.view);
+    dose_destroy(s->tmpl);
     delete s;
 }
 

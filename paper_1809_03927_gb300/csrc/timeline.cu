@@ -79,6 +79,8 @@ struct Clock {
     unsigned f;
     long long N, cyc_start, tph;
     unsigned long long cycle;
+    long long s0 = 0, s1 = -1;                     // the last slot looked up: [s0, s1), phase ph
+    unsigned ph = 0;
 
     __device__ long long cycle_tph(unsigned long long c) const
     {
@@ -97,8 +99,20 @@ struct Clock {
             tph = cycle_tph(cycle);
         }
     }
-    __device__ unsigned phase(long long t) { sync(t); return (unsigned)((t - cyc_start) / tph); }
-    __device__ long long slot_end(long long t) { sync(t); return cyc_start + ((t - cyc_start) / tph + 1) * tph; }
+    // The clock moves forward, so most look-ups fall in the slot of the last
+    // one and need no division.
+    __device__ unsigned phase(long long t)
+    {
+        sync(t);
+        if (t < s0 || t >= s1) {
+            const long long k = (t - cyc_start) / tph;
+            ph = (unsigned)k;
+            s0 = cyc_start + k * tph;
+            s1 = s0 + tph;
+        }
+        return ph;
+    }
+    __device__ long long slot_end(long long t) { phase(t); return s1; }
     __device__ bool on(unsigned ph) const
     {
         return !D->gated || ((int)ph >= D->gate_first && (int)ph <= D->gate_last);
@@ -121,7 +135,7 @@ __device__ void deposit(Clock &C, long long t, long long end, unsigned long long
                         unsigned long long *pp, int S, int q)
 {
     if (w == 0) return;
-    if (end <= t) { pp[(size_t)C.phase(t) * S + q] += w; return; }
+    if (end <= t) { atomicAdd(pp + (size_t)C.phase(t) * S + q, w); return; }
     const unsigned long long dur = (unsigned long long)(end - t);
     unsigned long long given = 0;
     while (t < end) {
@@ -130,7 +144,7 @@ __device__ void deposit(Clock &C, long long t, long long end, unsigned long long
         const unsigned ph = C.phase(t);
         const unsigned long long pj = (e == end) ? w - given : mul_div_floor(w, (unsigned long long)(e - t), dur);
         given += pj;
-        pp[(size_t)ph * S + q] += pj;
+        atomicAdd(pp + (size_t)ph * S + q, pj);
         t = e;
     }
 }
@@ -180,6 +194,18 @@ __device__ dose_delivery sample_trial(const dose_delivery &m, const dose_deliver
 __global__ void k_timeline(const TimelineArgs *__restrict__ args)
 {
     const TimelineArgs &a = args[blockIdx.x];
+    // the plan's protons, layers and fields in shared memory (the walk below
+    // reads them spot by spot)
+    extern __shared__ unsigned long long s_prot[];
+    const int S = a.n_spots;
+    int *s_layer = reinterpret_cast<int *>(s_prot + S);
+    unsigned char *s_field = reinterpret_cast<unsigned char *>(s_layer + S);
+    for (int q = threadIdx.x; q < S; q += blockDim.x) {
+        s_prot[q] = a.protons[q];
+        s_layer[q] = a.layer[q];
+        s_field[q] = (unsigned char)a.field[q];
+    }
+    __syncthreads();
     const int f = threadIdx.x;
     if (f >= a.n_fields) return;
     const dose_delivery D = a.spread ? sample_trial(a.d, *a.spread, a.trial) : a.d;
@@ -188,7 +214,6 @@ __global__ void k_timeline(const TimelineArgs *__restrict__ args)
         if (f == 0) *a.status = 1;
         return;
     }
-    const int S = a.n_spots;
     unsigned p0;
     if (D.start_phase >= 0) {
         p0 = (unsigned)D.start_phase;
@@ -208,12 +233,12 @@ __global__ void k_timeline(const TimelineArgs *__restrict__ args)
     int err = 0;
     int s = 0;
     while (s < S && !err) {
-        if (a.field[s] != f) { ++s; continue; }
+        if (s_field[s] != f) { ++s; continue; }
         const int l0 = s;
         int l1 = s;
         for (int q = s + 1; q < S; ++q) {
-            if (a.field[q] != f) continue;
-            if (a.layer[q] != a.layer[l0]) break;
+            if (s_field[q] != f) continue;
+            if (s_layer[q] != s_layer[l0]) break;
             l1 = q;
         }
         s = l1 + 1;
@@ -223,8 +248,8 @@ __global__ void k_timeline(const TimelineArgs *__restrict__ args)
             if (cap == 0 && r == R) break;
             bool any = false;
             for (int q = l0; q <= l1 && !err; ++q) {
-                if (a.field[q] != f) continue;
-                const unsigned long long p = a.protons[q];
+                if (s_field[q] != f) continue;
+                const unsigned long long p = s_prot[q];
                 unsigned long long w;
                 if (cap > 0) {
                     const unsigned long long done = r * cap;      // delivered by the earlier paintings
@@ -297,7 +322,7 @@ __global__ void k_timeline(const TimelineArgs *__restrict__ args)
                 const long long dur = spill_ns(w, D.rate_protons_per_s);
                 if (D.gated && !C.on(C.phase(t))) t = C.hold(t) + D.discard_ns;
                 if (dur == 0) {
-                    a.pp[(size_t)C.phase(t) * S + q] += w;
+                    atomicAdd(a.pp + (size_t)C.phase(t) * S + q, w);
                     continue;
                 }
                 long long rem = dur;
@@ -312,7 +337,7 @@ __global__ void k_timeline(const TimelineArgs *__restrict__ args)
                     const unsigned long long pj = rem > 0 ? mul_div_floor(w, (unsigned long long)d, (unsigned long long)dur)
                                                           : w - given;
                     given += pj;
-                    a.pp[(size_t)ph * S + q] += pj;
+                    atomicAdd(a.pp + (size_t)ph * S + q, pj);
                 }
             }
             if (cap > 0 && !any) break;
