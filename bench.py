@@ -40,11 +40,12 @@ WORKLOAD = "slab phantom 128^3 at 2 mm (water/lung/bone), 400 spots on 10 layers
 # quantisation 5, bookkeeping 10
 OPS_PER_STEP = 230
 # DRAM bytes (read + write) of one transport launch on the slab workload
-# (1e7 histories) in the shape it was measured in (registers variant,
+# (1e7 histories) per launch shape it was measured in (registers variant,
 # block, chunk, material grid): ncu --metrics dram__bytes_read.sum,
-# dram__bytes_write.sum on the full-size launch, 2.70 MB read, 0 written
-# (the grid is read once, the tally stays in L2)
-TRANSPORT_DRAM = {"bytes": 2.70e6, "shape": (1, 1024, 32, 0)}
+# dram__bytes_write.sum on the full-size launch (bench.py --launch R,B,C,M).
+# The grid is read once where the beam goes (HU + table, or the per-voxel
+# material grid) and the tally stays in L2.
+TRANSPORT_DRAM = {(1, 1024, 32, 0): 2.70e6, (1, 1024, 64, 0): 3.06e6, (1, 1024, 64, 1): 3.59e6}
 
 
 def _args():
@@ -69,6 +70,8 @@ def _args():
                    help="4D leg on a 128x128x80 grid at 2x2x5 mm (profiler captures), not the 4DCT workload")
     p.add_argument("--reference-seconds", type=float, default=10.0,
                    help="CPU seconds of each timed oracle step of the reference arm")
+    p.add_argument("--launch", default=None,
+                   help="transport launch shape 'registers,block,chunk,material' instead of the autotuner's")
     p.add_argument("--histories", type=int, default=N_HIST,
                    help="histories per step (smaller cases for profiling; the metric's workload is 1e7)")
     return p.parse_args()
@@ -238,7 +241,7 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed, small=False):
     try:
         D.dose_add_spots(ctx, spots, dlv, stream)
         phase_p = D.dose_read(ctx, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
-        tune = D.dose_autotune(ctx, int(np.argmax(phase_p)), n_per_phase, min(n_per_phase, 2_000_000), seed, stream)
+        tune = D.dose_autotune(ctx, int(np.argmax(phase_p)), n_per_phase, min(n_per_phase, 10_000_000), seed, stream)
 
         def plan_once():
             D.dose_add_spots(ctx, spots, dlv, stream)
@@ -583,8 +586,16 @@ def run_engine(args):
     D.dose_add_spots(ctx, spots, None, stream)
     seed = SEED + 1000 * rank
     n_hist = args.histories
-    # launch shape from the engine's autotuner (results do not depend on it)
-    tune = D.dose_autotune(ctx, 0, n_hist, min(n_hist, 2_000_000), seed, stream)
+    # launch shape from the engine's autotuner, timed on the whole run (before
+    # the timed region; results do not depend on the shape), or as given
+    if args.launch:
+        regs, block, chunk, mat = (int(v) for v in args.launch.split(","))
+        for opt, v in ((D.DOSE_OPT_REGISTERS, regs), (D.DOSE_OPT_BLOCK, block), (D.DOSE_OPT_CHUNK, chunk),
+                       (D.DOSE_OPT_MATERIAL_GRID, mat)):
+            D.dose_set_option(ctx, opt, v)
+        tune = (regs, block, chunk, 0)
+    else:
+        tune = D.dose_autotune(ctx, 0, n_hist, n_hist, seed, stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -677,7 +688,7 @@ def run_engine(args):
     shape = (int(tune[0]), int(tune[1]), int(tune[2]), material)
     # DRAM traffic of the transport launch, from an ncu capture of this
     # workload in this launch shape (null for any other shape or size)
-    traffic = TRANSPORT_DRAM["bytes"] if (shape == TRANSPORT_DRAM["shape"] and n_hist == N_HIST) else None
+    traffic = TRANSPORT_DRAM.get(shape) if n_hist == N_HIST else None
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12          # Top/s: 128 FP32/INT32 lanes per SM

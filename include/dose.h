@@ -394,7 +394,8 @@ int dose_read(dose_ctx *c, int what, int phase, void *dst, size_t bytes, int dst
  * budget (DOSE_OPT_REGISTERS 0 or 1) x threads per block in {128, 256, 512,
  * 1024} (the shapes that fit) x histories a warp takes per queue pull in
  * {32, 64, 128, 256} -- then, for the fastest, the material source
- * (DOSE_OPT_MATERIAL_GRID 0 or 1), and keep the winners on the context.
+ * (DOSE_OPT_MATERIAL_GRID 0 or 1, each timed twice, the faster minimum
+ * kept), and keep the winners on the context.
  * Launch shapes change speed only: the tallies are bit-identical.  The
  * phase's tally and dose are overwritten.  best (host, may be NULL)
  * receives {registers option, block, chunk, elapsed microseconds of the best
