@@ -242,6 +242,7 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed, small=False):
         D.dose_add_spots(ctx, spots, dlv, stream)
         phase_p = D.dose_read(ctx, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
         tune = D.dose_autotune(ctx, int(np.argmax(phase_p)), n_per_phase, min(n_per_phase, 10_000_000), seed, stream)
+        material = D.dose_get_option(ctx, D.DOSE_OPT_MATERIAL_GRID)
 
         def plan_once():
             D.dose_add_spots(ctx, spots, dlv, stream)
@@ -317,7 +318,8 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed, small=False):
             "workload": ("synthetic 4DCT 10 x 128x128x80 at 2x2x5 mm (small, for profiling)" if small else
                          "synthetic 4DCT 10 x 256x256x160 at 1x1x2.5 mm") + ", 3000 spots / 20 layers 70-180 MeV, "
                         f"{n_per_phase:.0e} histories per phase, EMTM 2x2x5 onto phase 0",
-            "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}}
+            "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2],
+                       "material_grid": material}}
 
 
 # ------------------------------------------------------------------ uncertainty trials
