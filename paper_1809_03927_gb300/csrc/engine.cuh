@@ -30,10 +30,13 @@ constexpr int kNR = 2048;
 constexpr float kRmax = 420.0f;        // mm, above the range of 256 MeV
 constexpr int kHuMin = -1000, kHuMax = 3000, kNHU = kHuMax - kHuMin + 1;
 
+// Each entry of re, hs and er also holds its FP32 difference to the next
+// entry (d = next - this, rounded as the FP32 subtraction rounds it), so a
+// lookup is one load and fma(f, d, value).
 struct Tables {
-    float2 re[kNE + 2];   // (CSDA range in water, mm; Bohr variance per mm of water path, MeV^2/mm)
-    float2 hs[kNE + 2];   // (p v in MeV, for the Highland coefficient; nuclear Sigma per mm of water)
-    float er[kNR + 4];    // energy at range (i kDS)^2
+    float4 re[kNE + 2];   // (CSDA range in water, mm; Bohr variance per mm of water path, MeV^2/mm; d, d)
+    float4 hs[kNE + 2];   // (p v in MeV, for the Highland coefficient; nuclear Sigma per mm of water; d, d)
+    float2 er[kNR + 4];   // (energy at range (i kDS)^2; d)
     float2 mat[kNHU + 3]; // (rho, SPR)
 };
 static_assert(sizeof(Tables) % 16 == 0, "tables are copied to shared memory as int4");
@@ -229,22 +232,23 @@ __device__ __forceinline__ float highland_coeff(float pv)
 }
 
 // Linear interpolation on the uniform energy grid.
-__device__ __forceinline__ float2 lerp_e(const float2 *t, float e)
+__device__ __forceinline__ float2 lerp_e(const float4 *t, float e)
 {
     const float x = e * kInvDE;                      // e >= 0 on every call
     const int i = (int)min((unsigned)(int)x, (unsigned)(kNE - 1));
     const float f = x - (float)i;
-    const float2 a = t[i], b = t[i + 1];
-    return make_float2(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y));
+    const float4 a = t[i];
+    return make_float2(fmaf(f, a.z, a.x), fmaf(f, a.w, a.y));
 }
 
 // Energy at a residual water range, linear on the sqrt(range) grid.
-__device__ __forceinline__ float energy_at_range(const float *er, float r, float inv_ds)
+__device__ __forceinline__ float energy_at_range(const float2 *er, float r, float inv_ds)
 {
     const float x = fast_sqrt(r) * inv_ds;
     const int i = (int)min((unsigned)(int)x, (unsigned)(kNR - 1));
     const float f = x - (float)i;
-    return fmaf(f, er[i + 1] - er[i], er[i]);
+    const float2 a = er[i];
+    return fmaf(f, a.y, a.x);
 }
 
 // The voxels an accumulation of one source phase has to visit: the box of

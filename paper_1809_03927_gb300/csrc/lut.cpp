@@ -103,13 +103,24 @@ void build_tables(Tables *t, float *inv_ds)
         const double bohr = K * ME * ZA * 0.5 * (gamma * gamma + 1.0) / 10.0;
         const double pv = ee * (ee + 2.0 * MP) / (ee + MP);
         const double sig = ee > 7.0 ? 0.0123 * (1.0 - std::exp(-(ee - 7.0) / 20.0)) / 10.0 : 0.0;
-        t->re[i] = make_float2((float)R(e), (float)bohr);
-        t->hs[i] = make_float2((float)pv, (float)sig);
+        t->re[i] = make_float4((float)R(e), (float)bohr, 0.0f, 0.0f);
+        t->hs[i] = make_float4((float)pv, (float)sig, 0.0f, 0.0f);
     }
     const double ds = std::sqrt((double)kRmax) / kNR;
     for (int i = 0; i < kNR + 4; ++i) {
         const double r = (i * ds) * (i * ds);
-        t->er[i] = (float)R.inverse(r);
+        t->er[i] = make_float2((float)R.inverse(r), 0.0f);
+    }
+    // FP32 differences to the next entry (volatile: rounded as stored floats)
+    for (int i = 0; i + 1 < kNE + 2; ++i) {
+        volatile float rz = t->re[i + 1].x - t->re[i].x, rw = t->re[i + 1].y - t->re[i].y;
+        volatile float hz = t->hs[i + 1].x - t->hs[i].x, hw = t->hs[i + 1].y - t->hs[i].y;
+        t->re[i].z = rz; t->re[i].w = rw;
+        t->hs[i].z = hz; t->hs[i].w = hw;
+    }
+    for (int i = 0; i + 1 < kNR + 4; ++i) {
+        volatile float d = t->er[i + 1].x - t->er[i].x;
+        t->er[i].y = d;
     }
     for (int i = 0; i < kNHU + 3; ++i) {
         const double hu = std::fmin((double)(kHuMin + i), (double)kHuMax);
