@@ -962,13 +962,15 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         int sms = 0;
         CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->g->device));
         // stage the job table in shared memory unless that costs resident blocks
+        // or leaves too little L1 (kStageSmemCap)
         const size_t smem_plain = transport_smem(kMaxStagedJobs + 1) + birth_smem(c0->block);
         int fit_plain = 0, fit_staged = 0;
         CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_plain, kern, c0->block, smem_plain));
         if ((int)tj.size() <= kMaxStagedJobs)
             CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_staged, kern, c0->block,
                                                                  transport_smem((int)tj.size()) + birth_smem(c0->block)));
-        const int stage = fit_staged > 0 && fit_staged >= fit_plain ? 1 : 0;
+        const int stage = fit_staged > 0 && fit_staged >= fit_plain &&
+                          transport_smem((int)tj.size()) + birth_smem(c0->block) <= kStageSmemCap ? 1 : 0;
         const size_t smem = stage ? transport_smem((int)tj.size()) + birth_smem(c0->block) : smem_plain;
         int per_sm = c0->blocks_per_sm;
         if (per_sm <= 0) per_sm = stage ? fit_staged : fit_plain;

@@ -94,6 +94,11 @@ __host__ __device__ constexpr size_t transport_smem(int n_jobs)
     return kSmemTables + (n_jobs <= kMaxStagedJobs ? (size_t)n_jobs * (sizeof(TJob) + 4 * sizeof(unsigned long long)) : 0);
 }
 constexpr size_t kSmemTransportMax = transport_smem(kMaxStagedJobs);
+// Staging stops where it would leave the block's SM less than ~75 KB of L1
+// for the grid and HU-table reads: a 243-job trial batch staged at 1024
+// threads (213 KB of shared memory) ran at 2.0e8 histories/s instead of
+// 2.7e8 unstaged, while a 74-job batch (169 KB) gains 3.5 % from staging.
+constexpr size_t kStageSmemCap = 180 * 1024;
 // Per warp, a buffer of 32 born histories between the tables and the staged
 // jobs: kBirthWords planes (position, direction, energy, nuclear path, weight,
 // voxel, job, history index) of 32 slots per warp.
