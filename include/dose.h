@@ -162,17 +162,20 @@ enum { DOSE_PHYS_STRAGGLING = 1, DOSE_PHYS_MCS = 2, DOSE_PHYS_NUCLEAR = 4, DOSE_
 enum {
     DOSE_OPT_PHYSICS = 0,         /* bit mask of DOSE_PHYS_*                     */
     DOSE_OPT_MAX_STEPS = 1,       /* step cap per history (default 20000)        */
-    DOSE_OPT_BLOCK = 2,           /* transport threads per block (64..1024)      */
+    DOSE_OPT_BLOCK = 2,           /* transport threads per block (64..1024, a
+                                     multiple of 32; default 1024)              */
     DOSE_OPT_BLOCKS_PER_SM = 3,   /* transport blocks per SM (0 = occupancy max) */
-    DOSE_OPT_CHUNK = 4,           /* histories a warp takes per queue pull       */
+    DOSE_OPT_CHUNK = 4,           /* histories a warp takes per queue pull (default 32) */
     DOSE_OPT_TIMEOUT_MS = 5,      /* host wait bound for dose_read (default 600000) */
     DOSE_OPT_FAIL_ALLOC_AFTER = 6,/* test hook: the n-th later device allocation
                                      of this context fails (-1 = off)            */
     DOSE_OPT_REGISTERS = 7,       /* transport register budget: 0 = up to 128 per
-                                     thread (blocks <= 512), 1 = 64 (blocks <= 1024) */
+                                     thread (blocks <= 512), 1 = 64 (blocks <= 1024;
+                                     default)                                     */
     DOSE_OPT_MATERIAL_GRID = 8    /* 1: the transport reads a per-voxel (density, SPR)
                                      grid (8 B per voxel per phase, built once per grid
-                                     on first use) instead of HU + table; same results */
+                                     on first use) instead of HU + table (0, default);
+                                     same results                                */
 };
 
 /* Create a context holding a voxel grid of `n_phases` HU volumes (Sec. 2.A:

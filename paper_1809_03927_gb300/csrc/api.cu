@@ -115,10 +115,10 @@ struct dose_ctx {
     unsigned long long *d_counter = nullptr;
     unsigned physics = DOSE_PHYS_ALL;
     unsigned max_steps = 20000;
-    int block = 256;
-    int blocks_per_sm = 0;
-    unsigned chunk = 64;
-    int regs = 0;
+    int block = 1024;                        // launch-shape defaults: the shape the autotuner
+    int blocks_per_sm = 0;                   // picks for most workloads (64 registers, 32 warps
+    unsigned chunk = 32;                     // per SM)
+    int regs = 1;
     int material_grid = 0;                   // DOSE_OPT_MATERIAL_GRID
     long long timeout_ms = 600000;
     long long fail_alloc_after = -1;

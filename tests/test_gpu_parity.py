@@ -307,7 +307,8 @@ def test_bit_reproducible_across_runs_and_launch_shapes(gpu):
     np.testing.assert_array_equal(ref, again)
     for opts in ({gpu.DOSE_OPT_BLOCK: 128}, {gpu.DOSE_OPT_BLOCK: 512, gpu.DOSE_OPT_CHUNK: 7},
                  {gpu.DOSE_OPT_BLOCKS_PER_SM: 1, gpu.DOSE_OPT_CHUNK: 1000},
-                 {gpu.DOSE_OPT_REGISTERS: 1, gpu.DOSE_OPT_BLOCK: 1024},
+                 {gpu.DOSE_OPT_REGISTERS: 0, gpu.DOSE_OPT_BLOCK: 256, gpu.DOSE_OPT_CHUNK: 64},
+                 {gpu.DOSE_OPT_REGISTERS: 0, gpu.DOSE_OPT_BLOCK: 512, gpu.DOSE_OPT_MATERIAL_GRID: 1},
                  {gpu.DOSE_OPT_REGISTERS: 1, gpu.DOSE_OPT_BLOCK: 256, gpu.DOSE_OPT_CHUNK: 32}):
         np.testing.assert_array_equal(H.gpu_run(gpu, ph, pl, 300_000, 4, options=opts)["tally"], ref)
 
