@@ -45,7 +45,7 @@ OPS_PER_STEP = 230
 # dram__bytes_write.sum on the full-size launch (bench.py --launch R,B,C,M).
 # The grid is read once where the beam goes (HU + table, or the per-voxel
 # material grid) and the tally stays in L2.
-TRANSPORT_DRAM = {(1, 1024, 32, 0): 2.79e6, (1, 1024, 64, 0): 2.90e6, (1, 1024, 64, 1): 3.54e6}
+TRANSPORT_DRAM = {(1, 1024, 32, 0): 3.07e6, (1, 1024, 64, 0): 3.02e6, (1, 1024, 64, 1): 3.64e6}
 
 
 def _args():

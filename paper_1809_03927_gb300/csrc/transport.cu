@@ -373,10 +373,12 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         const int nx = J.nx, ny = J.ny;
         const int vox = (iz * ny + iy) * nx + ix;
         float2 m;
+        // the grid is read at random voxels (few L1 hits): through L2 only,
+        // so L1 keeps the job descriptors and the HU table
         if (J.matg) {
-            m = __ldg(J.matg + vox);
+            m = __ldcg(J.matg + vox);
         } else {
-            const int hv = min(max((int)__ldg(J.hu + vox), kHuMin), kHuMax);
+            const int hv = min(max((int)__ldcg(J.hu + vox), kHuMin), kHuMax);
             m = __ldg(mat + (hv - kHuMin));
         }
         const float rho = m.x;
