@@ -277,7 +277,11 @@ int dose_run_4d(dose_ctx *c, uint64_t n_histories_per_phase, uint64_t seed, floa
  * slice ran (normalisation, and the accumulation onto ref_phase when
  * `accumulate`; dvf is a device array as in dose_accumulate_subvoxel) and
  * waits for the stream.  A request's result is bit-identical to the same
- * request served alone: histories are keyed by (seed, history, phase).     */
+ * request served alone: histories are keyed by (seed, history, phase).
+ * dose_server_create runs the delivery timeline of the plan once, on a
+ * template view of `base`; slots copy that plan and subplan, so the base's
+ * options and field beams are taken at creation (later changes to the base
+ * do not reach the server).                                                */
 typedef struct dose_server dose_server;
 typedef struct dose_server_config {
     uint64_t memory_budget_bytes;
