@@ -279,9 +279,9 @@ int dose_run_4d(dose_ctx *c, uint64_t n_histories_per_phase, uint64_t seed, floa
  * waits for the stream.  A request's result is bit-identical to the same
  * request served alone: histories are keyed by (seed, history, phase).
  * dose_server_create runs the delivery timeline of the plan once, on a
- * template view of `base`; slots copy that plan and subplan, so the base's
- * options and field beams are taken at creation (later changes to the base
- * do not reach the server).                                                */
+ * template view of `base`; slots copy that plan, its subplan and its field
+ * beams, so field beams set on the base later do not reach the server
+ * (launch options are read from the base when a slot is created).         */
 typedef struct dose_server dose_server;
 typedef struct dose_server_config {
     uint64_t memory_budget_bytes;
