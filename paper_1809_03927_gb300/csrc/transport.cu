@@ -201,7 +201,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
     const size_t birth_bytes = birth_smem(blockDim.x);
     float *bbuf = reinterpret_cast<float *>(reinterpret_cast<char *>(smem) + kSmemTables);
     TJob *s_jobs = reinterpret_cast<TJob *>(reinterpret_cast<char *>(smem) + kSmemTables + birth_bytes);
-    const bool staged = stage != 0;                   // the launch gave transport_smem(n_jobs)
+    const bool staged = stage != 0;   // the launch gave transport_smem(n_jobs) + birth_smem(block)
     unsigned long long *s_led = reinterpret_cast<unsigned long long *>(
         reinterpret_cast<char *>(smem) + kSmemTables + birth_bytes + (staged ? n_jobs : 0) * sizeof(TJob));
     {
@@ -223,7 +223,9 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
     const TJob *jt = staged ? s_jobs : jobs;
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    // word f of buffer slot k of this warp
+    // this warp's birth buffer: word f of slot k is wb[f * plane + k] (one
+    // plane of 32 slots per word and warp, so lanes writing consecutive
+    // slots hit distinct banks)
     float *wb = bbuf + warp * 32;
     const int plane = nwarps * 32;
 
