@@ -81,6 +81,54 @@ def test_served_results_equal_alone(gpu):
         D.dose_destroy(base)
 
 
+def test_served_two_field_plan_equals_alone(gpu):
+    """A second field entering along +x (dose_set_field_beam on the base
+    before the server is created): slots copy the template's plan with its
+    field beams, and each request equals the same request computed alone on
+    a view of the base."""
+    D = gpu
+    ph, dvf, spots0, dlv, base = _setup(D)
+    shape = ph.hu.shape[1:]
+    geo = W.phantom_4dct(48, 48, 32, (1.0, 1.0, 2.5), n_phases=4, motion_pp=8.0, with_dvf=False)[2]
+    plan = W.tumour_plan(geo, ph.origin, n_layers=3, per_layer=12, e_lo=70.0, e_hi=100.0)
+    two = W.Plan(np.concatenate([plan.x, plan.x]), np.concatenate([plan.y, plan.y]),
+                 np.concatenate([plan.energy, plan.energy]), np.concatenate([plan.sigma, plan.sigma]),
+                 np.concatenate([plan.protons, plan.protons]), np.concatenate([plan.layer, plan.layer]),
+                 np.concatenate([np.zeros(len(plan), np.int32), np.ones(len(plan), np.int32)]))
+    spots = D.spots_array(two)
+    reqs = [(30_000, 7, 1.0, (0.0, 0.0, 0.0)), (20_000, 8, 1.035, (2.0, 0.0, 0.0))]
+    try:
+        D.dose_set_field_beam(base, 1, (1.0, 0.0, 0.0))
+        srv = D.dose_server_create(base, 1 << 34, 20_000, spots, dlv, min_slice=50, nsub=NSUB, dvf=dvf)
+        out, ids = {}, {}
+        try:
+            for k, (n, seed, spr, sh) in enumerate(reqs):
+                ids[D.dose_server_submit(srv, n, seed, spr, sh)] = k
+            steps = 0
+            while len(out) < len(reqs):
+                for rid in D.dose_server_step(srv):
+                    out[ids[rid]] = D.dose_server_result(srv, rid, D.DOSE_ACCUM, 0, np.zeros(shape, np.float32))
+                    D.dose_server_release(srv, rid)
+                steps += 1
+                assert steps < 10_000
+        finally:
+            D.dose_server_destroy(srv)
+        view = D.dose_create_view(base)
+        try:
+            D.dose_add_spots(view, spots, dlv)
+            pp = D.dose_read(view, D.DOSE_SUBPLAN, 0, np.zeros((4, len(two)), np.uint64)).sum(axis=1)
+            reached = int(np.count_nonzero(pp))
+            for k, (n, seed, spr, sh) in enumerate(reqs):
+                D.dose_run_4d(view, n // reached, seed, 0, NSUB, dvf=dvf, spr_scale=spr, shift_mm=sh)
+                alone = D.dose_read(view, D.DOSE_ACCUM, 0, np.zeros(shape, np.float32))
+                np.testing.assert_array_equal(out[k], alone)
+                assert alone.max() > 0
+        finally:
+            D.dose_destroy(view)
+    finally:
+        D.dose_destroy(base)
+
+
 def test_slot_cap_and_reuse(gpu):
     """With one slot, requests run one at a time and reuse it; results are
     unchanged."""
