@@ -62,7 +62,7 @@ class RunOut(C.Structure):
         ("edep", C.c_void_p), ("depth_dose", C.c_void_p), ("plane_w", C.c_void_p),
         ("plane_m1", C.c_void_p), ("plane_m2", C.c_void_p), ("ledger", C.c_double * 4),
         ("steps", C.c_uint64), ("histories", C.c_uint64), ("status", C.c_int32),
-        ("end_depth", C.c_double * 2),
+        ("end_depth", C.c_double * 3),
     ]
 
 
@@ -277,6 +277,9 @@ def transport(phantom, plan, n_hist, seed, stream=0, phase=None, hist_range=None
     out = dict(edep=edep, ledger=np.array(O.ledger[:]), steps=int(O.steps),
                histories=int(O.histories), status=int(O.status),
                end_depth=(O.end_depth[0] / O.end_depth[1]) if O.end_depth[1] > 0 else float("nan"),
+               end_depth_sd=(np.sqrt(max(O.end_depth[2] / O.end_depth[1]
+                                         - (O.end_depth[0] / O.end_depth[1]) ** 2, 0.0))
+                             if O.end_depth[1] > 0 else float("nan")),
                end_weight=float(O.end_depth[1]))
     if dd is not None:
         out["depth_dose"] = dd

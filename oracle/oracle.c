@@ -313,17 +313,22 @@ double or_bohr_var(double E, double sw_mm)
     return OR_K * OR_ME * OR_ZA * (sw_mm / 10.0) * 0.5 * (gam * gam + 1.0);
 }
 
-/* Straggling fluctuation of a step whose mean (CSDA) loss is dE_mean: the
- * Bohr Gaussian sigma z, truncated symmetrically to [-dE_mean, +dE_mean] so
- * that the step's loss stays in [0, 2 dE_mean] and its expectation is the
- * CSDA loss for any step length (a one-sided cut at zero would add a
- * positive bias of about 0.4 sigma on thin steps, where sigma >> dE_mean). */
-static double or_straggle(double dE_mean, double var, double z)
+/* Energy loss of a step whose mean (CSDA) loss is m and whose Bohr
+ * variance is v, from the standard normal z: lognormal with exactly that
+ * mean and variance,
+ *   dE = m exp(sig z - sig^2 / 2),  sig^2 = ln(1 + v / m^2),
+ * so E[dE] = m and Var[dE] = m^2 (exp(sig^2) - 1) = v for every step length:
+ * the moments of the loss over a path do not depend on how the path is cut
+ * into steps (a Gaussian cut at zero or at +-m would lose variance on thin
+ * steps, where sqrt(v) >> m).  The loss is never negative and, like the
+ * loss in a thin absorber, skewed to high values; for thick steps
+ * (v << m^2) it tends to the Gaussian.  A step without mean loss loses
+ * nothing.                                                                 */
+static double or_straggle_loss(double m, double v, double z)
 {
-    double f = sqrt(var) * z;
-    if (f > dE_mean) f = dE_mean;
-    if (f < -dE_mean) f = -dE_mean;
-    return f;
+    if (!(m > 0.0) || !(v > 0.0)) return m;
+    double s2 = log1p(v / (m * m));
+    return m * exp(sqrt(s2) * z - 0.5 * s2);
 }
 
 /* Highland variance of the projected angle over radiation thickness
@@ -426,8 +431,9 @@ typedef struct {
     uint64_t steps;
     uint64_t histories;
     int32_t status;
-    double end_depth[2];         /* sum w z_end, sum w over histories that
-                                    stop by running out of energy */
+    double end_depth[3];         /* sum w z_end, sum w, sum w z_end^2 over
+                                    histories that stop by running out of
+                                    energy */
 } or_run_out;
 
 #define OR_PHYS_STRAG 1u
@@ -439,7 +445,7 @@ typedef struct {
     double ledger[4];
     uint64_t steps;
     int32_t status;
-    double end_depth[2];
+    double end_depth[3];
 } or_acc;
 
 static void or_depth_spread(const or_run_params *P, or_acc *A, double z0,
@@ -561,6 +567,7 @@ static void or_history(const or_run_params *P, const uint64_t *prefix,
             or_depth_spread(P, A, z_start, z_start, E * w);
             A->end_depth[0] += w * z_start;
             A->end_depth[1] += w;
+            A->end_depth[2] += w * z_start * z_start;
             return;
         }
         /* distance to the faces of the current voxel */
@@ -605,7 +612,7 @@ static void or_history(const or_run_params *P, const uint64_t *prefix,
 
         double dE = E - E1c;
         if (P->physics & OR_PHYS_STRAG) {
-            dE += or_straggle(dE, or_bohr_var(E, sw), zA0);
+            dE = or_straggle_loss(dE, or_bohr_var(E, sw), zA0);
             if (dE > E) dE = E;
         }
         double E1 = E - dE;
@@ -628,6 +635,7 @@ static void or_history(const or_run_params *P, const uint64_t *prefix,
             or_depth_spread(P, A, zend, zend, E1 * w);
             A->end_depth[0] += w * zend;
             A->end_depth[1] += w;
+            A->end_depth[2] += w * zend * zend;
             return;
         }
         A->edep[vox] += dE * w;
@@ -736,7 +744,7 @@ int or_transport(const or_run_params *P, or_run_out *O)
         }
         /* fixed-order reduction */
         memset(O->ledger, 0, sizeof(O->ledger));
-        O->end_depth[0] = O->end_depth[1] = 0.0;
+        O->end_depth[0] = O->end_depth[1] = O->end_depth[2] = 0.0;
         O->steps = 0;
         O->status = OR_OK;
         for (int t = 0; t < nt; ++t) {
@@ -752,6 +760,7 @@ int or_transport(const or_run_params *P, or_run_out *O)
             for (int k = 0; k < 4; ++k) O->ledger[k] += acc[t].ledger[k];
             O->end_depth[0] += acc[t].end_depth[0];
             O->end_depth[1] += acc[t].end_depth[1];
+            O->end_depth[2] += acc[t].end_depth[2];
             O->steps += acc[t].steps;
             if (acc[t].status) O->status = acc[t].status;
         }
@@ -787,8 +796,7 @@ void or_single_step(int hu, double E, double u0, double s, uint64_t seed,
     or_box_muller(u[0], u[1], &zA0, &zA1);
     or_box_muller(u[2], u[3], &z1u, &z2u);
     or_box_muller(u[4], u[5], &z1v, &z2v);
-    double dE = E - E1c;
-    dE += or_straggle(dE, or_bohr_var(E, sw), zA0);
+    double dE = or_straggle_loss(E - E1c, or_bohr_var(E, sw), zA0);
     if (dE > E) dE = E;
     double th2 = or_highland_theta2(Emean, u0, s * rho / OR_X0_MM);
     double th0 = th2 > 0.0 ? sqrt(th2) : 0.0;

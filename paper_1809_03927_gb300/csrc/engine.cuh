@@ -211,6 +211,25 @@ __device__ __forceinline__ float box_muller_first(float ua, float ub)
     return -r * __cosf(a);
 }
 
+// Energy loss of a step whose mean (CSDA) loss is m and whose Bohr variance
+// is v, from the standard normal z: lognormal with exactly that mean and
+// variance, m exp(sig z - sig^2 / 2) with sig^2 = ln(1 + v / m^2), so the
+// moments of the loss along a path do not depend on how it is cut into
+// steps.  Evaluated in base 2 with the hardware's approximate log2 and exp2
+// (PTX lg2.approx, ex2.approx): with L = log2(1 + v / m^2), the exponent
+// sig z - sig^2 / 2 is (sqrt(L log2(e)) z - L / 2) ln 2.  A step without a
+// positive mean loss keeps its CSDA loss (no fluctuation); m > 0 here is at
+// least an FP32 unit of the energy, so m * m does not underflow.
+__device__ __forceinline__ float straggle_loss(float m, float v, float z)
+{
+    const float x = __fdividef(v, m * m);
+    float L, f;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(L) : "f"(1.0f + x));
+    const float r = fast_sqrt(L * 1.44269504088896341f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(fmaf(r, z, -0.5f * L)));
+    return m > 0.0f ? m * f : m;
+}
+
 // a / b in FP64 for b > 0 without the library's double division (slow on
 // this part's FP64 units): the FP32 reciprocal refined by one Newton-Raphson
 // step y <- y + y (1 - b y) (24 -> ~48 correct bits), then one residual

@@ -439,11 +439,10 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         }
         float dE = E - E1c;
         if (physics & 1u) {
-            // Bohr fluctuation, truncated symmetrically at the mean loss so
-            // the step's expected loss is the CSDA loss for any length
+            // Bohr straggling: a lognormal loss with the CSDA loss as its
+            // mean and the Bohr variance, for any step length
             const float zA = box_muller_first(u.u[0], u.u[1]);
-            const float f = fast_sqrt(re0.y * sw) * zA;
-            dE = fminf(dE + fminf(fmaxf(f, -dE), dE), E);
+            dE = fminf(straggle_loss(dE, re0.y * sw, zA), E);
         }
         const float E1 = E - dE;
         dE = E - E1;

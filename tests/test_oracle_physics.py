@@ -225,10 +225,89 @@ def test_transverse_frame_is_orthonormal(orc):
 def test_straggling_unbiased_on_thin_steps(orc, hu, e, s):
     """The expected energy loss of a step is its CSDA loss E - E_w(R_w(E) -
     s SPR) whatever the step length, including steps so thin that the Bohr
-    width exceeds the mean loss (air, sub-micron remainders)."""
+    width exceeds the mean loss (air, sub-micron remainders); the loss is
+    never negative."""
     n = 40000
     de = np.array([orc.single_step(hu, e, 0.01, s, 3, h)[0] for h in range(n)])
     csda = e - orc.energy_from_range(orc.range_mm(e) - s * orc.spr(hu))
-    assert np.all(de >= 0.0) and np.all(de <= 2.0 * csda + 1e-15)
+    assert np.all(de >= 0.0)
     assert abs(de.mean() - csda) <= 5.0 * de.std() / math.sqrt(n) + 1e-12
     assert de.std() > 0.0
+
+
+@pytest.mark.parametrize("e,s", [(150.0, 2.0), (150.0, 0.05), (70.0, 0.02), (20.0, 0.5)])
+def test_straggling_variance_is_bohr_for_any_step(orc, e, s):
+    """Var(loss) of one step equals the Bohr variance K m_e (Z/A) s_w
+    (1 - beta^2/2)/(1 - beta^2) for thick steps (sigma << mean loss) and for
+    thin ones (sigma comparable to the mean loss), so the variance summed
+    along a path does not depend on how the path is cut into steps.  A
+    Gaussian cut at zero or at +-mean loss fails the thin cases (it keeps
+    0.67 of the variance at sigma/mean = 0.8)."""
+    n = 200000
+    de = np.array([orc.single_step(0, e, 0.01, s, 5, h)[0] for h in range(n)])
+    g = 1.0 + e / 938.27208816
+    want = 0.307075 * 0.51099895 * 0.55509 * (s / 10.0) * (g * g + 1.0) / 2.0
+    # the sample variance of a skewed loss: its standard error from the
+    # sample's fourth central moment
+    m = de.mean()
+    se = math.sqrt(max(np.mean((de - m) ** 4) - de.var() ** 2, 0.0) / n)
+    assert abs(de.var() - want) <= 4.0 * se + 1e-3 * want, (de.var(), want, se)
+    csda = e - orc.energy_from_range(orc.range_mm(e) - s)
+    assert abs(m - csda) <= 5.0 * de.std() / math.sqrt(n)
+
+
+# --------------------------------------------------- published tables
+# NIST PSTAR (Berger, Coursey, Zucker, Chang: ESTAR, PSTAR and ASTAR,
+# NIST Standard Reference Database 124; ICRU Report 49), liquid water,
+# I = 75 eV: electronic (collision) mass stopping power in MeV cm^2/g and
+# CSDA range in g/cm^2.
+PSTAR_WATER = {
+    70.0: (9.559, 4.080),
+    100.0: (7.289, 7.718),
+    150.0: (5.445, 15.77),
+    200.0: (4.492, 25.96),
+}
+
+
+@pytest.mark.parametrize("e", sorted(PSTAR_WATER))
+def test_stopping_power_and_range_against_pstar(orc, e):
+    """The Bethe formula with the full maximum transfer, I = 75 eV and Z/A =
+    0.55509 and no shell, density-effect or Barkas terms (the model) against
+    the published water table.  From 70 to 200 MeV the model is within
+    0.04 % of the table's stopping power and 0.13 % of its range (the
+    corrections the model leaves out matter most at low energy, where they
+    lengthen the tabulated range), so the stated gaps are 0.2 % (S) and
+    0.25 % (R).  A mean excitation energy
+    of 78 eV in place of 75 eV lowers S by about 0.5 % and lengthens R by
+    about 0.5 % and fails both; a wrong Z/A or a dropped beta^2 term fails
+    by more."""
+    s_tab, r_tab = PSTAR_WATER[e]
+    assert abs(orc.bethe_sw(e) - s_tab) / s_tab < 0.002, (orc.bethe_sw(e), s_tab)
+    r = orc.range_mm(e) / 10.0 + _range_below_cut(orc)           # g/cm^2 from zero energy
+    assert abs(r - r_tab) / r_tab < 0.0025, (r, r_tab)
+
+
+def _range_below_cut(orc):
+    """CSDA range of a 0.5 MeV proton in water (the tabulated range starts at
+    zero energy; the model's starts at the 0.5 MeV cut-off): 8.9e-4 g/cm^2 in
+    PSTAR.  Negligible against the tolerance, added for completeness."""
+    return 8.9e-4
+
+
+def test_planted_excitation_energy_fails_pstar(orc):
+    """Check that the PSTAR pin would catch I = 78 eV: the Bethe formula of
+    the model written out here with I = 78 eV misses the table by more than
+    the tolerance at every tabulated energy."""
+    me, mp, k, za = 0.51099895, 938.27208816, 0.307075, 0.55509
+
+    def bethe(e, i_mev):
+        g = 1.0 + e / mp
+        bg2 = g * g - 1.0
+        b2 = bg2 / (g * g)
+        r = me / mp
+        tmax = 2.0 * me * bg2 / (1.0 + 2.0 * g * r + r * r)
+        return k * za / b2 * (0.5 * math.log(2.0 * me * bg2 * tmax / (i_mev * i_mev)) - b2)
+
+    for e, (s_tab, _) in PSTAR_WATER.items():
+        assert abs(bethe(e, 75e-6) - orc.bethe_sw(e)) < 1e-12 * s_tab   # the same formula
+        assert abs(bethe(e, 78e-6) - s_tab) / s_tab > 0.004

@@ -69,6 +69,45 @@ def test_straggling_keeps_mean_range(orc):
     assert abs(r["end_depth"] - orc.range_mm(150.0)) < 0.1
 
 
+def _bohr_range_sd(orc, e0):
+    """Range straggling of the Bohr model, integrated here independently of
+    the transport: sigma_R^2 = int k(E) / S(E)^3 dE from the cut-off to E0,
+    with k the Bohr variance per mm of water and S the stopping power in
+    MeV/mm (each energy-loss fluctuation dE shifts the range by dE / S)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    v, _ = integrate.quad(lambda e: orc.bohr_var(e, 1.0) / (orc.bethe_sw(e) / 10.0) ** 3,
+                          0.5, e0, limit=400, epsrel=1e-10)
+    return math.sqrt(v)
+
+
+def _line_phantom(dz, depth_mm):
+    """One column of water voxels dz long along +z, 100 mm wide laterally,
+    so a zero-width pencil without scattering crosses only z faces."""
+    nz = int(math.ceil(depth_mm / dz))
+    return W.Phantom(np.zeros((nz, 1, 1), np.int16), (100.0, 100.0, dz), (-50.0, -50.0, 0.0))
+
+
+@pytest.mark.parametrize("energy,dz,n,tol", [(150.0, 0.05, 10000, 0.025), (70.0, 0.1, 20000, 0.02),
+                                             (150.0, 0.5, 20000, 0.02), (150.0, 2.0, 20000, 0.03),
+                                             (70.0, 2.0, 20000, 0.035)])
+def test_range_straggling_matches_bohr(orc, energy, dz, n, tol):
+    """With straggling alone, the standard deviation of the stopping depth of
+    a zero-width pencil is the Bohr range straggling (about 1.1 % of the
+    range), on voxels of 0.05 to 2 mm, i.e. for steps from 0.05 mm to 2 mm:
+    the loss model keeps the step's mean and variance whatever its length.
+    The coarse grids sit up to 2 % low (the discretisation of the
+    condensed-history steps, independent of the loss distribution); a
+    Gaussian fluctuation truncated at +-mean loss gives 0.88 at 0.05 mm and
+    150 MeV and fails.  Statistical error of the sd: 1/sqrt(2n), 0.5-0.7 %."""
+    want = _bohr_range_sd(orc, energy)
+    ph = _line_phantom(dz, orc.range_mm(energy) + 20.0)
+    r = orc.transport(ph, W.pencil_plan(energy=energy, sigma=0.0), n, 11,
+                      physics=orc.PHYS_STRAGGLING, max_steps=100000)
+    assert r["end_weight"] == n
+    assert abs(r["end_depth_sd"] / want - 1.0) < tol, (r["end_depth_sd"], want)
+    assert abs(r["end_depth"] - orc.range_mm(energy)) < 0.05
+
+
 @pytest.mark.parametrize("energy", [70.0, 150.0])
 def test_r80_full_physics(orc, energy):
     ph = W.water_phantom(nx=32, ny=32)
