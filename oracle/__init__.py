@@ -122,9 +122,9 @@ def lib():
                                         C.POINTER(DeliveryC)]
         L.or_breathing_deviate.argtypes = [C.c_uint64, C.c_int32, C.c_uint64]
         L.or_breathing_deviate.restype = C.c_int64
-        L.or_emtm.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P, P]
+        L.or_emtm.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P, C.c_double, P, P, P, P, P, P]
         L.or_dim.argtypes = [P, P, C.c_int32, C.c_int32, P, P, P, P, P]
-        L.or_dvf_decode.argtypes = [P] * 13
+        L.or_dvf_decode.argtypes = [P] * 11 + [C.c_double] + [P] * 3
         L.or_init_tables()
         _lib = L
     return _lib
@@ -365,13 +365,26 @@ def breathing_deviate(seed, field, cycle):
     return int(lib().or_breathing_deviate(int(seed), int(field), int(cycle)))
 
 
-def emtm(dose_phases, rho_phases, d, ref_phase, nsub, dvf=None, mask=None, return_sums=False):
-    """Energy/mass-transfer accumulation onto ``ref_phase`` plus Eq. 2 sum.
+# Tie tolerance of the accumulation's and the decode's integer decisions, in
+# cell / grid-index units: a single-precision implementation on grids of up
+# to a few hundred voxels per axis rounds the mapped coordinate by less than
+# about 3e-5 (a few units in the last place at 256).
+TIE_EPS = 1e-4
+
+
+def emtm(dose_phases, rho_phases, d, ref_phase, nsub, dvf=None, mask=None, return_sums=False,
+         bounds=False, eps=TIE_EPS):
+    """Energy/mass-transfer accumulation onto ``ref_phase`` plus Eq. 2 sum
+    (Sec. 2.D.2, Eqs. 2, 4-6), in FP64.
 
     ``dose_phases``/``rho_phases``: float32 (P, nz, ny, nx); ``dvf`` float32
     (P, 3, nz, ny, nx) mm (None = identity); ``mask`` uint8 (nz, ny, nx).
     Returns the FP64 accumulated dose (and the per-voxel E, M sums in units
     of the subvoxel volume when ``return_sums``) and the dropped count.
+    With ``bounds`` a dict follows: ``lo``/``hi`` bound the accumulated dose
+    of any decision of the subvoxels within ``eps`` of a cell face,
+    ``dropped_min``/``dropped_max`` the dropped count, ``ambiguous`` counts
+    those subvoxels.
     """
     ds = np.ascontiguousarray(dose_phases, np.float32)
     rs = np.ascontiguousarray(rho_phases, np.float32)
@@ -384,14 +397,19 @@ def emtm(dose_phases, rho_phases, d, ref_phase, nsub, dvf=None, mask=None, retur
     acc = np.zeros((nz, ny, nx), np.float64)
     es = np.zeros((nz, ny, nx), np.float64) if return_sums else None
     ms = np.zeros((nz, ny, nx), np.float64) if return_sums else None
-    dropped = np.zeros(1, np.uint64)
+    lo = np.zeros((nz, ny, nx), np.float64) if bounds else None
+    hi = np.zeros((nz, ny, nx), np.float64) if bounds else None
+    counts = np.zeros(4, np.uint64)
     rc = lib().or_emtm(_ptr(n), _ptr(dm), P_, int(ref_phase), _ptr(ns), _ptr(ds), _ptr(rs),
-                       _ptr(dv), _ptr(mk), _ptr(acc), _ptr(es), _ptr(ms), _ptr(dropped))
+                       _ptr(dv), _ptr(mk), float(eps), _ptr(acc), _ptr(es), _ptr(ms), _ptr(lo), _ptr(hi),
+                       _ptr(counts))
     if rc:
         raise ValueError(f"or_emtm failed: {rc}")
-    if return_sums:
-        return acc, es, ms, int(dropped[0])
-    return acc, int(dropped[0])
+    out = [acc] + ([es, ms] if return_sums else []) + [int(counts[0])]
+    if bounds:
+        out.append(dict(lo=lo, hi=hi, dropped_min=int(counts[1]), dropped_max=int(counts[2]),
+                        ambiguous=int(counts[3])))
+    return tuple(out)
 
 
 def dim(dose_phases, d, ref_phase, nsub, dvf=None, mask=None):
@@ -417,15 +435,18 @@ def dim(dose_phases, d, ref_phase, nsub, dvf=None, mask=None):
     return acc
 
 
-def dvf_decode(grid, delta, n, d, origin):
-    """Decode a registration's vector grid (App. B, Eqs. 7-8) onto a CT grid.
+def dvf_decode(grid, delta, n, d, origin, eps=TIE_EPS, return_ambiguous=False):
+    """Decode a registration's vector grid (App. B, Eqs. 7-8) onto a CT grid,
+    in FP64.
 
     ``grid``: dict with ``n`` (N_X, N_Y, N_Z), ``start_mm`` (centre of grid
     voxel 0), ``spacing_mm``, ``row_cos`` (U), ``col_cos`` (V) and optional
     ``pre``/``post`` row-major 4x4 rigid transforms; ``delta`` float32
     (N_Z, N_Y, N_X, 3) mm; the CT grid is ``n`` = (nx, ny, nz) voxels of
     size ``d`` with corner ``origin``.  Returns the FP64 displacement
-    (3, nz, ny, nx) in mm and the uint8 inside mask (nz, ny, nx).
+    (3, nz, ny, nx) in mm and the uint8 inside mask (nz, ny, nx), and with
+    ``return_ambiguous`` the uint8 flags of the voxels whose grid index lies
+    within ``eps`` of a hull face (either decision is then correct).
     """
     f32 = lambda v: np.ascontiguousarray(np.asarray(v, np.float32).ravel())
     eye = np.eye(4, dtype=np.float32)
@@ -437,8 +458,12 @@ def dvf_decode(grid, delta, n, d, origin):
     nx, ny, nz = (int(v) for v in n)
     disp = np.zeros((3, nz, ny, nx), np.float64)
     inside = np.zeros((nz, ny, nx), np.uint8)
-    args += [dl, np.array(n, np.int32), f32(d), f32(origin), disp, inside]   # kept alive for the call
-    rc = lib().or_dvf_decode(*[_ptr(a) for a in args])
+    amb = np.zeros((nz, ny, nx), np.uint8)
+    args += [dl, np.array(n, np.int32), f32(d), f32(origin)]                # kept alive for the call
+    ptrs = [_ptr(a) for a in args]
+    rc = lib().or_dvf_decode(*ptrs, float(eps), _ptr(disp), _ptr(inside), _ptr(amb))
     if rc:
         raise ValueError(f"or_dvf_decode failed: {rc}")
+    if return_ambiguous:
+        return disp, inside, amb
     return disp, inside

@@ -44,11 +44,15 @@
  *                      moments and bounds of the breathing deviates.
  *   or_trial_delivery  Sec. 2.B (the 25 uncertainty trials).  Pinned:
  *                      discrete-uniform periods, Gaussian moments.
- *   or_emtm            Sec. 2.D.2, Eqs. 2, 4-6.  Pinned: identity-DVF test
- *                      of Sec. 2.E, integer translation, mass conservation,
- *                      brute force.
+ *   or_emtm            Sec. 2.D.2, Eqs. 2, 4-6, in FP64, with bounds for
+ *                      points on cell faces.  Pinned: identity-DVF test of
+ *                      Sec. 2.E, integer and half-voxel translations,
+ *                      energy and mass conservation, the mask, convergence
+ *                      in n, agreement with the DIM for inverse whole-voxel
+ *                      shifts.
  *   or_dvf_decode      App. B, Eqs. 7-8, and the DICOM rule that positions
- *                      between grid voxels interpolate trilinearly.  Pinned:
+ *                      between grid voxels interpolate trilinearly; FP64,
+ *                      with a flag for voxels on the hull faces.  Pinned:
  *                      uniform and affine translations (exact under
  *                      trilinear interpolation), rotated grid axes, the
  *                      depth axis W = U x V, rigid pre/post transforms, the
@@ -1272,143 +1276,9 @@ int64_t or_breathing_deviate(uint64_t seed, int32_t f, uint64_t c)
     return or_irwin_hall(seed, (uint32_t)f, (uint32_t)c, 1u);
 }
 
-/* ======================================================================= */
-/* Energy/mass-transfer accumulation (Sec. 2.D.2, Eqs. 4-6) and the phase  */
-/* sum of Eq. 2.                                                           */
-/*                                                                         */
-/* Each voxel j of every source phase S != R is split into nsub[0] x       */
-/* nsub[1] x nsub[2] subvoxels; subvoxel centre r_jk is moved by the DVF   */
-/* of S (trilinear between voxel centres, edge-clamped) and lands in the   */
-/* reference voxel i whose half-open cell contains it.  Subvoxel mass is   */
-/* M = rho_j v_k and energy E = M D_j (Eq. 4); D_i^S = sum E / sum M over  */
-/* the subvoxels landing in i (Eqs. 5, 6), 0 where none lands; D_i = D_i^R */
-/* + sum_S D_i^S (Eq. 2), zero outside the mask.                           */
-/*                                                                         */
-/* The target voxel is an integer decided by floating point; it is taken  */
-/* in single precision with the operation order written below (the        */
-/* displacement goes to voxel units through the single-precision          */
-/* reciprocal of the voxel size), the precision the GPU kernel decides it */
-/* in.  Sums and ratios are FP64.                                          */
-/* ======================================================================= */
-static float or_f_lerp(float a, float b, float t)
-{
-    volatile float diff = b - a;
-    volatile float prod = t * diff;
-    volatile float r = a + prod;
-    return r;
-}
-
-static float or_f_sample(const float *comp, const int32_t *n, float qx, float qy, float qz)
-{
-    float q[3] = { qx, qy, qz };
-    int32_t i0[3], i1[3];
-    float f[3];
-    for (int a = 0; a < 3; ++a) {
-        float fl = floorf(q[a]);
-        volatile float fr = q[a] - fl;
-        f[a] = fr;
-        int32_t k = (int32_t)fl;
-        int32_t k1 = k + 1;
-        if (k < 0) k = 0;
-        if (k > n[a] - 1) k = n[a] - 1;
-        if (k1 < 0) k1 = 0;
-        if (k1 > n[a] - 1) k1 = n[a] - 1;
-        i0[a] = k; i1[a] = k1;
-    }
-#define OR_AT(x, y, z) comp[((size_t)(z) * n[1] + (y)) * n[0] + (x)]
-    float c00 = or_f_lerp(OR_AT(i0[0], i0[1], i0[2]), OR_AT(i1[0], i0[1], i0[2]), f[0]);
-    float c10 = or_f_lerp(OR_AT(i0[0], i1[1], i0[2]), OR_AT(i1[0], i1[1], i0[2]), f[0]);
-    float c01 = or_f_lerp(OR_AT(i0[0], i0[1], i1[2]), OR_AT(i1[0], i0[1], i1[2]), f[0]);
-    float c11 = or_f_lerp(OR_AT(i0[0], i1[1], i1[2]), OR_AT(i1[0], i1[1], i1[2]), f[0]);
-#undef OR_AT
-    float c0 = or_f_lerp(c00, c10, f[1]);
-    float c1 = or_f_lerp(c01, c11, f[1]);
-    return or_f_lerp(c0, c1, f[2]);
-}
-
-int or_emtm(const int32_t n[3], const float dmm[3], int32_t n_phases,
-            int32_t ref_phase, const int32_t nsub[3], const float *dose,
-            const float *rho, const float *dvf, const uint8_t *mask,
-            double *accum, double *e_sum, double *m_sum, uint64_t *dropped)
-{
-    if (n_phases <= 0 || ref_phase < 0 || ref_phase >= n_phases ||
-        nsub[0] <= 0 || nsub[1] <= 0 || nsub[2] <= 0)
-        return OR_EINVAL;
-    size_t nvox = (size_t)n[0] * n[1] * n[2];
-    double *E = (double *)calloc(nvox, sizeof(double));
-    double *M = (double *)calloc(nvox, sizeof(double));
-    if (!E || !M) { free(E); free(M); return OR_ENOMEM; }
-    for (size_t i = 0; i < nvox; ++i) accum[i] = (double)dose[(size_t)ref_phase * nvox + i];
-    uint64_t drop = 0;
-    for (int32_t S = 0; S < n_phases; ++S) {
-        if (S == ref_phase) continue;
-        memset(E, 0, nvox * sizeof(double));
-        memset(M, 0, nvox * sizeof(double));
-        const float *ds = dose + (size_t)S * nvox;
-        const float *rs = rho + (size_t)S * nvox;
-        for (int32_t jz = 0; jz < n[2]; ++jz)
-        for (int32_t jy = 0; jy < n[1]; ++jy)
-        for (int32_t jx = 0; jx < n[0]; ++jx) {
-            size_t j = ((size_t)jz * n[1] + jy) * n[0] + jx;
-            double m = (double)rs[j];
-            double e = (double)rs[j] * (double)ds[j];
-            for (int32_t kz = 0; kz < nsub[2]; ++kz)
-            for (int32_t ky = 0; ky < nsub[1]; ++ky)
-            for (int32_t kx = 0; kx < nsub[0]; ++kx) {
-                /* subvoxel centre in continuous voxel-centre index space:
-                   q = j + (k + 1/2)/nsub - 1/2 */
-                int32_t jj[3] = { jx, jy, jz }, kk[3] = { kx, ky, kz };
-                float q[3], t[3];
-                for (int a = 0; a < 3; ++a) {
-                    volatile float frac = ((float)kk[a] + 0.5f) / (float)nsub[a];
-                    volatile float s1 = (float)jj[a] + frac;
-                    volatile float s2 = s1 - 0.5f;
-                    q[a] = s2;
-                }
-                for (int a = 0; a < 3; ++a) {
-                    float disp = 0.0f;
-                    if (dvf) disp = or_f_sample(dvf + ((size_t)S * 3 + a) * nvox, n, q[0], q[1], q[2]);
-                    volatile float base = q[a] + 0.5f;
-                    volatile float inv = 1.0f / dmm[a];
-                    volatile float off = disp * inv;
-                    volatile float r = base + off;
-                    t[a] = r;
-                }
-                int32_t ix = (int32_t)floorf(t[0]), iy = (int32_t)floorf(t[1]), iz = (int32_t)floorf(t[2]);
-                if (ix < 0 || ix >= n[0] || iy < 0 || iy >= n[1] || iz < 0 || iz >= n[2]) { ++drop; continue; }
-                size_t i = ((size_t)iz * n[1] + iy) * n[0] + ix;
-                E[i] += e;
-                M[i] += m;
-            }
-        }
-        for (size_t i = 0; i < nvox; ++i) {
-            if (M[i] > 0.0) accum[i] += E[i] / M[i];
-            if (e_sum) e_sum[i] += E[i];
-            if (m_sum) m_sum[i] += M[i];
-        }
-    }
-    if (mask)
-        for (size_t i = 0; i < nvox; ++i) if (!mask[i]) accum[i] = 0.0;
-    if (dropped) *dropped = drop;
-    free(E); free(M);
-    return OR_OK;
-}
-
-/* ======================================================================= */
-/* Dose-interpolation accumulation (Sec. 2.D.2, Eq. 3) and the phase sum of */
-/* Eq. 2.                                                                   */
-/*                                                                          */
-/* For every source phase S != R and every reference voxel i, the voxel is  */
-/* split into nsub[0] x nsub[1] x nsub[2] subvoxels; the centre r_ik of     */
-/* each is carried to phase S by the reference-to-source field T^{R->S}     */
-/* (its displacement, in mm, given at the reference voxel centres and       */
-/* interpolated trilinearly between them), the dose of S is interpolated    */
-/* trilinearly at the carried point, and D_i^S is the mean over the         */
-/* subvoxels (Eq. 3).  D_i = D_i^R + sum_S D_i^S (Eq. 2), zero outside the  */
-/* mask.  Both interpolations use the values at voxel centres and clamp to  */
-/* the edge outside them (a point carried past the grid takes the dose of   */
-/* the nearest edge voxel).  Everything is FP64.                            */
-/* ======================================================================= */
+/* A component of a field given at voxel centres (x fastest), interpolated
+ * trilinearly at q in voxel-centre index space (voxel i's centre at i),
+ * clamped to the edge values outside the outermost centres.  FP64.        */
 static double or_d_sample(const float *comp, const int32_t *n, const double q[3])
 {
     int32_t lo[3], hi[3];
@@ -1432,6 +1302,188 @@ static double or_d_sample(const float *comp, const int32_t *n, const double q[3]
     return v;
 }
 
+/* ======================================================================= */
+/* Energy/mass-transfer accumulation (Sec. 2.D.2, Eqs. 4-6) and the phase  */
+/* sum of Eq. 2, in FP64.                                                  */
+/*                                                                         */
+/* Each voxel j of every source phase S != R is split into nsub[0] x       */
+/* nsub[1] x nsub[2] subvoxels; the centre of subvoxel k, in voxel-centre  */
+/* index space q = j + (k + 1/2)/nsub - 1/2, is moved by the DVF of S      */
+/* (trilinear between voxel centres, edge-clamped: or_d_sample), giving    */
+/* the cell coordinate t = q + 1/2 + u / d, and lands in the reference     */
+/* voxel i = floor(t) whose half-open cell [i, i + 1) holds it.  Subvoxel  */
+/* mass is M = rho_j v_k and energy E = M D_j (Eq. 4); D_i^S = sum E / sum */
+/* M over the subvoxels landing in i (Eqs. 5, 6), 0 where none lands; D_i  */
+/* = D_i^R + sum_S D_i^S (Eq. 2), zero outside the mask.  Points landing   */
+/* outside the grid are dropped and counted.                               */
+/*                                                                         */
+/* Ties.  The target voxel is an integer decided by floating point: a      */
+/* point within eps (cell units) of a cell face may be decided either way  */
+/* by any finite-precision implementation.  Besides its own decision, the  */
+/* oracle reports such points as ambiguous and bounds what any decision    */
+/* of them can give: with the unambiguous points fixed, the D_i^S that     */
+/* results when the ambiguous ones go to any of their candidate cells is a */
+/* mass-weighted mean of the unambiguous ratio and the source doses D_j of */
+/* the candidates (or 0 when nothing lands), so it lies in [lo_i^S,        */
+/* hi_i^S], the range of those values; lo_i and hi_i sum these bounds over */
+/* the phases like Eq. 2.  Without ambiguous points lo = hi = accum.       */
+/* counts: [0] dropped (this decision), [1] dropped under every decision   */
+/* of the ambiguous points, [2] dropped under some decision, [3] ambiguous */
+/* subvoxels.                                                              */
+/* ======================================================================= */
+static int or_cell_candidates(const double t[3], const int32_t n[3], double eps,
+                              int32_t cand[8][3], int *n_out)
+{
+    int32_t lo[3], alt[3];
+    int amb = 0;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (int32_t)floor(t[a]);
+        double face = floor(t[a] + 0.5);              /* nearest cell face */
+        alt[a] = lo[a];
+        if (fabs(t[a] - face) < eps) {
+            alt[a] = (lo[a] == (int32_t)face) ? lo[a] - 1 : (int32_t)face;
+            amb = 1;
+        }
+    }
+    int m = 0, out = 0;
+    for (int c = 0; c < 8; ++c) {
+        int32_t v[3];
+        int skip = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (c & (1 << a)) { if (alt[a] == lo[a]) { skip = 1; break; } v[a] = alt[a]; }
+            else v[a] = lo[a];
+        }
+        if (skip) continue;
+        cand[m][0] = v[0]; cand[m][1] = v[1]; cand[m][2] = v[2];
+        if (v[0] < 0 || v[0] >= n[0] || v[1] < 0 || v[1] >= n[1] || v[2] < 0 || v[2] >= n[2]) ++out;
+        ++m;
+    }
+    *n_out = m;
+    return amb ? (out == m ? 2 : (out ? 1 : 0)) + 4 : (out ? 2 : 0);
+}
+
+int or_emtm(const int32_t n[3], const float dmm[3], int32_t n_phases,
+            int32_t ref_phase, const int32_t nsub[3], const float *dose,
+            const float *rho, const float *dvf, const uint8_t *mask, double eps,
+            double *accum, double *e_sum, double *m_sum, double *accum_lo,
+            double *accum_hi, uint64_t counts[4])
+{
+    if (n_phases <= 0 || ref_phase < 0 || ref_phase >= n_phases ||
+        nsub[0] <= 0 || nsub[1] <= 0 || nsub[2] <= 0)
+        return OR_EINVAL;
+    size_t nvox = (size_t)n[0] * n[1] * n[2];
+    double *E = (double *)calloc(nvox, sizeof(double));
+    double *M = (double *)calloc(nvox, sizeof(double));
+    double *E0 = (double *)calloc(nvox, sizeof(double));
+    double *M0 = (double *)calloc(nvox, sizeof(double));
+    double *clo = (double *)malloc(nvox * sizeof(double));
+    double *chi = (double *)malloc(nvox * sizeof(double));
+    if (!E || !M || !E0 || !M0 || !clo || !chi) {
+        free(E); free(M); free(E0); free(M0); free(clo); free(chi);
+        return OR_ENOMEM;
+    }
+    for (size_t i = 0; i < nvox; ++i) {
+        double r = (double)dose[(size_t)ref_phase * nvox + i];
+        accum[i] = r;
+        if (accum_lo) accum_lo[i] = r;
+        if (accum_hi) accum_hi[i] = r;
+    }
+    uint64_t cnt[4] = { 0, 0, 0, 0 };
+    for (int32_t S = 0; S < n_phases; ++S) {
+        if (S == ref_phase) continue;
+        memset(E, 0, nvox * sizeof(double));
+        memset(M, 0, nvox * sizeof(double));
+        memset(E0, 0, nvox * sizeof(double));
+        memset(M0, 0, nvox * sizeof(double));
+        for (size_t i = 0; i < nvox; ++i) { clo[i] = INFINITY; chi[i] = -INFINITY; }
+        const float *ds = dose + (size_t)S * nvox;
+        const float *rs = rho + (size_t)S * nvox;
+        for (int32_t jz = 0; jz < n[2]; ++jz)
+        for (int32_t jy = 0; jy < n[1]; ++jy)
+        for (int32_t jx = 0; jx < n[0]; ++jx) {
+            size_t j = ((size_t)jz * n[1] + jy) * n[0] + jx;
+            double m = (double)rs[j];
+            double dj = (double)ds[j];
+            double e = m * dj;
+            int32_t jj[3] = { jx, jy, jz };
+            for (int32_t kz = 0; kz < nsub[2]; ++kz)
+            for (int32_t ky = 0; ky < nsub[1]; ++ky)
+            for (int32_t kx = 0; kx < nsub[0]; ++kx) {
+                int32_t kk[3] = { kx, ky, kz };
+                double q[3], t[3];
+                for (int a = 0; a < 3; ++a)
+                    q[a] = (double)jj[a] + ((double)kk[a] + 0.5) / (double)nsub[a] - 0.5;
+                for (int a = 0; a < 3; ++a) {
+                    double u = dvf ? or_d_sample(dvf + ((size_t)S * 3 + a) * nvox, n, q) : 0.0;
+                    t[a] = q[a] + 0.5 + u / (double)dmm[a];
+                }
+                int32_t ix = (int32_t)floor(t[0]), iy = (int32_t)floor(t[1]), iz = (int32_t)floor(t[2]);
+                int inside = !(ix < 0 || ix >= n[0] || iy < 0 || iy >= n[1] || iz < 0 || iz >= n[2]);
+                size_t i = inside ? ((size_t)iz * n[1] + iy) * n[0] + ix : 0;
+                if (inside) { E[i] += e; M[i] += m; } else ++cnt[0];
+                int32_t cand[8][3];
+                int nc = 0;
+                int cls = or_cell_candidates(t, n, eps, cand, &nc);
+                if (!(cls & 4)) {                       /* unambiguous */
+                    if (inside) { E0[i] += e; M0[i] += m; }
+                    else { ++cnt[1]; ++cnt[2]; }
+                    continue;
+                }
+                ++cnt[3];
+                if ((cls & 3) == 2) ++cnt[1];          /* every candidate outside */
+                if (cls & 3) ++cnt[2];                 /* some candidate outside */
+                if (!(m > 0.0)) continue;              /* carries no mass */
+                for (int c = 0; c < nc; ++c) {
+                    if (cand[c][0] < 0 || cand[c][0] >= n[0] || cand[c][1] < 0 ||
+                        cand[c][1] >= n[1] || cand[c][2] < 0 || cand[c][2] >= n[2])
+                        continue;
+                    size_t ic = ((size_t)cand[c][2] * n[1] + cand[c][1]) * n[0] + cand[c][0];
+                    if (dj < clo[ic]) clo[ic] = dj;
+                    if (dj > chi[ic]) chi[ic] = dj;
+                }
+            }
+        }
+        for (size_t i = 0; i < nvox; ++i) {
+            if (M[i] > 0.0) accum[i] += E[i] / M[i];
+            if (e_sum) e_sum[i] += E[i];
+            if (m_sum) m_sum[i] += M[i];
+            double base = M0[i] > 0.0 ? E0[i] / M0[i] : 0.0;
+            double lo = base, hi = base;
+            if (clo[i] <= chi[i]) {                    /* an ambiguous point may land here */
+                if (clo[i] < lo) lo = clo[i];
+                if (chi[i] > hi) hi = chi[i];
+            }
+            if (accum_lo) accum_lo[i] += lo;
+            if (accum_hi) accum_hi[i] += hi;
+        }
+    }
+    if (mask)
+        for (size_t i = 0; i < nvox; ++i)
+            if (!mask[i]) {
+                accum[i] = 0.0;
+                if (accum_lo) accum_lo[i] = 0.0;
+                if (accum_hi) accum_hi[i] = 0.0;
+            }
+    if (counts) for (int k = 0; k < 4; ++k) counts[k] = cnt[k];
+    free(E); free(M); free(E0); free(M0); free(clo); free(chi);
+    return OR_OK;
+}
+
+/* ======================================================================= */
+/* Dose-interpolation accumulation (Sec. 2.D.2, Eq. 3) and the phase sum of */
+/* Eq. 2.                                                                   */
+/*                                                                          */
+/* For every source phase S != R and every reference voxel i, the voxel is  */
+/* split into nsub[0] x nsub[1] x nsub[2] subvoxels; the centre r_ik of     */
+/* each is carried to phase S by the reference-to-source field T^{R->S}     */
+/* (its displacement, in mm, given at the reference voxel centres and       */
+/* interpolated trilinearly between them), the dose of S is interpolated    */
+/* trilinearly at the carried point, and D_i^S is the mean over the         */
+/* subvoxels (Eq. 3).  D_i = D_i^R + sum_S D_i^S (Eq. 2), zero outside the  */
+/* mask.  Both interpolations use the values at voxel centres and clamp to  */
+/* the edge outside them (a point carried past the grid takes the dose of   */
+/* the nearest edge voxel).  Everything is FP64.                            */
+/* ======================================================================= */
 int or_dim(const int32_t n[3], const float dmm[3], int32_t n_phases, int32_t ref_phase,
            const int32_t nsub[3], const float *dose, const float *dvf, const uint8_t *mask,
            double *accum)
@@ -1475,7 +1527,7 @@ int or_dim(const int32_t n[3], const float dmm[3], int32_t n_phases, int32_t ref
 
 /* ======================================================================= */
 /* Decoding a registration's vector grid (App. B, Eqs. 7-8) onto the CT     */
-/* grid.                                                                    */
+/* grid, in FP64.                                                           */
 /*                                                                          */
 /* Grid voxel (i, j, k) sits at r0 = start + i dX U + j dY V + k dZ W with  */
 /* W = U x V (Eq. 8) and maps to r_f = M_post (M_pre r0 + Delta_ijk)        */
@@ -1488,11 +1540,12 @@ int or_dim(const int32_t n[3], const float dmm[3], int32_t n_phases, int32_t ref
 /* voxel is left out of the mask (Sec. 2.D.2: dose is reported only where   */
 /* every DVF is defined).                                                   */
 /*                                                                          */
-/* Inside-ness is an integer decided by floating point: the continuous     */
-/* index is formed in single precision in the order written below, the     */
-/* precision and order of the GPU kernel.  Positions and interpolation are  */
-/* FP64.  pre, post: row-major 4 x 4.  delta: (Dx, Dy, Dz) per grid voxel,  */
-/* x fastest.                                                               */
+/* Inside-ness is an integer decided by floating point: a voxel whose       */
+/* continuous index lies within eps (grid-index units) of 0 or N - 1 on     */
+/* some axis, and clearly inside on the others, may be decided either way  */
+/* by a finite-precision implementation, and is flagged in `ambiguous` (the */
+/* oracle's own decision is the FP64 one above).  pre, post: row-major      */
+/* 4 x 4.  delta: (Dx, Dy, Dz) per grid voxel, x fastest.                   */
 /* ======================================================================= */
 static void or_affine(const float *M, const double v[3], double out[3])
 {
@@ -1501,15 +1554,11 @@ static void or_affine(const float *M, const double v[3], double out[3])
                  (double)M[4 * r + 2] * v[2] + (double)M[4 * r + 3];
 }
 
-static float or_f_mul(float a, float b) { volatile float r = a * b; return r; }
-static float or_f_add(float a, float b) { volatile float r = a + b; return r; }
-static float or_f_sub(float a, float b) { volatile float r = a - b; return r; }
-static float or_f_div(float a, float b) { volatile float r = a / b; return r; }
-
 int or_dvf_decode(const int32_t gn[3], const float gstart[3], const float gsp[3],
                   const float U[3], const float V[3], const float pre[16],
                   const float post[16], const float *delta, const int32_t n[3],
-                  const float d[3], const float origin[3], double *disp, uint8_t *inside)
+                  const float d[3], const float origin[3], double eps, double *disp,
+                  uint8_t *inside, uint8_t *ambiguous)
 {
     if (gn[0] <= 0 || gn[1] <= 0 || gn[2] <= 0 || !(gsp[0] > 0) || !(gsp[1] > 0) ||
         !(gsp[2] > 0))
@@ -1518,49 +1567,47 @@ int or_dvf_decode(const int32_t gn[3], const float gstart[3], const float gsp[3]
     const size_t nvox = (size_t)n[0] * n[1] * n[2];
     double *rf = (double *)malloc(3 * ng * sizeof(double));
     if (!rf) return OR_ENOMEM;
-    /* depth direction W = U x V (FP64 for positions, FP32 for the decision) */
-    const double Wd[3] = { (double)U[1] * V[2] - (double)U[2] * V[1],
-                           (double)U[2] * V[0] - (double)U[0] * V[2],
-                           (double)U[0] * V[1] - (double)U[1] * V[0] };
-    const float Wf[3] = { or_f_sub(or_f_mul(U[1], V[2]), or_f_mul(U[2], V[1])),
-                          or_f_sub(or_f_mul(U[2], V[0]), or_f_mul(U[0], V[2])),
-                          or_f_sub(or_f_mul(U[0], V[1]), or_f_mul(U[1], V[0])) };
+    const double Ud[3] = { U[0], U[1], U[2] }, Vd[3] = { V[0], V[1], V[2] };
+    const double Wd[3] = { Ud[1] * Vd[2] - Ud[2] * Vd[1],     /* W = U x V */
+                           Ud[2] * Vd[0] - Ud[0] * Vd[2],
+                           Ud[0] * Vd[1] - Ud[1] * Vd[0] };
     for (int32_t k = 0; k < gn[2]; ++k)
     for (int32_t j = 0; j < gn[1]; ++j)
     for (int32_t i = 0; i < gn[0]; ++i) {
         size_t g = ((size_t)k * gn[1] + j) * gn[0] + i;
         double r0[3], a[3], b[3];
         for (int c = 0; c < 3; ++c)           /* Eq. 8 */
-            r0[c] = (double)gstart[c] + (double)i * gsp[0] * U[c] + (double)j * gsp[1] * V[c] +
+            r0[c] = (double)gstart[c] + (double)i * gsp[0] * Ud[c] + (double)j * gsp[1] * Vd[c] +
                     (double)k * gsp[2] * Wd[c];
         or_affine(pre, r0, a);                /* Eq. 7 */
         for (int c = 0; c < 3; ++c) a[c] += (double)delta[3 * g + c];
         or_affine(post, a, b);
         for (int c = 0; c < 3; ++c) rf[c * ng + g] = b[c];
     }
-    const float *axes[3] = { U, V, Wf };
+    const double *axes[3] = { Ud, Vd, Wd };
     for (int32_t iz = 0; iz < n[2]; ++iz)
     for (int32_t iy = 0; iy < n[1]; ++iy)
     for (int32_t ix = 0; ix < n[0]; ++ix) {
         size_t v = ((size_t)iz * n[1] + iy) * n[0] + ix;
         int32_t ii[3] = { ix, iy, iz };
-        float rel[3];
-        double p[3];
+        double p[3], rel[3];
         for (int c = 0; c < 3; ++c) {
-            float pc = or_f_add(origin[c], or_f_mul(or_f_add((float)ii[c], 0.5f), d[c]));
-            rel[c] = or_f_sub(pc, gstart[c]);
             p[c] = (double)origin[c] + ((double)ii[c] + 0.5) * (double)d[c];
+            rel[c] = p[c] - (double)gstart[c];
         }
-        float q[3];
-        int in = 1;
+        double q[3];
+        int in = 1, near = 0, far_out = 0;
         for (int a = 0; a < 3; ++a) {
-            const float *ax = axes[a];
-            float dot = or_f_add(or_f_add(or_f_mul(ax[0], rel[0]), or_f_mul(ax[1], rel[1])),
-                                 or_f_mul(ax[2], rel[2]));
-            q[a] = or_f_div(dot, gsp[a]);
-            if (!(q[a] >= 0.0f && q[a] <= (float)(gn[a] - 1))) in = 0;
+            const double *ax = axes[a];
+            q[a] = (ax[0] * rel[0] + ax[1] * rel[1] + ax[2] * rel[2]) / (double)gsp[a];
+            if (!(q[a] >= 0.0 && q[a] <= (double)(gn[a] - 1))) in = 0;
+            if (fabs(q[a]) < eps || fabs(q[a] - (double)(gn[a] - 1)) < eps) near = 1;
+            else if (!(q[a] > 0.0 && q[a] < (double)(gn[a] - 1))) far_out = 1;
         }
+        /* a decision can change only near a face and not outside on another axis */
+        int amb = near && !far_out;
         inside[v] = (uint8_t)in;
+        if (ambiguous) ambiguous[v] = (uint8_t)amb;
         if (!in) {
             for (int c = 0; c < 3; ++c) disp[c * nvox + v] = 0.0;
             continue;
@@ -1568,8 +1615,8 @@ int or_dvf_decode(const int32_t gn[3], const float gstart[3], const float gsp[3]
         int32_t lo[3], hi[3];
         double f[3];
         for (int a = 0; a < 3; ++a) {
-            double fl = floor((double)q[a]);
-            f[a] = (double)q[a] - fl;
+            double fl = floor(q[a]);
+            f[a] = q[a] - fl;
             lo[a] = (int32_t)fl;
             hi[a] = lo[a] + 1 > gn[a] - 1 ? gn[a] - 1 : lo[a] + 1;
         }

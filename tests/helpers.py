@@ -151,6 +151,27 @@ def gamma_pass(ref, evl, spacing, dd=0.01, dta=1.0, threshold=0.1, step=0.25):
     return float(np.mean(best <= 1.0))
 
 
+def check_emtm(got, want, bounds, rtol=2e-6, atol=1e-9, where=None):
+    """The device's energy/mass-transfer accumulation against the oracle's
+    (Sec. 2.D.2, Eqs. 2, 4-6).  A subvoxel whose mapped point lies within the
+    tie tolerance of a cell face may be decided either way by any
+    finite-precision implementation; every other subvoxel must land where
+    the oracle puts it.  So: where no such subvoxel can land (the oracle's
+    bounds coincide) the doses agree within the tolerance of the fixed-point
+    sums; elsewhere the device's dose lies within the oracle's bounds.
+    ``where`` restricts the check to a boolean region.  Returns the number of
+    voxels an ambiguous subvoxel can reach (to report)."""
+    lo, hi = bounds["lo"], bounds["hi"]
+    sel = np.ones(got.shape, bool) if where is None else where
+    exact = (lo == hi) & sel
+    np.testing.assert_allclose(got[exact], want[exact], rtol=rtol, atol=atol)
+    tied = (lo != hi) & sel
+    g = got[tied].astype(np.float64)
+    ok = (g >= lo[tied] * (1 - rtol) - atol) & (g <= hi[tied] * (1 + rtol) + atol)
+    assert ok.all(), (int((~ok).sum()), int(tied.sum()))
+    return int(tied.sum())
+
+
 def small_4dct(n_phases=4, nx=64, ny=64, nz=40, motion_pp=15.0):
     ph, dvf, geo = W.phantom_4dct(nx, ny, nz, (1.0, 1.0, 2.5), n_phases=n_phases, motion_pp=motion_pp)
     return ph, dvf, geo

@@ -1,12 +1,15 @@
 """Registration-grid decode (App. B, Eqs. 7-8) on the GPU against the
 oracle's or_dvf_decode.
 
-The hull mask is an integer decision taken in the same single-precision
-order on both sides, so it must match bit for bit.  The displacement is
-FP32 on the GPU (grid displacement e = r_f - r0 formed with the rigid parts
-folded, then interpolated) and FP64 in the oracle; with |r0| < 100 mm and
-|e| < 20 mm the FP32 rounding is below 1e-5 mm, so the test allows
-1e-4 mm + 1e-5 relative.
+The hull mask is an integer decided by floating point: the oracle decides
+it in FP64 and flags the CT voxels whose grid index lies within its tie
+tolerance of a hull face, where either decision is correct; every other
+voxel must match bit for bit (and where every quantity is exactly
+representable, as on the grids of CT voxel centres below, so must those).
+The displacement is FP32 on the GPU (grid displacement e = r_f - r0 formed
+with the rigid parts folded, then interpolated) and FP64 in the oracle; with
+|r0| < 100 mm and |e| < 20 mm the FP32 rounding is below 1e-5 mm, so the
+test allows 1e-4 mm + 1e-5 relative where both sides call the voxel inside.
 """
 import numpy as np
 import pytest
@@ -92,13 +95,15 @@ def test_decode_parity(gpu, orc, name):
         gmask = mask.cpu().numpy().reshape(nz, ny, nx)
     finally:
         gpu.dose_destroy(ctx)
-    want, inside = orc.dvf_decode(g, delta, N, D, ORIGIN)
-    np.testing.assert_array_equal(gmask, inside)
-    assert inside.sum() > 500
-    assert np.all(got[:, inside == 0] == 0.0)
+    want, inside, amb = orc.dvf_decode(g, delta, N, D, ORIGIN, return_ambiguous=True)
+    sure = amb == 0
+    np.testing.assert_array_equal(gmask[sure], inside[sure])
+    assert inside.sum() > 500 and amb.sum() <= 0.01 * amb.size, int(amb.sum())
+    assert np.all(got[:, gmask == 0] == 0.0)
+    both = (gmask == 1) & (inside == 1)
     tol = 1e-4 + 1e-5 * np.abs(want)
-    bad = np.abs(got - want) > tol
-    assert not bad.any(), (int(bad.sum()), float(np.abs(got - want).max()))
+    bad = (np.abs(got - want) > tol) & both[None]
+    assert not bad.any(), (int(bad.sum()), float(np.abs(got - want)[:, both].max()))
 
 
 def test_decode_masks_intersect_over_phases(gpu, orc):
@@ -114,11 +119,12 @@ def test_decode_masks_intersect_over_phases(gpu, orc):
         gmask = mask.cpu().numpy().reshape(nz, ny, nx)
     finally:
         gpu.dose_destroy(ctx)
-    a = orc.dvf_decode(gs["axis_partial"], np.zeros(tuple(gs["axis_partial"]["n"][::-1]) + (3,), np.float32),
-                       N, D, ORIGIN)[1]
-    b = orc.dvf_decode(gs["oblique"], np.zeros(tuple(gs["oblique"]["n"][::-1]) + (3,), np.float32),
-                       N, D, ORIGIN)[1]
-    np.testing.assert_array_equal(gmask, a & b)
+    _, a, amb_a = orc.dvf_decode(gs["axis_partial"], np.zeros(tuple(gs["axis_partial"]["n"][::-1]) + (3,),
+                                                             np.float32), N, D, ORIGIN, return_ambiguous=True)
+    _, b, amb_b = orc.dvf_decode(gs["oblique"], np.zeros(tuple(gs["oblique"]["n"][::-1]) + (3,), np.float32),
+                                 N, D, ORIGIN, return_ambiguous=True)
+    sure = (amb_a == 0) & (amb_b == 0)
+    np.testing.assert_array_equal(gmask[sure], (a & b)[sure])
     assert 0 < gmask.sum() < min(a.sum(), b.sum())
 
 
@@ -170,5 +176,7 @@ def test_decoded_field_drives_the_accumulation(gpu, orc):
     assert gmask.all()
     np.testing.assert_allclose(dec, dvf, rtol=0, atol=2e-5)
     rho = np.stack([orc.density(ph, p) for p in range(P)]).astype(np.float32)
-    want, _ = orc.emtm(doses, rho, ph.d, 0, (2, 2, 5), dvf=dec, mask=gmask)
-    np.testing.assert_allclose(acc, want, rtol=2e-6, atol=1e-9)
+    _, inside = orc.dvf_decode(g, np.ascontiguousarray(np.moveaxis(dvf[P - 1], 0, -1)), ph.n, ph.d, ph.origin)
+    assert inside.all()                  # grid on the CT voxel centres: exact, hull faces included
+    want, _, B = orc.emtm(doses, rho, ph.d, 0, (2, 2, 5), dvf=dec, mask=gmask, bounds=True)
+    H.check_emtm(acc, want, B)

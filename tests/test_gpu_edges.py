@@ -123,7 +123,7 @@ def test_one_voxel_registration_grid(gpu, orc):
     finally:
         gpu.dose_destroy(ctx)
     want, inside = orc.dvf_decode(g, delta, (nx, ny, nz), (2.0, 2.0, 2.0), (0.0, 0.0, 0.0))
-    np.testing.assert_array_equal(m, inside)
+    np.testing.assert_array_equal(m, inside)          # exact values: the single centre is inside
     assert m.sum() == 1 and m[0, 1, 2] == 1                 # centre (5, 3, 1) is voxel (2, 1, 0)
     np.testing.assert_allclose(got[:, 0, 1, 2], [0.25, -0.5, 1.0], atol=1e-6)
     np.testing.assert_allclose(got, want, atol=1e-6)

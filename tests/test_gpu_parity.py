@@ -442,11 +442,14 @@ def test_emtm_parity(gpu, orc, case):
         stats = gpu.dose_read(ctx, gpu.DOSE_EMTM_STATS, 0, np.zeros(4, np.uint64))
     finally:
         gpu.dose_destroy(ctx)
-    want, dropped = orc.emtm(doses, rho, ph.d, ref, nsub, dvf=use_dvf, mask=mask)
-    np.testing.assert_allclose(acc, want, rtol=2e-6, atol=1e-9)
-    assert int(stats[1]) == dropped
+    want, dropped, B = orc.emtm(doses, rho, ph.d, ref, nsub, dvf=use_dvf, mask=mask, bounds=True)
+    tied = H.check_emtm(acc, want, B)
     nvox = doses[0].size
     assert int(stats[0]) == (doses.shape[0] - 1) * nvox * 20
+    assert B["dropped_min"] <= int(stats[1]) <= B["dropped_max"]
+    # subvoxels on a cell face are rare: a few per ten thousand pushed
+    assert B["ambiguous"] <= 1e-3 * int(stats[0]), B["ambiguous"]
+    print(f"{case}: {B['ambiguous']} of {int(stats[0])} subvoxels within the tie tolerance, {tied} voxels affected")
     if case == "identity":
         np.testing.assert_allclose(acc, doses.astype(np.float64).sum(axis=0), rtol=2e-6)
 
@@ -479,9 +482,9 @@ def test_emtm_sparse_dose_reach(gpu, orc, case):
         stats = gpu.dose_read(ctx, gpu.DOSE_EMTM_STATS, 0, np.zeros(4, np.uint64))
     finally:
         gpu.dose_destroy(ctx)
-    want, dropped = orc.emtm(doses, rho, ph.d, 0, nsub, dvf=field)
-    np.testing.assert_allclose(acc, want, rtol=2e-6, atol=1e-9)
-    assert acc.max() > 0 and int(stats[1]) <= dropped
+    want, dropped, B = orc.emtm(doses, rho, ph.d, 0, nsub, dvf=field, bounds=True)
+    H.check_emtm(acc, want, B)
+    assert acc.max() > 0 and int(stats[1]) <= B["dropped_max"]
     boxes = [H.reach_box((rho[p] > 0) & (doses[p] > 0), None if field is None else field[p], ph.d, 2)
              for p in range(1, P)]
     assert int(stats[0]) == 20 * sum(H.box_voxels(b) for b in boxes)
@@ -513,8 +516,8 @@ def test_emtm_after_a_dense_accumulation(gpu, orc):
     finally:
         gpu.dose_destroy(ctx)
     for acc, doses in zip(got, (dense, sparse, dense)):
-        want, _ = orc.emtm(doses, rho, ph.d, 0, (2, 2, 5), dvf=dvf)
-        np.testing.assert_allclose(acc, want, rtol=2e-6, atol=1e-9)
+        want, _, B = orc.emtm(doses, rho, ph.d, 0, (2, 2, 5), dvf=dvf, bounds=True)
+        H.check_emtm(acc, want, B)
     np.testing.assert_array_equal(got[0], got[2])
 
 

@@ -105,12 +105,17 @@ def test_readme_example_runs(gpu):
     assert scope["acc"].max() > 0
 
 
-def test_emtm_full_size_properties(gpu):
+def test_emtm_full_size_properties(gpu, orc):
     """The EMTM on the 10-phase 256 x 256 x 160 4DCT with (2, 2, 5)
     subvoxels, properties that hold at any size: with no field the
     accumulation is the phase sum; with the breathing field, voxels whose
     whole neighbourhood stays still in every phase keep the phase sum, every
-    subvoxel is pushed once, and the moving region changes the dose."""
+    subvoxel is pushed once, and the moving region changes the dose.  Then
+    the oracle's EMTM on a crop through the right lung and the tumour, wider
+    than the largest displacement (15 mm = 6 voxels, along z only): inside
+    the crop's interior (8 voxels from its z faces, 1 from the others) every
+    subvoxel that lands comes from the crop and sees the same field, so the
+    full-size device result there is the oracle's."""
     import torch
     ph, dvf, geo = W.phantom_4dct()
     P = ph.n_phases
@@ -142,3 +147,14 @@ def test_emtm_full_size_properties(gpu):
     np.testing.assert_allclose(moved[safe], total[safe], rtol=2e-6)
     assert not np.allclose(moved[~safe], total[~safe], rtol=1e-3)
     assert int(stats[0]) == (P - 1) * nx * ny * nz * 20
+    assert np.abs(dvf[:, :2]).max() == 0.0 and np.abs(dvf).max() <= 15.0
+    z0, z1, y0, y1, x0, x1 = 30, 130, 90, 150, 50, 100
+    rho = np.stack([orc.density(ph, p)[z0:z1, y0:y1, x0:x1] for p in range(P)]).astype(np.float32)
+    sub = np.ascontiguousarray(doses[:, z0:z1, y0:y1, x0:x1])
+    field = np.ascontiguousarray(dvf[:, :, z0:z1, y0:y1, x0:x1])
+    want, _, B = orc.emtm(sub, rho, ph.d, 0, NSUB, dvf=field, bounds=True)
+    inner = np.zeros(want.shape, bool)
+    inner[8:-8, 1:-1, 1:-1] = True
+    crop = moved[z0:z1, y0:y1, x0:x1]
+    H.check_emtm(crop, want, B, where=inner)
+    assert not np.allclose(crop[inner], sub.astype(np.float64).sum(axis=0)[inner], rtol=1e-3)

@@ -297,3 +297,87 @@ def test_emtm_converges_in_n(orc):
     err1 = np.abs(res[1] - res[6]).mean()
     err2 = np.abs(res[2] - res[6]).mean()
     assert err2 < 0.5 * err1
+
+
+def _emtm_numpy(dose, rho, d, nsub, u_x, flip_ties):
+    """An independent restatement of Eqs. 2, 4-6 for a field that moves every
+    point by the constant u_x (mm) along x: the subvoxel centre at cell
+    coordinate t = j + (k + 1/2)/n lands in floor(t + u_x/d_x).  With
+    ``flip_ties`` a point exactly on a cell face goes to the cell below it
+    instead (the other legitimate decision).  Returns (accumulated dose,
+    dropped count)."""
+    P, nz, ny, nx = dose.shape
+    dose, rho = dose.astype(np.float64), rho.astype(np.float64)
+    acc = dose[0].copy()
+    dropped = 0
+    for S in range(1, P):
+        E = np.zeros((nz, ny, nx))
+        M = np.zeros((nz, ny, nx))
+        for kz in range(nsub[2]):
+            for ky in range(nsub[1]):
+                for kx in range(nsub[0]):
+                    t = np.arange(nx) + (kx + 0.5) / nsub[0] + u_x / d[0]
+                    i = np.floor(t).astype(int)
+                    if flip_ties:
+                        i = np.where(t == np.floor(t), i - 1, i)
+                    ok = (i >= 0) & (i < nx)
+                    dropped += int((~ok).sum()) * nz * ny
+                    for jx in np.nonzero(ok)[0]:
+                        E[:, :, i[jx]] += rho[S, :, :, jx] * dose[S, :, :, jx]
+                        M[:, :, i[jx]] += rho[S, :, :, jx]
+        acc += np.where(M > 0, E / np.where(M > 0, M, 1.0), 0.0)
+    return acc, dropped
+
+
+def test_emtm_bounds_cover_either_decision_of_points_on_faces(orc):
+    """A field of a quarter voxel along x with two subvoxels along x puts every
+    second subvoxel centre exactly on a cell face (t = j + 1).  The oracle
+    flags those points, decides them itself (floor: the upper cell), and
+    bounds what any decision gives: an independent implementation deciding
+    every tie the other way (the lower cell) gives another dose, inside the
+    bounds, and a dropped count inside the reported range; an implementation
+    deciding like the oracle gives the oracle's dose; voxels no tied point
+    can reach have lo = hi = the oracle's dose."""
+    rng = np.random.default_rng(11)
+    shape = (3, 4, 7)
+    dose, rho = _fields(rng, 3, shape)
+    d = (2.0, 1.0, 1.0)
+    dvf = np.zeros((3, 3) + shape, np.float32)
+    dvf[1:, 0] = 0.5                                   # u/d = 1/4 exactly
+    nsub = (2, 1, 1)
+    acc, dropped, B = orc.emtm(dose, rho, d, 0, nsub, dvf=dvf, bounds=True)
+    same, drop_same = _emtm_numpy(dose, rho, d, nsub, 0.5, flip_ties=False)
+    other, drop_other = _emtm_numpy(dose, rho, d, nsub, 0.5, flip_ties=True)
+    np.testing.assert_allclose(acc, same, rtol=1e-12)
+    assert dropped == drop_same
+    assert B["ambiguous"] == 2 * 3 * 4 * 7             # half of the subvoxels of two source phases
+    assert not np.allclose(other, acc, rtol=1e-6)
+    for a in (acc, other):
+        assert np.all(a >= B["lo"] * (1 - 1e-12)) and np.all(a <= B["hi"] * (1 + 1e-12))
+    assert B["dropped_min"] <= min(dropped, drop_other) and max(dropped, drop_other) <= B["dropped_max"]
+    # no field: no ties, the bounds collapse onto the result
+    acc0, _, B0 = orc.emtm(dose, rho, d, 0, nsub, bounds=True)
+    assert B0["ambiguous"] == 0
+    np.testing.assert_array_equal(B0["lo"], acc0)
+    np.testing.assert_array_equal(B0["hi"], acc0)
+
+
+def test_decode_flags_voxels_on_the_hull_faces(orc):
+    """A registration grid whose hull faces pass through CT voxel centres:
+    those voxels are flagged (either decision is correct there), the ones
+    strictly inside or outside are not, and the FP64 decision puts the faces
+    inside (the hull is closed)."""
+    g = dict(n=(5, 4, 3), start_mm=(1.0, 1.0, 1.0), spacing_mm=(2.0, 2.0, 2.0), row_cos=(1, 0, 0),
+             col_cos=(0, 1, 0))
+    delta = np.zeros((3, 4, 5, 3), np.float32)
+    n = (12, 10, 8)
+    _, inside, amb = orc.dvf_decode(g, delta, n, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), return_ambiguous=True)
+    # CT centres i + 1/2 never meet the grid points 1 + 2 m: nothing is on a face
+    assert amb.sum() == 0 and inside.sum() > 0
+    g2 = dict(g, start_mm=(0.5, 0.5, 0.5))                # grid points on CT centres 0, 2, 4, ...
+    _, inside2, amb2 = orc.dvf_decode(g2, delta, n, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), return_ambiguous=True)
+    k, j, i = np.meshgrid(np.arange(8), np.arange(10), np.arange(12), indexing="ij")
+    want_in = (i <= 8) & (j <= 6) & (k <= 4)
+    np.testing.assert_array_equal(inside2.astype(bool), want_in)
+    face = want_in & ((i == 0) | (i == 8) | (j == 0) | (j == 6) | (k == 0) | (k == 4))
+    np.testing.assert_array_equal(amb2.astype(bool), face)
