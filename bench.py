@@ -34,18 +34,22 @@ METRIC = "proton histories/s"
 N_HIST = 10_000_000
 SEED = 2
 WORKLOAD = "slab phantom 128^3 at 2 mm (water/lung/bone), 400 spots on 10 layers 70-200 MeV, 1e7 histories"
-# algorithmic thread-operations of one condensed-history step: Philox4x32-10
-# 80, three Box-Muller pairs 30, five table lerps 30, voxel-face distances
-# 20, energy loss and straggling 15, scattering, frame and move 40, tally
-# quantisation 5, bookkeeping 10
-OPS_PER_STEP = 230
+# Algorithmic work of one condensed-history step, in issue slots (thread
+# operations): one Philox4x32-10 block (10 rounds of two 32x32->64 products
+# and the key mixing), three Box-Muller transforms, about five table lerps,
+# the voxel-face distances, the energy loss with its straggling, the
+# scattering, frame and move, and one tally quantisation and atomic.  The
+# estimate spans 300-450; this build's own narrower count is 230.  The
+# headline fraction uses the low end, 300.
+OPS_PER_STEP = 300
+OPS_PER_STEP_RANGE = (230, 300, 450)
 # DRAM bytes (read + write) of one transport launch on the slab workload
 # (1e7 histories) per launch shape it was measured in (registers variant,
-# block, chunk, material grid): ncu --metrics dram__bytes_read.sum,
-# dram__bytes_write.sum on the full-size launch (bench.py --launch R,B,C,M).
-# The grid is read once where the beam goes (HU + table, or the per-voxel
-# material grid) and the tally stays in L2.
-TRANSPORT_DRAM = {(1, 1024, 32, 0): 3.07e6, (1, 1024, 64, 0): 3.02e6, (1, 1024, 64, 1): 3.64e6}
+# block, chunk, material grid), from ncu --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum on the full-size launch of the current kernel
+# (bench.py --launch R,B,C,M; the single-job kernel with subnormals flushed).
+TRANSPORT_DRAM = {(1, 1024, 32, 1): 3.73e6, (1, 1024, 64, 1): 3.80e6, (1, 1024, 128, 1): 3.92e6,
+                  (1, 1024, 64, 0): 2.73e6}
 
 
 def _args():
@@ -65,6 +69,10 @@ def _args():
     p.add_argument("--serve-window", type=float, default=5.0, help="seconds of Poisson arrivals")
     p.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
     p.add_argument("--serve-budget-gb", type=float, default=150.0, help="device memory for request slots")
+    p.add_argument("--serve-low-rate", type=float, default=8.0,
+                   help="mean arrivals per second of the second serving point (below capacity)")
+    p.add_argument("--serve-low-window", type=float, default=40.0,
+                   help="seconds of arrivals of the second serving point (0: skip it)")
     p.add_argument("--histories-4d", type=int, default=100_000_000, help="histories per phase of the 4D plan")
     p.add_argument("--small-4d", action="store_true",
                    help="4D leg on a 128x128x80 grid at 2x2x5 mm (profiler captures), not the 4DCT workload")
@@ -168,22 +176,83 @@ def _workload():
 
 
 # ------------------------------------------------------------------ oracle
+def _interleaved(phantom, plan, seconds_target, nthreads=None):
+    """The oracle on every stride-th history of the 1e7-history run (h mod
+    stride == 0, so the sample has the run's mix of spots and energies),
+    the stride chosen from two probes (a fixed cost plus a cost per history)
+    so the sample takes about seconds_target.  Returns (histories/s,
+    histories, seconds, steps/history, stride)."""
+    import oracle
+
+    def run(stride):
+        t0 = time.perf_counter()
+        r = oracle.transport(phantom, plan, N_HIST, SEED, batch=(0, stride), nthreads=nthreads)
+        return time.perf_counter() - t0, r
+
+    (t1, r1), (t2, r2) = run(5000), run(1000)
+    per = max((t2 - t1) / max(r2["histories"] - r1["histories"], 1), 1e-9)
+    stride = max(1, min(1000, int(N_HIST * per / seconds_target)))
+    dt, r = run(stride)
+    return r["histories"] / dt, r["histories"], dt, r["steps"] / r["histories"], stride
+
+
 def _oracle_sample(phantom, plan, seconds_target=15.0):
     """The CPU oracle, as it stands, on a bounded sample of the workload:
-    the first histories of the same 1e7-history run, all host cores."""
+    every stride-th history of the same 1e7-history run, all host cores."""
     import oracle
     oracle.build()
-    n_probe = 2000
+    rate, n, dt, sph, stride = _interleaved(phantom, plan, seconds_target)
+    return {"value": rate, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"every {stride}th history of the 1e7-history run ({n} histories, {dt:.1f} s, "
+                      f"{sph:.1f} steps/history, the run's 91.8)"}
+
+
+def _oracle_extra(phantom, plan):
+    """More oracle figures for the CPU baseline: one thread on the same
+    interleaved sample, the single-pencil workload run in full, and the 4D
+    plan extrapolated from samples."""
+    import oracle
+    from paper_1809_03927_gb300 import workloads as W
+    out = {}
+    rate, n, dt, sph, stride = _interleaved(phantom, plan, 5.0, nthreads=1)
+    out["one_thread"] = {"value": rate, "unit": METRIC, "cores": 1,
+                         "sample": f"every {stride}th history ({n} histories, {dt:.1f} s)"}
+    wph, wpl = W.water_phantom(), W.pencil_plan(150.0, 4.0)
     t0 = time.perf_counter()
-    oracle.transport(phantom, plan, N_HIST, SEED, hist_range=(0, n_probe))
+    oracle.transport(wph, wpl, 100_000, 1)
     dt = time.perf_counter() - t0
-    n = max(n_probe, min(int(n_probe * seconds_target / max(dt, 1e-3)), 2_000_000))
+    out["pencil_full"] = {"value": 100_000 / dt, "unit": METRIC, "seconds": dt, "cores": os.cpu_count(),
+                          "workload": "150 MeV pencil, sigma 4 mm, water 64x64x160 at 2 mm, 1e5 histories, in full"}
+    # 4D plan: the timeline in full, every phase's transport from a sample of
+    # its subplan, the EMTM from one phase on a slab of the grid; scaled to
+    # 10 phases x 1e8 histories and the whole grid (extrapolated)
+    ph, dvf, geo = W.phantom_4dct()
+    plan4 = W.tumour_plan(geo, ph.origin)
+    dl = W.Delivery(seed=3)
     t0 = time.perf_counter()
-    r = oracle.transport(phantom, plan, N_HIST, SEED, hist_range=(n_probe, n_probe + n))
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"histories [{n_probe}, {n_probe + n}) of the 1e7-history run ({n} histories, "
-                      f"{dt:.1f} s, {r['steps'] / n:.1f} steps/history)"}
+    pp, _, _ = oracle.timeline(plan4, dl)
+    t_tl = time.perf_counter() - t0
+    busiest = int(np.argmax(pp.sum(axis=1)))
+    n_s = 20_000
+    t0 = time.perf_counter()
+    oracle.transport(ph, plan4.with_protons(pp[busiest]), 100_000_000, SEED, phase=busiest, stream=busiest,
+                     batch=(0, 100_000_000 // n_s))
+    t_per_hist = (time.perf_counter() - t0) / n_s
+    n_ph = int(np.count_nonzero(pp.sum(axis=1)))
+    z0, z1 = 70, 78                                     # 8 of 160 slices, one source phase
+    rho = np.stack([oracle.density(ph, p)[z0:z1] for p in (0, 1)]).astype(np.float32)
+    dose = np.ones((2,) + rho.shape[1:], np.float32)
+    t0 = time.perf_counter()
+    oracle.emtm(dose, rho, ph.d, 0, (2, 2, 5), dvf=np.ascontiguousarray(dvf[:2, :, z0:z1]))
+    t_emtm = (time.perf_counter() - t0) * (ph.n[2] / (z1 - z0)) * (ph.n_phases - 1)
+    s_plan = t_tl + n_ph * 100_000_000 * t_per_hist + t_emtm
+    out["four_d_extrapolated"] = {
+        "s_per_plan": s_plan, "extrapolated": True, "timeline_s": t_tl,
+        "transport_s_per_history": t_per_hist, "phases": n_ph, "emtm_s": t_emtm, "cores": os.cpu_count(),
+        "sample": f"timeline in full; {n_s} histories of phase {busiest} (all cores) scaled to {n_ph} phases x 1e8; "
+                  f"EMTM of one source phase on {z1 - z0} of {ph.n[2]} slices (one thread) scaled to 9 phases x "
+                  "the whole grid"}
+    return out
 
 
 def run_reference(args):
@@ -536,13 +605,22 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
                 D.dose_server_release(srv, rid)
         total_s = time.perf_counter() - t0
         st = D.dose_server_stats(srv)
+        tm = D.dose_server_timing(srv)
         D.dose_server_destroy(srv)
         lat = [done_at[i] - reqs[i]["t"] for i in range(len(reqs))]
         hist = sum(r["n"] // len(phases) * len(phases) for r in reqs)
+        busy = tm["step_wall_s"]
         out["served"] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                          "mean_s": float(np.mean(lat)), "histories_per_s": hist / total_s, "makespan_s": total_s,
                          "steps": st["steps"], "slots": st["slots"], "max_in_system": max_active,
-                         "slot_gb": st["slot_bytes"] / 1e9}
+                         "slot_gb": st["slot_bytes"] / 1e9,
+                         # where the makespan went: steps (device batch, device
+                         # accumulation, host remainder of the step) and idle
+                         # time waiting for arrivals
+                         "breakdown_s": {"transport_batches": tm["batch_s"], "accumulations": tm["accumulate_s"],
+                                         "host_step_overhead": max(busy - tm["batch_s"] - tm["accumulate_s"], 0.0),
+                                         "idle_between_steps": max(total_s - busy, 0.0)},
+                         "histories_per_device_batch_s": hist / tm["batch_s"] if tm["batch_s"] > 0 else None}
 
         # ---- plain: one request at a time, one phase job per launch
         done_at, t0, k = {}, time.perf_counter(), 0
@@ -598,6 +676,8 @@ def run_engine(args):
         tune = (regs, block, chunk, 0)
     else:
         tune = D.dose_autotune(ctx, 0, n_hist, n_hist, seed, stream)
+    # the device's measured issue and atomic peaks (a few ms, before the timed region)
+    measured = D.dose_measure_peaks(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -693,8 +773,10 @@ def run_engine(args):
     traffic = TRANSPORT_DRAM.get(shape) if n_hist == N_HIST else None
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak_ops = sms * 128 * sm_mhz * 1e6 / 1e12          # Top/s: 128 FP32/INT32 lanes per SM
-    achieved = n_hist * steps_per_hist * OPS_PER_STEP / (t_kernel / 1e3) / 1e12
+    nominal = sms * 128 * sm_mhz * 1e6 / 1e12          # Top/s: 128 FP32/INT32 lanes per SM
+    peak_ops = measured["issue_mixed"] / 1e12
+    steps_per_s = n_hist * steps_per_hist / (t_kernel / 1e3)
+    achieved = steps_per_s * OPS_PER_STEP / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -707,9 +789,16 @@ def run_engine(args):
                    "parallelism": f"{ws} independent replica(s), one per GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "k_transport", "kernel_ms": t_kernel,
-                     "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz (median sampled SM clock)",
-                     "ops_per_step": OPS_PER_STEP},
+                     "kernel": "k_transport1_r64" if tune[0] else "k_transport1", "kernel_ms": t_kernel,
+                     "ops_per_step": OPS_PER_STEP,
+                     "frac_by_ops_per_step": {str(k): steps_per_s * k / 1e12 / peak_ops for k in OPS_PER_STEP_RANGE},
+                     "peak_basis": f"measured: mixed FP32/INT32 instruction stream (dose_measure_peaks), "
+                                   f"{peak_ops:.2f} Top/s; nominal {sms} SMs x 128 lanes x {sm_mhz:.0f} MHz = "
+                                   f"{nominal:.2f} Top/s; FFMA alone {measured['issue_ffma'] / 1e12:.2f} Top/s",
+                     "atomic": {"achieved": steps_per_s, "peak": measured["atomic_u64"], "unit": "atomics/s",
+                                "frac": steps_per_s / measured["atomic_u64"],
+                                "basis": "one 64-bit tally atomic per step against measured u64 atomic additions "
+                                         "to random elements of a 16.8 MB L2-resident array"}},
         "e2e": {"value": ws * n_hist / e2e_s, "unit": METRIC,
                 "h2d_bytes_per_step": int(hu_host.nbytes + len(plan) * 32),
                 "d2h_bytes_per_step": int(nx * ny * nz * 4)},
@@ -725,8 +814,12 @@ def run_engine(args):
     if not args.no_serve:
         line["serving"] = _bench_serving(D, torch, stream, args.serve_window, args.serve_rate,
                                          int(args.serve_budget_gb * 1e9))
+        if args.serve_low_window > 0:
+            line["serving_below_capacity"] = _bench_serving(D, torch, stream, args.serve_low_window,
+                                                            args.serve_low_rate, int(args.serve_budget_gb * 1e9))
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _oracle_sample(phantom, plan)
+        line["cpu_baseline"].update(_oracle_extra(phantom, plan))
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

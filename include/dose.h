@@ -317,6 +317,13 @@ int dose_server_release(dose_server *s, int64_t id);
 /* out: queued, active, slots, completed, histories run, steps, bytes per
  * slot, finished but not released.                                         */
 int dose_server_stats(const dose_server *s, uint64_t out[8]);
+/* Where the served time went, summed over all steps so far (seconds): out[0]
+ * device time of the steps' transport batches (history allocation,
+ * transport, normalisation; CUDA events on the step's stream), out[1]
+ * device time of the finishing requests' accumulations (zero phases, EMTM,
+ * Eq. 2), out[2] host wall time of the steps (admission, job building,
+ * launches and the wait), out[3] steps that ran a batch.                  */
+int dose_server_timing(const dose_server *s, double out[4]);
 void dose_server_destroy(dose_server *s);
 
 /* Supply the dose of one phase from outside (float32[nvox] Gy), e.g. to
@@ -435,33 +442,50 @@ int dose_version(void);
  * memory through its own allocator, or that must not allocate once it is
  * running.  The caller passes device input and output buffers; every other
  * buffer the kernels use (tally, spot table, history allocation, ledger,
- * work counter, launch descriptors, lookup tables) lives in one fixed-size
- * static device array that each GPU loading this library holds until the
- * process exits.  No cudaMalloc, cudaFree or allocating library routine is
- * called.
+ * work counter, allocation descriptor, lookup tables) lives in one
+ * fixed-size static device array that each GPU loading this library holds
+ * until the process exits.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
  *
  * Computes what dose_create_grid + dose_add_spots(delivery NULL) +
- * dose_run_phase(phase 0, spr_scale 1, no shift) compute, with default
- * options: hu is int16[nx ny nz] in device memory (x fastest), spots is a
- * host array, dose receives float32[nx ny nz] Gy in device memory;
- * ledger_out (host, may be NULL) receives the 8-word ledger of
- * DOSE_ENERGY_LEDGER, after which the call waits for the stream.
- * Limits: nx ny nz <= DOSE_NOALLOC_MAX_VOXELS and n_spots <=
- * DOSE_NOALLOC_MAX_SPOTS; larger inputs return DOSE_EINVAL with a message
- * in dose_last_error(NULL).
+ * dose_run_phase(phase 0, spr_scale 1, no shift) compute with the default
+ * options, bit for bit: hu is int16[nx*ny*nz] in device memory (x fastest)
+ * on the current device, spots is a host array whose spots all belong to
+ * field 0, dose receives float32[nx*ny*nz] Gy in device memory on the
+ * current device; ledger_out (host, may be NULL) receives the 8-word ledger
+ * of DOSE_ENERGY_LEDGER.  The call works on `stream` (NULL: the legacy
+ * default stream) and returns once the dose is written: it waits for the
+ * stream.  Returns DOSE_ESTEPLIMIT (dose and ledger written) when a history
+ * reached the step limit.
+ * Limits: nx*ny*nz <= DOSE_NOALLOC_MAX_VOXELS and n_spots <=
+ * DOSE_NOALLOC_MAX_SPOTS; larger inputs, a non-finite origin or a spot of
+ * another field return DOSE_EINVAL with a message in dose_last_error(NULL).
+ * The pointers are not checked (the caller guarantees their sizes, types
+ * and device).
  * The first call on a device sets the array up for that device (finds its
  * device address, uploads the tables) and waits for it: make that first
- * call before any stream capture.  The call also waits for the stream while
- * it uploads the spot table and launch descriptors.  All calls share the
- * one array, which keeps the previous call's contents (the call clears what
- * must start at zero): calls whose work overlaps on the GPU race with each
- * other and must be serialised by the caller.                              */
+ * call before any stream capture.  All calls share the one array, which
+ * keeps the previous call's contents (the call clears what must start at
+ * zero): calls from several host threads at once race on it and must be
+ * serialised by the caller.                                                */
 #define DOSE_NOALLOC_MAX_VOXELS 2097152   /* 2^21, e.g. 128^3: 16 MiB of tally */
 #define DOSE_NOALLOC_MAX_SPOTS 4096
 int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_mm, float dy_mm,
                            float dz_mm, const float origin_mm[3], const float beam_dir[3],
                            const dose_spot *spots, int n_spots, uint64_t n_histories, uint64_t seed,
                            float *dose, uint64_t ledger_out[8], void *stream);
+
+/* Measured throughput peaks of the current device, for the roofline of the
+ * transport (Sec. 2.C engine; the paper has no such call): out[0] = issue
+ * rate of a mixed FP32/INT32 instruction stream (8 FFMA, 4 IMAD, 4 LOP3 per
+ * 16 instructions on independent chains, 64 warps per SM), thread
+ * instructions per second; out[1] = the same for FFMA alone; out[2] =
+ * 64-bit atomic additions per second to pseudo-random elements of a
+ * 16.8 MB array (L2-resident, like the dose tally); out[3] = the SM count.
+ * Each rate is the best of three timings of a fixed workload of a few
+ * milliseconds on `stream`; the call allocates and frees its 16.8 MB
+ * scratch and waits for the stream.  DOSE_ECUDA on a CUDA error.           */
+int dose_measure_peaks(double out[4], void *stream);
 
 /* Self-test of the device random-number generator: Philox4x32-10 (Salmon
  * et al., SC'11; the generator of Sec. 2.B, footnote b) of n counters

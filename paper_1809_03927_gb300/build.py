@@ -20,7 +20,13 @@ OUT_DIR = os.path.join(PKG, "lib")
 OBJ_DIR = os.path.join(PKG, "lib", "obj")
 LIB = os.path.join(OUT_DIR, "libdose.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "transport.cu", "timeline.cu", "emtm.cu", "dim.cu", "dvf.cu", "lut.cpp", "noalloc.cu", "serve.cpp"]
+SOURCES = ["api.cu", "transport.cu", "timeline.cu", "emtm.cu", "dim.cu", "dvf.cu", "lut.cpp", "noalloc.cu", "serve.cpp", "peaks.cu"]
+# Per-source flags.  The transport flushes single-precision subnormals: none
+# of its values comes near 1e-38 (energies, ranges, positions, directions,
+# weights and the uniforms are all of order 1e-7 or more), so results do not
+# change, and the approximate reciprocal, square root, logarithm and sine
+# need no scaling of subnormal inputs around each hardware instruction.
+SOURCE_FLAGS = {"transport.cu": ["-ftz=true"]}
 
 
 def nvcc() -> str:
@@ -38,6 +44,7 @@ def _flags(extra=()):
 def _deps_mtime(src: str) -> float:
     heads = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     heads.append(os.path.join(INCLUDE, "dose.h"))
+    heads.append(os.path.abspath(__file__))            # flags live here
     return max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in heads])
 
 
@@ -45,7 +52,7 @@ def _compile(src: str, verbose: bool, extra) -> str:
     obj = os.path.join(OBJ_DIR, os.path.splitext(os.path.basename(src))[0] + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime(src):
         return obj
-    cmd = [nvcc(), "-c", src, "-o", obj + ".tmp"] + _flags(extra)
+    cmd = [nvcc(), "-c", src, "-o", obj + ".tmp"] + _flags(list(extra) + SOURCE_FLAGS.get(os.path.basename(src), []))
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

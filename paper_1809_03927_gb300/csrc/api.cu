@@ -953,34 +953,66 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         CK(c0, cudaGetLastError());
     }
     if (work) {
-        CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
+        // one job: its descriptor goes in the launch's parameters; several: a
+        // table in device memory
+        // a table whose jobs share their per-step fields (the phases of one
+        // plan and seed) reads those from the launch's parameters too
+        const bool single = tj.size() == 1;
+        const bool shared = !single && jobs_share_step_fields(tj.data(), (int)tj.size());
+        if (!single)
+            CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
         CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
-        auto kern = c0->regs ? k_transport_r64 : k_transport;
+        const void *kern = single ? (c0->regs ? (const void *)k_transport1_r64 : (const void *)k_transport1)
+                         : shared ? (c0->regs ? (const void *)k_transportS_r64 : (const void *)k_transportS)
+                                  : (c0->regs ? (const void *)k_transport_r64 : (const void *)k_transport);
         if (!c0->regs && c0->block > 512)
             return fail(c0, DOSE_EINVAL, "block %d needs the 64-register variant (DOSE_OPT_REGISTERS 1)", c0->block);
-        CK(c0, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemTransportMax + birth_smem(1024))));
+        CK(c0, transport_allow_smem());
         int sms = 0;
         CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->g->device));
-        // stage the job table in shared memory unless that costs resident blocks
-        // or leaves too little L1 (kStageSmemCap)
-        const size_t smem_plain = transport_smem(kMaxStagedJobs + 1) + birth_smem(c0->block);
-        int fit_plain = 0, fit_staged = 0;
-        CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_plain, kern, c0->block, smem_plain));
-        if ((int)tj.size() <= kMaxStagedJobs)
-            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_staged, kern, c0->block,
-                                                                 transport_smem((int)tj.size()) + birth_smem(c0->block)));
-        const int stage = fit_staged > 0 && fit_staged >= fit_plain &&
-                          transport_smem((int)tj.size()) + birth_smem(c0->block) <= kStageSmemCap ? 1 : 0;
-        const size_t smem = stage ? transport_smem((int)tj.size()) + birth_smem(c0->block) : smem_plain;
+        size_t smem;
+        int stage = 0, fit = 0;
+        if (single) {
+            smem = transport_smem(1) + birth_smem(c0->block);
+            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, c0->block, smem));
+        } else {
+            // stage the job table in shared memory unless that costs resident
+            // blocks or leaves too little L1 (kStageSmemCap)
+            const size_t smem_plain = transport_smem(kMaxStagedJobs + 1) + birth_smem(c0->block);
+            int fit_plain = 0, fit_staged = 0;
+            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_plain, kern, c0->block, smem_plain));
+            if ((int)tj.size() <= kMaxStagedJobs)
+                CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_staged, kern, c0->block,
+                                                                     transport_smem((int)tj.size()) + birth_smem(c0->block)));
+            stage = fit_staged > 0 && fit_staged >= fit_plain &&
+                    transport_smem((int)tj.size()) + birth_smem(c0->block) <= kStageSmemCap ? 1 : 0;
+            smem = stage ? transport_smem((int)tj.size()) + birth_smem(c0->block) : smem_plain;
+            fit = stage ? fit_staged : fit_plain;
+        }
         int per_sm = c0->blocks_per_sm;
-        if (per_sm <= 0) per_sm = stage ? fit_staged : fit_plain;
+        if (per_sm <= 0) per_sm = fit;
         if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
         const unsigned long long warps = (unsigned long long)sms * per_sm * (c0->block / 32);
         unsigned chunk = c0->chunk;
         // keep at least ~4 pulls per warp so the tail stays short
         while (chunk > 32 && (unsigned long long)chunk * warps * 4 > work) chunk >>= 1;
-        kern<<<sms * per_sm, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
-                                                    tab.dev, tab.inv_ds, chunk, stage);
+        const unsigned grid = (unsigned)(sms * per_sm);
+        if (single && c0->regs)
+            k_transport1_r64<<<grid, c0->block, smem, st>>>(tj[0], work, c0->d_counter, tab.dev, tab.inv_ds, chunk);
+        else if (single)
+            k_transport1<<<grid, c0->block, smem, st>>>(tj[0], work, c0->d_counter, tab.dev, tab.inv_ds, chunk);
+        else if (shared && c0->regs)
+            k_transportS_r64<<<grid, c0->block, smem, st>>>(tj[0], c0->d_jobs, (int)tj.size(), work, c0->d_counter,
+                                                            tab.dev, tab.inv_ds, chunk, stage);
+        else if (shared)
+            k_transportS<<<grid, c0->block, smem, st>>>(tj[0], c0->d_jobs, (int)tj.size(), work, c0->d_counter,
+                                                        tab.dev, tab.inv_ds, chunk, stage);
+        else if (c0->regs)
+            k_transport_r64<<<grid, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
+                                                           tab.dev, tab.inv_ds, chunk, stage);
+        else
+            k_transport<<<grid, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
+                                                       tab.dev, tab.inv_ds, chunk, stage);
         CK(c0, cudaGetLastError());
     }
     if (!nj.empty()) {
@@ -1031,8 +1063,7 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
     j.shift_mm[0] = j.shift_mm[1] = j.shift_mm[2] = 0.0f;
     c->blocks_per_sm = 0;
     // the occupancy query needs the kernels' dynamic shared-memory limit set
-    CK(c, cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemTransportMax + birth_smem(1024))));
-    CK(c, cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemTransportMax + birth_smem(1024))));
+    CK(c, transport_allow_smem());
     // allocate the phase's histories once; each trial then only transports
     j.flags = DOSE_JOB_CLEAR; j.hist_begin = 0; j.hist_end = 0;
     if ((rc = dose_run_batch(&j, 1, stream))) goto done;
@@ -1040,7 +1071,8 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
         for (int b : blocks) {
             if (!regs && b > 512) continue;
             int fits = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, regs ? k_transport_r64 : k_transport, b,
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, regs ? (const void *)k_transport1_r64
+                                                                          : (const void *)k_transport1, b,
                                                               transport_smem(1) + birth_smem(b)) != cudaSuccess || fits <= 0) {
                 cudaGetLastError();
                 continue;

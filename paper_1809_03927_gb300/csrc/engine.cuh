@@ -80,6 +80,12 @@ struct alignas(16) TJob {
     unsigned long long work_begin;      // offset in the launch's work index
 };
 
+// The fields every step reads that jobs of one context and seed share;
+// they precede the per-job pointers (no padding: all 4-byte scalars and
+// 16-byte vectors).
+constexpr size_t kStepFieldBytes = offsetof(TJob, hu);
+static_assert(kStepFieldBytes == 128, "per-step shared fields: 12 words and five round-key words");
+
 // A transport launch's dynamic shared memory holds the physics tables, the
 // warps' birth buffers (birth_smem(block)) and, when staged, the descriptors
 // and per-job counters (escaped, removed, steps, flags) of up to
@@ -170,15 +176,22 @@ __device__ __forceinline__ float unit_from_bits(unsigned b)   // k in bits [2, 2
 {
     return __int_as_float((b & 0x007FFFFCu) | 0x3F800002u) - 1.0f;
 }
+__device__ __forceinline__ float one_plus_unit(unsigned b)    // 1 + (k + 1/2) 2^-21, k in bits [2, 23)
+{
+    return __int_as_float((b & 0x007FFFFCu) | 0x3F800002u);
+}
 __device__ __forceinline__ U6 uniforms6(uint4 w)
 {
+    // the six subtractions of 1 as three paired additions (exact either way)
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 a = __fadd2_rn(make_float2(one_plus_unit(w.x << 2),                        // bits 0..20
+                                            one_plus_unit(__funnelshift_r(w.x, w.y, 19))), m1);   // 21..41
+    const float2 b = __fadd2_rn(make_float2(one_plus_unit(w.y >> 8),                        // bits 42..62
+                                            one_plus_unit(__funnelshift_r(w.y, w.z, 29))), m1);   // 63..83
+    const float2 c = __fadd2_rn(make_float2(one_plus_unit(__funnelshift_r(w.z, w.w, 18)),   // 84..104
+                                            one_plus_unit(w.w >> 7)), m1);                        // 105..125
     U6 r;
-    r.u[0] = unit_from_bits(w.x << 2);                          // bits 0..20
-    r.u[1] = unit_from_bits(__funnelshift_r(w.x, w.y, 19));     // bits 21..41
-    r.u[2] = unit_from_bits(w.y >> 8);                          // bits 42..62
-    r.u[3] = unit_from_bits(__funnelshift_r(w.y, w.z, 29));     // bits 63..83
-    r.u[4] = unit_from_bits(__funnelshift_r(w.z, w.w, 18));     // bits 84..104
-    r.u[5] = unit_from_bits(w.w >> 7);                          // bits 105..125
+    r.u[0] = a.x; r.u[1] = a.y; r.u[2] = b.x; r.u[3] = b.y; r.u[4] = c.x; r.u[5] = c.y;
     return r;
 }
 

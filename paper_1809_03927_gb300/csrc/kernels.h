@@ -1,6 +1,7 @@
 // Kernel declarations shared between the engine's translation units.
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 #include "dose.h"
 #include "engine.cuh"
@@ -33,6 +34,31 @@ __global__ void k_transport(const TJob *jobs, int n_jobs, unsigned long long tot
 __global__ void k_transport_r64(const TJob *jobs, int n_jobs, unsigned long long total,
                                 unsigned long long *counter, const Tables *gtab, float inv_ds,
                                 unsigned chunk, int stage);
+// One job, passed by value (kernel-parameter memory); the launch gives
+// transport_smem(1) + birth_smem(block) bytes of shared memory.
+__global__ void k_transport1(const __grid_constant__ TJob job, unsigned long long total, unsigned long long *counter,
+                             const Tables *gtab, float inv_ds, unsigned chunk);
+__global__ void k_transport1_r64(const __grid_constant__ TJob job, unsigned long long total, unsigned long long *counter,
+                                 const Tables *gtab, float inv_ds, unsigned chunk);
+// Several jobs that agree on every field before TJob::hu (see
+// jobs_share_step_fields): those fields from `common`, the rest per job.
+__global__ void k_transportS(const __grid_constant__ TJob common, const TJob *jobs, int n_jobs,
+                             unsigned long long total, unsigned long long *counter, const Tables *gtab,
+                             float inv_ds, unsigned chunk, int stage);
+__global__ void k_transportS_r64(const __grid_constant__ TJob common, const TJob *jobs, int n_jobs,
+                                 unsigned long long total, unsigned long long *counter, const Tables *gtab,
+                                 float inv_ds, unsigned chunk, int stage);
+// True when every job agrees with the first on the per-step fields (the
+// first kStepFieldBytes bytes of a TJob).
+inline bool jobs_share_step_fields(const TJob *jobs, int n)
+{
+    for (int j = 1; j < n; ++j)
+        if (std::memcmp(&jobs[j], &jobs[0], kStepFieldBytes) != 0) return false;
+    return true;
+}
+// The six transport kernels accept up to kSmemTransportMax + birth_smem(1024)
+// bytes of dynamic shared memory (set once per device before a launch).
+cudaError_t transport_allow_smem();
 __global__ void k_normalise(const NormJob *jobs);
 __global__ void k_debug_philox(const uint4 *ctr, const uint2 *key, uint4 *out, float *uni, int n);
 __global__ void k_debug_tables(const Tables *tab, float inv_ds, const float *e, int n, float *out);

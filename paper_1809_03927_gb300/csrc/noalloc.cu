@@ -6,10 +6,10 @@
 // given a fixed budget, a real-time service that forbids allocation after
 // start-up).  They pass their own input and output buffers; everything else
 // the kernels need -- the 64-bit tally, the spot table, the allocation
-// arrays, the ledger, the work counter, the launch descriptors and the
+// arrays, the ledger, the work counter, the allocation descriptor and the
 // lookup tables -- lives in one file-scope static __device__ array of fixed
 // size, which every GPU that loads the library keeps until the process
-// exits.
+// exits.  The transport job itself travels in the launch's parameters.
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstdio>
@@ -38,8 +38,7 @@ constexpr size_t kOffWh = align256(kOffRem + kMaxSpots * sizeof(unsigned long lo
 constexpr size_t kOffLedger = align256(kOffWh + kMaxSpots * sizeof(float));
 constexpr size_t kOffCounter = align256(kOffLedger + LED_WORDS * sizeof(unsigned long long));
 constexpr size_t kOffAlloc = align256(kOffCounter + 2 * sizeof(unsigned long long));
-constexpr size_t kOffTJob = align256(kOffAlloc + sizeof(AllocJob));
-constexpr size_t kOffTables = align256(kOffTJob + sizeof(TJob));
+constexpr size_t kOffTables = align256(kOffAlloc + sizeof(AllocJob));
 constexpr size_t kScratchBytes = align256(kOffTables + sizeof(Tables));
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -79,7 +78,7 @@ int setup(int dev, unsigned char **base)
     if (e != cudaSuccess) return fail(DOSE_ECUDA, "cudaGetSymbolAddress", e);
     e = cudaMemcpy(p + kOffTables, &g_host_tab, sizeof(Tables), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(DOSE_ECUDA, "table upload", e);
-    e = cudaFuncSetAttribute(k_transport_r64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemTransportMax + birth_smem(1024)));
+    e = transport_allow_smem();
     if (e != cudaSuccess) return fail(DOSE_ECUDA, "cudaFuncSetAttribute", e);
     g_base[dev] = p;
     *base = p;
@@ -87,7 +86,9 @@ int setup(int dev, unsigned char **base)
 }
 
 // Dose from the tally with the density of each voxel taken from its HU
-// through the calibration table (no density grid is kept).
+// through the calibration table (no density grid is kept): the same FP32
+// density, the same FP64 factor and the same quotient (div64) as
+// k_normalise, so the dose is bit for bit that of dose_run_phase.
 __global__ void k_normalise_hu(const unsigned long long *__restrict__ tally,
                                unsigned long long *__restrict__ ledger, const int16_t *__restrict__ hu,
                                const Tables *__restrict__ tab, float *__restrict__ dose, long long nvox,
@@ -102,7 +103,7 @@ __global__ void k_normalise_hu(const unsigned long long *__restrict__ tally,
         const unsigned long long t = tally[i];
         dep += t;
         const int h = min(max((int)hu[i], kHuMin), kHuMax);
-        dose[i] = (float)((double)t * factor / (double)tab->mat[h - kHuMin].x);
+        dose[i] = t ? (float)div64((double)t * factor, (double)tab->mat[h - kHuMin].x) : 0.0f;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) dep += __shfl_xor_sync(0xffffffffu, dep, o);
@@ -121,7 +122,9 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
     if (!hu || !dose || !spots || !origin_mm || !beam_dir) return fail(DOSE_EINVAL, "NULL argument");
     if (nx <= 0 || ny <= 0 || nz <= 0) return fail(DOSE_EINVAL, "grid dimensions must be positive");
     const long long nvox = (long long)nx * ny * nz;
-    if ((size_t)nvox > kMaxVoxels) return fail(DOSE_EINVAL, "grid exceeds DOSE_NOALLOC_MAX_VOXELS");
+    if ((size_t)nvox > kMaxVoxels) return fail(DOSE_EINVAL, "grid of nx*ny*nz voxels exceeds DOSE_NOALLOC_MAX_VOXELS");
+    if (!std::isfinite(origin_mm[0]) || !std::isfinite(origin_mm[1]) || !std::isfinite(origin_mm[2]))
+        return fail(DOSE_EINVAL, "origin must be 3 finite values");
     if (n_spots <= 0 || (size_t)n_spots > kMaxSpots) return fail(DOSE_EINVAL, "spots must be in 1..DOSE_NOALLOC_MAX_SPOTS");
     if (n_histories == 0) return fail(DOSE_EINVAL, "n_histories is 0");
     if (!(dx_mm > 0 && dy_mm > 0 && dz_mm > 0) || !std::isfinite(dx_mm) || !std::isfinite(dy_mm) || !std::isfinite(dz_mm))
@@ -138,8 +141,11 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
         total += spots[s].protons;
         if (!(spots[s].energy_MeV >= 1.0f && spots[s].energy_MeV <= 250.0f))
             return fail(DOSE_EINVAL, "spot energy outside 1..250 MeV");
-        if (!(spots[s].sigma_mm >= 0.0f) || !std::isfinite(spots[s].x_mm) || !std::isfinite(spots[s].y_mm))
+        if (!(spots[s].sigma_mm >= 0.0f) || !std::isfinite(spots[s].sigma_mm) || !std::isfinite(spots[s].x_mm) ||
+            !std::isfinite(spots[s].y_mm))
             return fail(DOSE_EINVAL, "spot position and sigma must be finite, sigma >= 0");
+        if (spots[s].field != 0)
+            return fail(DOSE_EINVAL, "every spot must belong to field 0 (one static field along beam_dir)");
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -191,6 +197,7 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
     a.ledger = d_ledger;
     a.n_spots = n_spots;
     a.n_hist = n_histories;
+    // the transport job, as dose_run_phase describes it (default options)
     TJob t;
     t.hu = hu; t.matg = nullptr; t.tally = tally; t.ledger = d_ledger;
     t.spot = d_spot; t.wh = a.wh; t.prefix = a.prefix; t.n_spots = n_spots;
@@ -207,31 +214,31 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
     t.stream = 0;
     t.hist_begin = 0; t.work_begin = 0;
     AllocJob *d_a = reinterpret_cast<AllocJob *>(base + kOffAlloc);
-    TJob *d_t = reinterpret_cast<TJob *>(base + kOffTJob);
     e = cudaMemcpyAsync(d_a, &a, sizeof a, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, &t, sizeof t, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);                   // a, t live on this stack
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);                   // a lives on this stack
     if (e != cudaSuccess) return fail(DOSE_ECUDA, "descriptor upload", e);
 
     k_alloc<<<1, 1024, 0, st>>>(d_a);
     int sms = 0, per_sm = 0;
+    const size_t smem = transport_smem(1) + birth_smem(1024);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport_r64, 1024, transport_smem(1) + birth_smem(1024));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport1_r64, 1024, smem);
     if (e != cudaSuccess || per_sm <= 0) return fail(DOSE_ECUDA, "transport launch set-up", e);
-    unsigned chunk = 256;
-    const unsigned long long warps = (unsigned long long)sms * per_sm * 32;
-    while (chunk > 32 && (unsigned long long)chunk * warps * 4 > n_histories) chunk >>= 1;
-    k_transport_r64<<<sms * per_sm, 1024, transport_smem(1) + birth_smem(1024), st>>>(d_t, 1, n_histories, d_counter, d_tab, g_inv_ds, chunk, 1);
+    const unsigned chunk = 32;                    // the default launch shape: 1024 threads, chunk 32
+    k_transport1_r64<<<sms * per_sm, 1024, smem, st>>>(t, n_histories, d_counter, d_tab, g_inv_ds, chunk);
     k_normalise_hu<<<304, 256, 0, st>>>(tally, d_ledger, hu, d_tab, dose, nvox, n_histories,
                                         (double)dx_mm * dy_mm * dz_mm / 1000.0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(DOSE_ECUDA, "launch", e);
-    if (ledger_out) {
-        e = cudaMemcpyAsync(ledger_out, d_ledger, LED_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return fail(DOSE_ECUDA, "ledger read", e);
-    }
+    // wait for the work, then report the ledger and the step-limit flag
+    unsigned long long led[LED_WORDS];
+    e = cudaMemcpyAsync(led, d_ledger, sizeof led, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(DOSE_ECUDA, "ledger read", e);
+    if (ledger_out) std::memcpy(ledger_out, led, sizeof led);
+    if (led[LED_FLAGS] & FLAG_STEPLIMIT)
+        return fail(DOSE_ESTEPLIMIT, "a history reached the step limit (its energy is counted as escaped)");
     return DOSE_OK;
 }
 

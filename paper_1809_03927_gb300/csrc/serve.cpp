@@ -16,6 +16,7 @@
 // on the mix it was served in.
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <deque>
@@ -61,6 +62,11 @@ struct dose_server {
     std::vector<std::pair<int64_t, int>> finished_slot;  // id -> slot
     int64_t next_id = 0;
     uint64_t histories_done = 0, completed = 0, steps = 0;
+    // timing of the steps (seconds): batch and accumulation on the device,
+    // the step on the host; events reused by every step
+    double t_batch = 0.0, t_accum = 0.0, t_wall = 0.0;
+    uint64_t timed_steps = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::string err;
 };
 
@@ -217,6 +223,11 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
         s->active.push_back(a);
     }
     if (s->active.empty()) return DOSE_OK;
+    const auto wall0 = std::chrono::steady_clock::now();
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (!s->ev[0])
+        for (auto &e : s->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return sfail(s, DOSE_ECUDA, "cudaEventCreate failed");
     // every active request gets an equal share of the step's histories
     size_t phase_jobs = 0;
     for (const auto &a : s->active) phase_jobs += a.phases.size();
@@ -249,8 +260,10 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
         a.next = end;
         if (end == a.per_phase) finishing.push_back((int)i);
     }
+    cudaEventRecord(s->ev[0], cs);
     int rc = jobs.empty() ? DOSE_OK : dose_run_batch(jobs.data(), (int)jobs.size(), stream);
     if (rc) return rc;
+    cudaEventRecord(s->ev[1], cs);
     for (int i : finishing) {
         auto &a = s->active[i];
         dose_ctx *v = s->slots[a.slot].view;
@@ -264,8 +277,18 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
             (rc = dose_accumulate_subvoxel(v, s->cfg.ref_phase, s->cfg.nsub, s->cfg.dvf, 1, nullptr, 0, 0, stream)))
             return rc;
     }
-    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    cudaEventRecord(s->ev[2], cs);
+    cudaError_t e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) return sfail(s, DOSE_ECUDA, cudaGetErrorString(e));
+    float ms_batch = 0.0f, ms_accum = 0.0f;
+    if (cudaEventElapsedTime(&ms_batch, s->ev[0], s->ev[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms_accum, s->ev[1], s->ev[2]) == cudaSuccess) {
+        s->t_batch += 1e-3 * ms_batch;
+        s->t_accum += 1e-3 * ms_accum;
+        ++s->timed_steps;
+    }
+    cudaGetLastError();
+    s->t_wall += std::chrono::duration<double>(std::chrono::steady_clock::now() - wall0).count();
     ++s->steps;
     std::vector<dose_server::Active> keep;
     int nc = 0;
@@ -320,9 +343,21 @@ int dose_server_stats(const dose_server *s, uint64_t out[8])
     return DOSE_OK;
 }
 
+int dose_server_timing(const dose_server *s, double out[4])
+{
+    if (!s || !out) return sfail(nullptr, DOSE_EINVAL, "server and out are required");
+    out[0] = s->t_batch;
+    out[1] = s->t_accum;
+    out[2] = s->t_wall;
+    out[3] = (double)s->timed_steps;
+    return DOSE_OK;
+}
+
 void dose_server_destroy(dose_server *s)
 {
     if (!s) return;
+    for (auto &e : s->ev)
+        if (e) cudaEventDestroy(e);
     for (auto &sl : s->slots) dose_destroy(sl.view);
     dose_destroy(s->tmpl);
     delete s;

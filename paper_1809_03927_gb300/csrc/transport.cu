@@ -177,6 +177,41 @@ __device__ __forceinline__ float highland_g(float u)
     return u * t * t;
 }
 
+// Linear interpolation on the uniform energy grid for 0 <= e < kEmax: spot
+// energies are at most 250 MeV (checked where plans enter) and a history's
+// energy only decreases, so the index needs no clamp.  The two values of an
+// entry are interpolated by one paired FMA.
+__device__ __forceinline__ float2 lerp_e_in(const float4 *t, float e)
+{
+    const float x = e * kInvDE;
+    const int i = (int)x;
+    const float f = x - (float)i;
+    const float4 a = t[i];
+    return __ffma2_rn(make_float2(f, f), make_float2(a.z, a.w), make_float2(a.x, a.y));
+}
+
+// Energy at a residual water range 0 <= r < kRmax (below the range of
+// 250 MeV), linear on the sqrt(range) grid.
+__device__ __forceinline__ float energy_at_range_in(const float2 *er, float r, float inv_ds)
+{
+    const float x = fast_sqrt(r) * inv_ds;
+    const int i = (int)x;
+    const float f = x - (float)i;
+    const float2 a = er[i];
+    return fmaf(f, a.y, a.x);
+}
+
+// Box-Muller pair of box_muller(), its two products as one paired multiply.
+__device__ __forceinline__ float2 box_muller2(float ua, float ub)
+{
+    const float t = fmaxf(-2.0f * __logf(ua), 1e-30f);
+    const float r = t * rsqrtf(t);
+    const float a = __fmaf_rn(6.28318530717958647f, ub, -3.14159265358979324f);
+    float s, c;
+    __sincosf(a, &s, &c);
+    return __fmul2_rn(make_float2(-r, -r), make_float2(c, s));
+}
+
 }  // namespace
 
 // Persistent kernel: every warp pulls `chunk` consecutive work items (one
@@ -190,7 +225,18 @@ __device__ __forceinline__ float highland_g(float u)
 // lane of the warp is idle.  Every history is a pure function of (seed,
 // history index, stream), so results do not depend on the launch shape, on
 // the chunking, on the buffering or on the batching.
-__device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, int n_jobs,
+//
+// kMode kTable: the jobs come from the table `jobs` (staged in shared
+// memory when `stage`), P is unused.  kSingle: one job, whose descriptor P
+// is a kernel parameter (constant memory, read as instruction operands; no
+// job search at birth); its counters are added in shared memory.  kShared:
+// a table of jobs that agree on every per-step field before `hu` (grid
+// size, voxel size, SPR scale, physics, step limit, Philox round keys),
+// which come from P; each step reads only its job's grid, tally and stream
+// from the table.
+enum { kTable = 0, kSingle = 1, kShared = 2 };
+template <int kMode>
+__device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, const TJob &P, int n_jobs,
                                                unsigned long long total,
                                                unsigned long long *__restrict__ counter,
                                                const Tables *__restrict__ gtab, float inv_ds,
@@ -201,26 +247,33 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
     const size_t birth_bytes = birth_smem(blockDim.x);
     float *bbuf = reinterpret_cast<float *>(reinterpret_cast<char *>(smem) + kSmemTables);
     TJob *s_jobs = reinterpret_cast<TJob *>(reinterpret_cast<char *>(smem) + kSmemTables + birth_bytes);
-    const bool staged = stage != 0;   // the launch gave transport_smem(n_jobs) + birth_smem(block)
+    const bool table_staged = kMode != kSingle && stage != 0;  // transport_smem(n_jobs) + birth_smem(block)
+    const bool staged = kMode == kSingle || table_staged;     // per-job counters in shared memory
     unsigned long long *s_led = reinterpret_cast<unsigned long long *>(
-        reinterpret_cast<char *>(smem) + kSmemTables + birth_bytes + (staged ? n_jobs : 0) * sizeof(TJob));
+        reinterpret_cast<char *>(smem) + kSmemTables + birth_bytes + (table_staged ? n_jobs : 0) * sizeof(TJob));
+    const int n_led = kMode == kSingle ? 1 : n_jobs;
     {
         const int4 *src = reinterpret_cast<const int4 *>(gtab);
         for (int i = threadIdx.x; i < (int)(kSmemTables / 16); i += blockDim.x) smem[i] = src[i];
-        if (staged) {
+        if (table_staged) {
             const int words = n_jobs * (int)(sizeof(TJob) / 4);
             const int *js = reinterpret_cast<const int *>(jobs);
             int *jd = reinterpret_cast<int *>(s_jobs);
             for (int i = threadIdx.x; i < words; i += blockDim.x) jd[i] = js[i];
-            for (int i = threadIdx.x; i < n_jobs * 4; i += blockDim.x) s_led[i] = 0ull;
         }
+        if (staged)
+            for (int i = threadIdx.x; i < n_led * 4; i += blockDim.x) s_led[i] = 0ull;
     }
     __syncthreads();
     // re, hs, er from shared memory; mat (beyond the staged part) from global
     const Tables &T = *reinterpret_cast<const Tables *>(smem);
     const float2 *__restrict__ mat = gtab->mat;
-    // job descriptors: shared memory when staged, else global (generic loads)
-    const TJob *jt = staged ? s_jobs : jobs;
+    // job descriptors: the parameter, shared memory when staged, else global
+    const TJob *jt = table_staged ? s_jobs : jobs;
+    // job_of: the per-step fields shared by the launch's jobs (and everything
+    // a birth reads); own_of: the job's grid, tally, stream and ledger
+    auto job_of = [&](int j) -> const TJob & { return kMode == kTable ? jt[j] : P; };
+    auto own_of = [&](int j) -> const TJob & { return kMode == kSingle ? P : jt[j]; };
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     // this warp's birth buffer: word f of slot k is wb[f * plane + k] (one
@@ -237,9 +290,10 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         else atomicAdd(jobs[j].ledger + (which == 0 ? LED_ESC : which == 1 ? LED_REM : LED_STEPS), v);
     };
 
-    // per-lane history state
+    // per-lane history state; wq is the history weight times the tally
+    // quantum 2^24 (an exact scaling), so a deposit e is e * wq units
     bool alive = false;
-    float px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0, E = 0, eta = 0, uth = 0, gth = 0, wh = 0;
+    float px = 0, py = 0, pz = 0, ux = 0, uy = 0, uz = 0, E = 0, eta = 0, uth = 0, gth = 0, wq = 0;
     int ix = 0, iy = 0, iz = 0;
     unsigned step = 0;
     unsigned long long h = 0;
@@ -267,17 +321,20 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                 }
                 const unsigned long long avail = pool_end - pool_next;
                 bool ok = false;
-                float bpx = 0, bpy = 0, bpz = 0, bux = 0, buy = 0, buz = 0, bE = 0, beta = 0, bwh = 0;
+                float bpx = 0, bpy = 0, bpz = 0, bux = 0, buy = 0, buz = 0, bE = 0, beta = 0, bwq = 0;
                 int bix = 0, biy = 0, biz = 0, bjob = 0;
                 unsigned long long bh = 0;
                 if (lane < avail) {
                     const unsigned long long w = pool_next + lane;
-                    int lo = 0, hi = n_jobs;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (jt[mid].work_begin <= w) lo = mid; else hi = mid;
+                    int lo = 0;
+                    if (kMode != kSingle) {
+                        int hi = n_jobs;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (jt[mid].work_begin <= w) lo = mid; else hi = mid;
+                        }
                     }
-                    const TJob &J = jt[lo];
+                    const TJob &J = own_of(lo);
                     bjob = lo;
                     bh = J.hist_begin + (w - J.work_begin);
                     const int S = J.n_spots;
@@ -289,7 +346,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                             if (prefix[m] <= bh) a = m; else b = m;
                         }
                         const float4 sp = J.spot[a];
-                        bwh = J.wh[a];
+                        bwq = J.wh[a] * kQuantum;
                         bE = sp.z;
                         const U6 u = uniforms6(philox4x32_10(
                             make_uint4(0u, (unsigned)bh, (unsigned)(bh >> 32), J.stream), J.key0, J.key1));
@@ -323,7 +380,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                         // guard the floor against rounding at the far faces
                         bix = min(max(bix, 0), nx - 1); biy = min(max(biy, 0), ny - 1); biz = min(max(biz, 0), nz - 1);
                         if (inside) ok = true;
-                        else led_add(bjob, 0, to_units(bE * bwh));
+                        else led_add(bjob, 0, __float2ull_rn(bE * bwq));
                     }
                 }
                 pool_next += min(32ull, avail);
@@ -332,7 +389,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                     float *e = wb + __popc(okm & lt_mask);
                     e[0 * plane] = bpx; e[1 * plane] = bpy; e[2 * plane] = bpz;
                     e[3 * plane] = bux; e[4 * plane] = buy; e[5 * plane] = buz;
-                    e[6 * plane] = bE; e[7 * plane] = beta; e[8 * plane] = bwh;
+                    e[6 * plane] = bE; e[7 * plane] = beta; e[8 * plane] = bwq;
                     e[9 * plane] = __int_as_float(bix); e[10 * plane] = __int_as_float(biy);
                     e[11 * plane] = __int_as_float(biz); e[12 * plane] = __int_as_float(bjob);
                     e[13 * plane] = __uint_as_float((unsigned)bh); e[14 * plane] = __uint_as_float((unsigned)(bh >> 32));
@@ -347,9 +404,10 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                 const float *e = wb + (n_buf - 1 - rank);
                 px = e[0 * plane]; py = e[1 * plane]; pz = e[2 * plane];
                 ux = e[3 * plane]; uy = e[4 * plane]; uz = e[5 * plane];
-                E = e[6 * plane]; eta = e[7 * plane]; wh = e[8 * plane];
+                E = e[6 * plane]; eta = e[7 * plane]; wq = e[8 * plane];
                 ix = __float_as_int(e[9 * plane]); iy = __float_as_int(e[10 * plane]);
-                iz = __float_as_int(e[11 * plane]); job = __float_as_int(e[12 * plane]);
+                iz = __float_as_int(e[11 * plane]);
+                if (kMode != kSingle) job = __float_as_int(e[12 * plane]);
                 h = (unsigned long long)__float_as_uint(e[13 * plane]) |
                     ((unsigned long long)__float_as_uint(e[14 * plane]) << 32);
                 uth = 0.0f; gth = 0.0f; step = 0;
@@ -363,9 +421,10 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         if (!alive) continue;
 
         // ---------------- one condensed-history step
-        const TJob &J = jt[job];
+        const TJob &J = job_of(job);
+        const TJob &Jo = own_of(job);
         if (step >= J.max_steps) {
-            led_add(job, 0, to_units(E * wh));
+            led_add(job, 0, __float2ull_rn(E * wq));
             led_add(job, 2, step);
             if (staged) atomicOr(s_led + 4 * job + 3, (unsigned long long)FLAG_STEPLIMIT);
             else atomicOr(jobs[job].ledger + LED_FLAGS, (unsigned long long)FLAG_STEPLIMIT);
@@ -377,52 +436,56 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         float2 m;
         // the grid is read at random voxels (few L1 hits): through L2 only,
         // so L1 keeps the job descriptors and the HU table
-        if (J.matg) {
-            m = __ldcg(J.matg + vox);
+        if (Jo.matg) {
+            m = __ldcg(Jo.matg + vox);
         } else {
-            const int hv = min(max((int)__ldcg(J.hu + vox), kHuMin), kHuMax);
+            const int hv = min(max((int)__ldcg(Jo.hu + vox), kHuMin), kHuMax);
             m = __ldg(mat + (hv - kHuMin));
         }
         const float rho = m.x;
         const float spr = m.y * J.spr_scale;
         const float inv_spr = __fdividef(1.0f, spr);
-        const float2 re0 = lerp_e(T.re, E);
+        const float2 re0 = lerp_e_in(T.re, E);
         const float R0 = re0.x;
         ++step;
         // this step's random numbers: independent of the geometry below, so
         // the generator's rounds can interleave with the table lookups
         const U6 u = uniforms6(philox_rk(
-            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), J.stream), J.rk));
-        if (R0 * inv_spr <= kSmin) {                   // residual range below s_min
-            const unsigned long long eu = to_units(E * wh);
-            atomicAdd(J.tally + vox, eu);
+            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), Jo.stream), J.rk));
+        const float q = R0 * inv_spr;                  // residual range in the medium
+        if (q <= kSmin) {                              // residual range below s_min
+            atomicAdd(Jo.tally + vox, __float2ull_rn(E * wq));
             led_add(job, 2, step);
             alive = false;
             continue;
         }
         const float dx = J.dx, dy = J.dy, dz = J.dz;
-        // distance to the faces of the current voxel (ties: lowest axis)
+        // distance to the faces of the current voxel (ties: lowest axis):
+        // (face - p) / u towards the face the direction points at, none
+        // along an axis the direction does not move on
         const float inf = __int_as_float(0x7f800000);
-        float tx = ux > 0.0f ? ((ix + 1) * dx - px) * __fdividef(1.0f, ux)
-                 : (ux < 0.0f ? (ix * dx - px) * __fdividef(1.0f, ux) : inf);
-        float ty = uy > 0.0f ? ((iy + 1) * dy - py) * __fdividef(1.0f, uy)
-                 : (uy < 0.0f ? (iy * dy - py) * __fdividef(1.0f, uy) : inf);
-        float tz = uz > 0.0f ? ((iz + 1) * dz - pz) * __fdividef(1.0f, uz)
-                 : (uz < 0.0f ? (iz * dz - pz) * __fdividef(1.0f, uz) : inf);
+        const float bx = (float)(ux > 0.0f ? ix + 1 : ix), by = (float)(uy > 0.0f ? iy + 1 : iy);
+        const float bz = (float)(uz > 0.0f ? iz + 1 : iz);
+        const float2 dxy = __fmul2_rn(__ffma2_rn(make_float2(bx, by), make_float2(dx, dy), make_float2(-px, -py)),
+                                      make_float2(__fdividef(1.0f, ux), __fdividef(1.0f, uy)));
+        float tx = ux != 0.0f ? dxy.x : inf;
+        float ty = uy != 0.0f ? dxy.y : inf;
+        float tz = uz != 0.0f ? __fmaf_rn(bz, dz, -pz) * __fdividef(1.0f, uz) : inf;
         tx = fmaxf(tx, 0.0f); ty = fmaxf(ty, 0.0f); tz = fmaxf(tz, 0.0f);
         int across = 0;
         float dbound = tx;
         if (ty < dbound) { dbound = ty; across = 1; }
         if (tz < dbound) { dbound = tz; across = 2; }
         // the step ends at the voxel boundary or after the physics length
-        float s = fmaxf(kFstep * R0 * inv_spr, kSmin);
+        // (kFstep R0 / SPR: the factor 1/4 scales exactly)
+        float s = fmaxf(kFstep * q, kSmin);
         bool geom = false;
         if (dbound <= s) { s = dbound; geom = true; }
 
         float sw = s * spr;                              // water-equivalent mm
-        float E1c = energy_at_range(T.er, R0 - sw, inv_ds);
+        float E1c = energy_at_range_in(T.er, R0 - sw, inv_ds);
         float Emean = 0.5f * (E + E1c);
-        float2 hs = lerp_e(T.hs, Emean);
+        float2 hs = lerp_e_in(T.hs, Emean);
         const unsigned physics = J.physics;
         bool nuclear = false;
         if (physics & 4u) {
@@ -432,7 +495,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
                 sw = __fdividef(eta, hs.y);
                 s = sw * inv_spr;
                 geom = false;
-                E1c = energy_at_range(T.er, R0 - sw, inv_ds);
+                E1c = energy_at_range_in(T.er, R0 - sw, inv_ds);
             } else {
                 eta -= tau;
             }
@@ -451,33 +514,32 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
             float local = E;                              // stop: dE + E1
             if (nuclear) {
                 local = dE + kFloc * E1;
-                led_add(job, 1, to_units((E1 - kFloc * E1) * wh));
+                led_add(job, 1, __float2ull_rn((E1 - kFloc * E1) * wq));
             }
-            const unsigned long long eu = to_units(local * wh);
-            atomicAdd(J.tally + vox, eu);
+            atomicAdd(Jo.tally + vox, __float2ull_rn(local * wq));
             led_add(job, 2, step);
             alive = false;
             continue;
         }
-        {
-            const unsigned long long eu = to_units(dE * wh);
-            atomicAdd(J.tally + vox, eu);
-        }
+        atomicAdd(Jo.tally + vox, __float2ull_rn(dE * wq));
 
-        // multiple Coulomb scattering over the step (cumulative Highland)
-        float y1 = 0.0f, y2 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+        // multiple Coulomb scattering over the step (cumulative Highland);
+        // the two transverse planes as float2 pairs (y1, y2) and (t1, t2)
+        float2 y = make_float2(0.0f, 0.0f), t = make_float2(0.0f, 0.0f);
         if (physics & 2u) {
             const float u1 = fmaf(s * rho, kInvX0, uth);
             const float g1 = highland_g(u1);
             const float th2 = highland_coeff(hs.x) * (g1 - gth);
             uth = u1; gth = g1;
             const float th0 = fast_sqrt(th2);
-            const float2 zu = box_muller(u.u[2], u.u[3]);
-            const float2 zv = box_muller(u.u[4], u.u[5]);
-            y1 = s * th0 * fmaf(zu.x, kInvSqrt12, 0.5f * zu.y);
-            t1 = th0 * zu.y;
-            y2 = s * th0 * fmaf(zv.x, kInvSqrt12, 0.5f * zv.y);
-            t2 = th0 * zv.y;
+            const float2 zu = box_muller2(u.u[2], u.u[3]);
+            const float2 zv = box_muller2(u.u[4], u.u[5]);
+            const float st = s * th0;
+            // y = s th0 (z1 / sqrt(12) + z2 / 2), t = th0 z2, per plane
+            const float2 g = __ffma2_rn(make_float2(zu.x, zv.x), make_float2(kInvSqrt12, kInvSqrt12),
+                                        __fmul2_rn(make_float2(0.5f, 0.5f), make_float2(zu.y, zv.y)));
+            y = __fmul2_rn(make_float2(st, st), g);
+            t = __fmul2_rn(make_float2(th0, th0), make_float2(zu.y, zv.y));
         }
         // transverse frame (Duff et al., JCGT 2017)
         const float sgn = uz >= 0.0f ? 1.0f : -1.0f;
@@ -486,14 +548,24 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         const float e1x = fmaf(sgn * ux * ux, fa, 1.0f), e1y = sgn * fb, e1z = -sgn * ux;
         const float e2x = fb, e2y = fmaf(uy * uy, fa, sgn), e2z = -uy;
         const float ux0 = ux, uy0 = uy, uz0 = uz;
-        px = fmaf(s, ux, fmaf(y1, e1x, fmaf(y2, e2x, px)));
-        py = fmaf(s, uy, fmaf(y1, e1y, fmaf(y2, e2y, py)));
-        pz = fmaf(s, uz, fmaf(y1, e1z, fmaf(y2, e2z, pz)));
-        ux = fmaf(t1, e1x, fmaf(t2, e2x, ux));
-        uy = fmaf(t1, e1y, fmaf(t2, e2y, uy));
-        uz = fmaf(t1, e1z, fmaf(t2, e2z, uz));
+        {
+            const float2 pxy = __ffma2_rn(make_float2(s, s), make_float2(ux, uy),
+                                          __ffma2_rn(make_float2(y.x, y.x), make_float2(e1x, e1y),
+                                                     __ffma2_rn(make_float2(y.y, y.y), make_float2(e2x, e2y),
+                                                                make_float2(px, py))));
+            pz = fmaf(s, uz, fmaf(y.x, e1z, fmaf(y.y, e2z, pz)));
+            const float2 uxy = __ffma2_rn(make_float2(t.x, t.x), make_float2(e1x, e1y),
+                                          __ffma2_rn(make_float2(t.y, t.y), make_float2(e2x, e2y),
+                                                     make_float2(ux, uy)));
+            uz = fmaf(t.x, e1z, fmaf(t.y, e2z, uz));
+            px = pxy.x; py = pxy.y; ux = uxy.x; uy = uxy.y;
+        }
         const float nrm = rsqrtf(ux * ux + uy * uy + uz * uz);
-        ux *= nrm; uy *= nrm; uz *= nrm;
+        {
+            const float2 uxy = __fmul2_rn(make_float2(ux, uy), make_float2(nrm, nrm));
+            ux = uxy.x; uy = uxy.y;
+            uz *= nrm;
+        }
         E = E1;
 
         // voxel update: the crossed axis steps by one and its coordinate is
@@ -502,32 +574,35 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
         // floor(p / d) once the lateral displacement carried it outside
         if (geom && across == 0) {
             if (ux0 > 0.0f) { ix += 1; px = ix * dx; } else { px = ix * dx; ix -= 1; }
-        } else if (!(px >= ix * dx && px <= (ix + 1) * dx)) {
-            ix = (int)floorf(px * J.idx);
+        } else {
+            const float2 ext = __fmul2_rn(make_float2((float)ix, (float)(ix + 1)), make_float2(dx, dx));
+            if (!(px >= ext.x && px <= ext.y)) ix = (int)floorf(px * J.idx);
         }
         if (geom && across == 1) {
             if (uy0 > 0.0f) { iy += 1; py = iy * dy; } else { py = iy * dy; iy -= 1; }
-        } else if (!(py >= iy * dy && py <= (iy + 1) * dy)) {
-            iy = (int)floorf(py * J.idy);
+        } else {
+            const float2 ext = __fmul2_rn(make_float2((float)iy, (float)(iy + 1)), make_float2(dy, dy));
+            if (!(py >= ext.x && py <= ext.y)) iy = (int)floorf(py * J.idy);
         }
         if (geom && across == 2) {
             if (uz0 > 0.0f) { iz += 1; pz = iz * dz; } else { pz = iz * dz; iz -= 1; }
-        } else if (!(pz >= iz * dz && pz <= (iz + 1) * dz)) {
-            iz = (int)floorf(pz * J.idz);
+        } else {
+            const float2 ext = __fmul2_rn(make_float2((float)iz, (float)(iz + 1)), make_float2(dz, dz));
+            if (!(pz >= ext.x && pz <= ext.y)) iz = (int)floorf(pz * J.idz);
         }
         if ((unsigned)ix >= (unsigned)nx || (unsigned)iy >= (unsigned)ny || (unsigned)iz >= (unsigned)J.nz) {
-            led_add(job, 0, to_units(E * wh));
+            led_add(job, 0, __float2ull_rn(E * wq));
             led_add(job, 2, step);
             alive = false;
         }
     }
     if (staged) {
         __syncthreads();
-        for (int i = threadIdx.x; i < n_jobs * 4; i += blockDim.x) {
+        for (int i = threadIdx.x; i < n_led * 4; i += blockDim.x) {
             const unsigned long long v = s_led[i];
             if (!v) continue;
             const int j = i >> 2, which = i & 3;
-            unsigned long long *led = jobs[j].ledger;
+            unsigned long long *led = own_of(j).ledger;
             if (which == 3) atomicOr(led + LED_FLAGS, v);
             else atomicAdd(led + (which == 0 ? LED_ESC : which == 1 ? LED_REM : LED_STEPS), v);
         }
@@ -536,13 +611,14 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, in
 
 // Two register budgets of the same kernel: up to 128 registers per thread
 // (blocks of at most 512 threads) or 64 (blocks up to 1024 threads, more
-// resident warps, some spilling).  The autotuner picks; results are equal.
+// resident warps).  The autotuner picks; results are equal.  k_transport1*
+// run one job given as a parameter; k_transport* a table of jobs.
 __global__ void __launch_bounds__(512, 1)
 k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
             unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
             unsigned chunk, int stage)
 {
-    transport_body(jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+    transport_body<kTable>(jobs, *jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
 }
 
 __global__ void __launch_bounds__(1024, 1)
@@ -550,7 +626,50 @@ k_transport_r64(const TJob *__restrict__ jobs, int n_jobs, unsigned long long to
                 unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab,
                 float inv_ds, unsigned chunk, int stage)
 {
-    transport_body(jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+    transport_body<kTable>(jobs, *jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+}
+
+__global__ void __launch_bounds__(512, 1)
+k_transport1(const __grid_constant__ TJob job, unsigned long long total, unsigned long long *__restrict__ counter,
+             const Tables *__restrict__ gtab, float inv_ds, unsigned chunk)
+{
+    transport_body<kSingle>(nullptr, job, 1, total, counter, gtab, inv_ds, chunk, 0);
+}
+
+__global__ void __launch_bounds__(1024, 1)
+k_transport1_r64(const __grid_constant__ TJob job, unsigned long long total,
+                 unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
+                 unsigned chunk)
+{
+    transport_body<kSingle>(nullptr, job, 1, total, counter, gtab, inv_ds, chunk, 0);
+}
+
+__global__ void __launch_bounds__(512, 1)
+k_transportS(const __grid_constant__ TJob common, const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
+             unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
+             unsigned chunk, int stage)
+{
+    transport_body<kShared>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+}
+
+__global__ void __launch_bounds__(1024, 1)
+k_transportS_r64(const __grid_constant__ TJob common, const TJob *__restrict__ jobs, int n_jobs,
+                 unsigned long long total, unsigned long long *__restrict__ counter,
+                 const Tables *__restrict__ gtab, float inv_ds, unsigned chunk, int stage)
+{
+    transport_body<kShared>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+}
+
+cudaError_t transport_allow_smem()
+{
+    const int bytes = (int)(kSmemTransportMax + birth_smem(1024));
+    const void *k[6] = {(const void *)k_transport, (const void *)k_transport_r64, (const void *)k_transport1,
+                        (const void *)k_transport1_r64, (const void *)k_transportS, (const void *)k_transportS_r64};
+    for (const void *f : k) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------- self-tests

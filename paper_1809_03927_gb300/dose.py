@@ -122,6 +122,8 @@ def _load():
         "dose_add_spots_trials": ([P, I, P, I64, P, P, U64, P], I),
         "dose_set_field_beam": ([P, I, P], I),
         "dose_get_option": ([P, I, C.POINTER(I64)], I),
+        "dose_measure_peaks": ([P, P], I),
+        "dose_server_timing": ([P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -330,21 +332,43 @@ def dose_autotune(ctx, phase, n_histories, sample_histories, seed, stream=None):
     return tuple(int(v) for v in best)
 
 
+def dose_measure_peaks(stream=None):
+    """Measured peaks of the current device: mixed FP32/INT32 issue rate
+    and FFMA rate (thread instructions/s), 64-bit atomic additions/s to an
+    L2-resident array, SM count."""
+    out = (C.c_double * 4)()
+    _check(_lib.dose_measure_peaks(out, _stream(stream)), None)
+    return dict(issue_mixed=out[0], issue_ffma=out[1], atomic_u64=out[2], sms=int(out[3]))
+
+
 def dose_run_phase_noalloc(hu, nx, ny, nz, dx_mm, dy_mm, dz_mm, origin_mm, beam_dir, spots,
-                           n_histories, seed, dose, stream=None):
+                           n_histories, seed, dose, stream=None, ledger=True):
     """Allocation-free dose of a static plan: ``hu`` (int16) and ``dose``
-    (float32) are device tensors, ``spots`` a ``dose_spot`` array; returns
-    the 8-word ledger (the call waits for the stream)."""
-    hp, hdev = _ptr(hu)
-    dp, ddev = _ptr(dose)
-    if not (hdev and ddev):
-        raise ValueError("hu and dose must be device tensors")
-    led = (C.c_uint64 * 8)()
+    (float32) are contiguous device tensors of at least nx*ny*nz elements on
+    the current device, ``spots`` a ``dose_spot`` array; returns the 8-word
+    ledger (None with ``ledger=False``, which passes no ledger buffer).  The
+    call returns once the dose is written.  The C call cannot check raw
+    pointers, so the types, sizes and device are checked here."""
+    import torch
+    nvox = int(nx) * int(ny) * int(nz)
+    for name, t, dt in (("hu", hu, torch.int16), ("dose", dose, torch.float32)):
+        if not (_is_torch(t) and t.is_cuda):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if t.numel() < nvox:
+            raise ValueError(f"{name} has {t.numel()} elements, needs nx*ny*nz = {nvox}")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
+                             f"cuda:{torch.cuda.current_device()}")
+    hp, _ = _ptr(hu)
+    dp, _ = _ptr(dose)
+    led = (C.c_uint64 * 8)() if ledger else None
     _check(_lib.dose_run_phase_noalloc(hp, int(nx), int(ny), int(nz), float(dx_mm), float(dy_mm),
                                        float(dz_mm), _f3(origin_mm), _f3(beam_dir),
                                        C.cast(spots, C.c_void_p), len(spots), int(n_histories),
                                        int(seed), dp, led, _stream(stream)), None)
-    return np.array(led[:], dtype=np.uint64)
+    return np.array(led[:], dtype=np.uint64) if ledger else None
 
 
 def dose_server_create(base, memory_budget_bytes, step_histories, spots, delivery=None,
@@ -401,6 +425,15 @@ def dose_server_stats(server):
     _check(_lib.dose_server_stats(server, out), None)
     return dict(zip(("queued", "active", "slots", "completed", "histories", "steps", "slot_bytes",
                      "unreleased"), [int(v) for v in out]))
+
+
+def dose_server_timing(server):
+    """Seconds summed over the server's steps: device time of the transport
+    batches and of the finishing accumulations, host wall time of the
+    steps, and the number of timed steps."""
+    out = (C.c_double * 4)()
+    _check(_lib.dose_server_timing(server, out), None)
+    return dict(batch_s=out[0], accumulate_s=out[1], step_wall_s=out[2], steps=int(out[3]))
 
 
 def dose_server_destroy(server):

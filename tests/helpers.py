@@ -71,6 +71,34 @@ def gpu_batches(D, phantom, plan, n_hist, seed, n_batches, phase=0, physics=7, *
     return doses.mean(axis=0), doses.std(axis=0, ddof=1) / np.sqrt(n_batches)
 
 
+def gpu_batches_on_device(D, phantom, plan, n_hist, seed, n_batches, phase=0):
+    """As gpu_batches, with the batch doses summed on the device (a large
+    grid's 100 doses are not copied to the host): mean dose and its
+    standard error, float64 on the host."""
+    import torch
+    ctx = make_ctx(D, phantom)
+    shape = phantom.hu.shape[-3:]
+    try:
+        dl = None if phase == 0 else D.delivery_struct(whole_plan_on(phase, phantom.n_phases))
+        D.dose_add_spots(ctx, D.spots_array(plan), dl)
+        nb = n_hist // n_batches
+        d = torch.empty(shape, dtype=torch.float32, device="cuda")
+        s1 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        s2 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        for b in range(n_batches):
+            D.dose_run_phase(ctx, phase, nb, seed + 7919 * b)
+            D.dose_read(ctx, D.DOSE_PHASE_DOSE, phase, d)
+            x = d.double()
+            s1 += x
+            s2 += x * x
+        torch.cuda.synchronize()
+    finally:
+        D.dose_destroy(ctx)
+    mean = (s1 / n_batches).cpu().numpy()
+    var = np.maximum((s2 / n_batches).cpu().numpy() - mean * mean, 0.0) * n_batches / (n_batches - 1)
+    return mean, np.sqrt(var / n_batches)
+
+
 def body_mask(orc, phantom, phase=None, rho_min=0.1):
     """Voxels inside the patient (density above air); dose outside the
     external contour is not evaluated (Sec. 2.A: the MC is limited to it)."""
@@ -127,15 +155,19 @@ def _trilinear(a, k, j, i):
     return out
 
 
-def gamma_pass(ref, evl, spacing, dd=0.01, dta=1.0, threshold=0.1, step=0.25):
+def gamma_pass(ref, evl, spacing, dd=0.01, dta=1.0, threshold=0.1, step=0.25, dmax=None, select=None):
     """Global gamma index (Low, Harms, Mutic, Purdy, Med. Phys. 25, 1998):
     for each reference voxel with dose >= threshold * max, gamma^2 is the
     minimum over evaluated points r' within dta of |r'-r|^2/dta^2 +
     (D_e(r') - D_r(r))^2/(dd * max)^2, the evaluated dose interpolated
     trilinearly between voxel centres on a `step`-mm sub-grid.  Returns the
-    fraction of voxels with gamma <= 1."""
-    dmax = float(ref.max())
-    idx = np.argwhere(ref >= threshold * dmax)
+    fraction of voxels with gamma <= 1.  ``dmax`` overrides the maximum
+    (global normalisation); ``select`` restricts the reference voxels."""
+    dmax = float(ref.max()) if dmax is None else float(dmax)
+    sel = ref >= threshold * dmax
+    if select is not None:
+        sel &= select
+    idx = np.argwhere(sel)
     dr = ref[tuple(idx.T)]
     r = np.arange(-dta, dta + 1e-9, step)
     best = np.full(len(idx), np.inf)

@@ -96,9 +96,18 @@ def test_decode_parity(gpu, orc, name):
     finally:
         gpu.dose_destroy(ctx)
     want, inside, amb = orc.dvf_decode(g, delta, N, D, ORIGIN, return_ambiguous=True)
-    sure = amb == 0
-    np.testing.assert_array_equal(gmask[sure], inside[sure])
-    assert inside.sum() > 500 and amb.sum() <= 0.01 * amb.size, int(amb.sum())
+    if name == "oblique":
+        # cosines of 30 degrees: the hull test is rounded on both sides, and
+        # only voxels within the tie tolerance of a hull face may differ
+        sure = amb == 0
+        np.testing.assert_array_equal(gmask[sure], inside[sure])
+        assert amb.sum() <= 0.01 * amb.size, int(amb.sum())
+    else:
+        # axis-aligned grids with binary-exact start, spacing and CT centres:
+        # the hull test is exact on both sides, faces included (these grids
+        # have a hull face through a row of CT voxel centres)
+        np.testing.assert_array_equal(gmask, inside)
+    assert inside.sum() > 500
     assert np.all(got[:, gmask == 0] == 0.0)
     both = (gmask == 1) & (inside == 1)
     tol = 1e-4 + 1e-5 * np.abs(want)

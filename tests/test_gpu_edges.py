@@ -144,3 +144,32 @@ def test_one_spot_delivery(gpu, orc):
     opp, _, _ = orc.timeline(plan, dlv)
     np.testing.assert_array_equal(pp, opp)
     assert np.count_nonzero(pp) == 4 and int(pp.sum()) == 7_777_777
+
+
+def test_host_wait_gives_up_while_the_kernel_finishes(gpu):
+    """Failure detection on the host (no GPU fault): with a 1 ms wait limit,
+    reading a 1e8-history run's tally into pinned host memory returns
+    DOSE_ETIMEOUT while the transport is still running; the work itself is
+    untouched, so after waiting normally the tally is the untimed run's, bit
+    for bit, and the context keeps working."""
+    D = gpu
+    ph = W.slab_phantom(n=64)
+    pl = W.slab_plan(n_layers=4, nx=3, ny=2)
+    n, seed = 100_000_000, 31
+    ref = H.gpu_run(D, ph, pl, n, seed)["tally"]
+    ctx = H.make_ctx(D, ph)
+    try:
+        D.dose_add_spots(ctx, D.spots_array(pl), None)
+        D.dose_set_option(ctx, D.DOSE_OPT_TIMEOUT_MS, 1)
+        out = torch.zeros(ph.hu.shape, dtype=torch.int64).pin_memory()
+        D.dose_run_phase(ctx, 0, n, seed)
+        with pytest.raises(D.DoseError) as e:
+            D.dose_read(ctx, D.DOSE_TALLY_I64, 0, out)
+        assert e.value.code == D.DOSE_ETIMEOUT and "did not finish" in str(e.value)
+        torch.cuda.synchronize()                      # the copy the read enqueued lands here
+        np.testing.assert_array_equal(out.numpy().view(np.uint64), ref)
+        D.dose_set_option(ctx, D.DOSE_OPT_TIMEOUT_MS, 600_000)
+        again = D.dose_read(ctx, D.DOSE_TALLY_I64, 0, np.zeros(ph.hu.shape, np.uint64))
+        np.testing.assert_array_equal(again, ref)
+    finally:
+        D.dose_destroy(ctx)
