@@ -444,8 +444,13 @@ def _bench_trials(D, torch, stream, n_per_phase, n_trials=25, seed=SEED):
             return len(jobs), e0.elapsed_time(e1) / 1e3
 
         D.dose_add_spots_trials(views, spots, D.delivery_struct(mean), D.spread_struct(spread), 0, stream)
-        pp0 = D.dose_read(views[0], D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
-        tune = D.dose_autotune(views[0], int(np.argmax(pp0)), n_per_phase, min(n_per_phase, 2_000_000), seed, stream)
+        # launch shape of the study's batch, tuned on a 2e7-history sample of it
+        tjobs = []
+        for k, v in enumerate(views):
+            pp = D.dose_read(v, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64))
+            tjobs += [dict(ctx=v, phase=p, n_histories=n_per_phase, seed=seed + k)
+                      for p in range(ph.n_phases) if pp[p].sum()]
+        tune = D.dose_autotune_batch(D.make_jobs(tjobs), 20_000_000, stream)
         study()                                    # warm-up (and first allocation of the views)
         t0 = time.perf_counter()
         n_jobs, mc_s = study()
@@ -498,11 +503,9 @@ def _bench_ragged(D, torch, stream, n_random=62, seed=4, reps=2):
                     specs.append(dict(ctx=c, phase=p, n_histories=10_000_000, seed=77 + p))
         total = sum(sp["n_histories"] for sp in specs)
         jobs = D.make_jobs(specs)
-        big = max(specs, key=lambda sp: sp["n_histories"])
-        tune = D.dose_autotune(big["ctx"], big["phase"], big["n_histories"], 2_000_000, 1, stream)
-        for c in ctxs:
-            for opt, v in ((D.DOSE_OPT_REGISTERS, tune[0]), (D.DOSE_OPT_BLOCK, tune[1]), (D.DOSE_OPT_CHUNK, tune[2])):
-                D.dose_set_option(c, opt, v)
+        # the batch's launch shape from the batch autotuner (a 2e7-history
+        # sample spread over the jobs), set on every context
+        tune = D.dose_autotune_batch(jobs, 20_000_000, stream)
         D.dose_run_batch(jobs, stream)                    # warm-up
         torch.cuda.synchronize()
         tb = []
@@ -513,6 +516,15 @@ def _bench_ragged(D, torch, stream, n_random=62, seed=4, reps=2):
             e1.record(stream)
             torch.cuda.synchronize()
             tb.append(e0.elapsed_time(e1) / 1e3)
+        # one job per launch: the single-job shape, tuned on the largest job
+        big = max(specs, key=lambda sp: sp["n_histories"])
+        tune1 = D.dose_autotune(big["ctx"], big["phase"], big["n_histories"], 2_000_000, 1, stream)
+        for c in ctxs:
+            for opt, v in ((D.DOSE_OPT_REGISTERS, tune1[0]), (D.DOSE_OPT_BLOCK, tune1[1]), (D.DOSE_OPT_CHUNK, tune1[2])):
+                D.dose_set_option(c, opt, v)
+        for sp in specs:                                  # warm-up
+            D.dose_run_phase(sp["ctx"], sp["phase"], sp["n_histories"], sp["seed"], 1.0, None, stream)
+        torch.cuda.synchronize()
         tp = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -528,7 +540,8 @@ def _bench_ragged(D, torch, stream, n_random=62, seed=4, reps=2):
     return {"jobs": len(specs), "histories": total, "batched_s": float(np.median(tb)),
             "batched_histories_per_s": total / float(np.median(tb)), "plain_s": float(np.median(tp)),
             "plain_histories_per_s": total / float(np.median(tp)),
-            "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}}
+            "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]},
+            "plain_launch": {"registers": "64" if tune1[0] else "<=128", "block": tune1[1], "chunk": tune1[2]}}
 
 
 # ------------------------------------------------------------------ serving
@@ -573,15 +586,25 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
     out = {"requests": len(reqs), "window_s": window_s, "rate_per_s": rate,
            "offered_histories_per_s": sum(r["n"] for r in reqs) / window_s}
     try:
-        # launch shape for the 4DCT from the autotuner (shared by both engines)
+        # launch shapes from the autotuners: the server's steps are batches of
+        # several requests (tuned on two requests' phases in one batch; the
+        # slots take the base's options), the plain engine runs one phase
+        # job per launch (tuned on the fullest phase)
         probe = D.dose_create_view(base)
         D.dose_add_spots(probe, spots, dlv, stream)
         pp = D.dose_read(probe, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
-        tune = D.dose_autotune(probe, int(np.argmax(pp)), 10_000_000, 2_000_000, 1, stream)
-        for opt, v in ((D.DOSE_OPT_REGISTERS, tune[0]), (D.DOSE_OPT_BLOCK, tune[1]), (D.DOSE_OPT_CHUNK, tune[2])):
-            D.dose_set_option(base, opt, v)
-            D.dose_set_option(probe, opt, v)
         phases = [p for p in range(ph.n_phases) if pp[p] > 0]
+        probe2 = D.dose_create_view(base)
+        D.dose_add_spots(probe2, spots, dlv, stream)
+        tune = D.dose_autotune_batch(D.make_jobs([dict(ctx=v, phase=p, n_histories=5_000_000, seed=1 + k)
+                                                  for k, v in enumerate((probe, probe2)) for p in phases]),
+                                     20_000_000, stream)
+        mat = D.dose_get_option(probe2, D.DOSE_OPT_MATERIAL_GRID)
+        D.dose_destroy(probe2)
+        for opt, v in ((D.DOSE_OPT_REGISTERS, tune[0]), (D.DOSE_OPT_BLOCK, tune[1]), (D.DOSE_OPT_CHUNK, tune[2]),
+                       (D.DOSE_OPT_MATERIAL_GRID, mat)):
+            D.dose_set_option(base, opt, v)
+        tune1 = D.dose_autotune(probe, int(np.argmax(pp)), 10_000_000, 2_000_000, 1, stream)
 
         # ---- served: continuous batching
         srv = D.dose_server_create(base, budget_bytes, 40_000_000, spots, dlv, min_slice=20_000,
@@ -641,6 +664,7 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
         out["plain"] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                         "mean_s": float(np.mean(lat)), "histories_per_s": hist / total_s, "makespan_s": total_s}
         out["launch"] = {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]}
+        out["plain_launch"] = {"registers": "64" if tune1[0] else "<=128", "block": tune1[1], "chunk": tune1[2]}
     finally:
         D.dose_destroy(base)
     return out

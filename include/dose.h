@@ -418,6 +418,18 @@ int dose_read(dose_ctx *c, int what, int phase, void *dst, size_t bytes, int dst
 int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_histories,
                   uint64_t seed, void *stream, int64_t best[4]);
 
+/* Autotuner for a ragged batch (the launch dose_run_batch makes of `jobs`):
+ * times a sample of about sample_histories histories spread over the jobs
+ * in proportion to their ranges (job k: the first histories of its range)
+ * under the launch shapes and material sources of dose_autotune, with the
+ * kernel the batch itself launches, and sets the winners on every context
+ * of the batch.  Every (context, phase) of the batch is cleared and its
+ * histories allocated first; their tallies and doses are overwritten, so
+ * run the batch (with DOSE_JOB_CLEAR) afterwards.  best as dose_autotune.
+ * Waits for the stream.                                                    */
+int dose_autotune_batch(const dose_job *jobs, int n_jobs, uint64_t sample_histories, void *stream,
+                        int64_t best[4]);
+
 /* Set an option (DOSE_OPT_*).                                              */
 int dose_set_option(dose_ctx *c, int option, int64_t value);
 

@@ -1038,19 +1038,23 @@ int dose_run_phase(dose_ctx *c, int phase, uint64_t n_histories, uint64_t seed, 
     return rc;
 }
 
-int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_histories, uint64_t seed,
-                  void *stream, int64_t best[4])
+}  // extern "C"
+
+namespace {
+
+// Time run() (one transport launch of a history sample on `st`) under each
+// launch shape -- register variant x block x chunk, then the material source
+// for the fastest -- with c's options, which the launches read; leaves the
+// winners in c's options (or the previous ones on error).
+template <class Run>
+int tune_shapes(dose_ctx *c, cudaStream_t st, bool single, Run run, int64_t best[4])
 {
-    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
-    if (sample_histories == 0 || sample_histories > n_histories)
-        return fail(c, DOSE_EINVAL, "sample must be in 1..n_histories");
     static const int blocks[] = {128, 256, 512, 1024};
     static const unsigned chunks[] = {32, 64, 128, 256};
     const int keep_block = c->block, keep_regs = c->regs, keep_per_sm = c->blocks_per_sm;
     const int keep_mat = c->material_grid;
-    int best_mat = keep_mat;
     const unsigned keep_chunk = c->chunk;
-    cudaStream_t st = S(stream);
+    int best_mat = keep_mat;
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
@@ -1058,22 +1062,26 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
     int best_block = keep_block, best_regs = keep_regs;
     unsigned best_chunk = keep_chunk;
     int rc = DOSE_OK;
-    dose_job j;
-    j.ctx = c; j.phase = phase; j.n_histories = n_histories; j.seed = seed; j.spr_scale = 1.0f;
-    j.shift_mm[0] = j.shift_mm[1] = j.shift_mm[2] = 0.0f;
+    auto timed = [&](float *ms) -> int {
+        cudaEventRecord(e0, st);
+        int r = run();
+        if (r) return r;
+        cudaEventRecord(e1, st);
+        if ((r = sync_stream(c, st))) return r;
+        cudaEventElapsedTime(ms, e0, e1);
+        return DOSE_OK;
+    };
     c->blocks_per_sm = 0;
     // the occupancy query needs the kernels' dynamic shared-memory limit set
-    CK(c, transport_allow_smem());
-    // allocate the phase's histories once; each trial then only transports
-    j.flags = DOSE_JOB_CLEAR; j.hist_begin = 0; j.hist_end = 0;
-    if ((rc = dose_run_batch(&j, 1, stream))) goto done;
+    if (transport_allow_smem() != cudaSuccess) { rc = fail(c, DOSE_ECUDA, "cudaFuncSetAttribute failed"); goto done; }
     for (int regs = 0; regs < 2; ++regs) {
         for (int b : blocks) {
             if (!regs && b > 512) continue;
             int fits = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, regs ? (const void *)k_transport1_r64
-                                                                          : (const void *)k_transport1, b,
-                                                              transport_smem(1) + birth_smem(b)) != cudaSuccess || fits <= 0) {
+            const void *k = single ? (regs ? (const void *)k_transport1_r64 : (const void *)k_transport1)
+                                   : (regs ? (const void *)k_transport_r64 : (const void *)k_transport);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, k, b, transport_smem(1) + birth_smem(b)) != cudaSuccess ||
+                fits <= 0) {
                 cudaGetLastError();
                 continue;
             }
@@ -1081,13 +1089,8 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
                 c->regs = regs;
                 c->block = b;
                 c->chunk = ch;
-                j.flags = 0; j.hist_begin = 0; j.hist_end = sample_histories;
-                cudaEventRecord(e0, st);
-                if ((rc = dose_run_batch(&j, 1, stream))) goto done;
-                cudaEventRecord(e1, st);
-                if ((rc = sync_stream(c, st))) goto done;
                 float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
+                if ((rc = timed(&ms))) goto done;
                 if (best_ms < 0.0f || ms < best_ms) { best_ms = ms; best_block = b; best_chunk = ch; best_regs = regs; }
             }
         }
@@ -1102,13 +1105,8 @@ int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_
         for (int rep = 0; rep < 2; ++rep) {
             for (int m = 0; m < 2; ++m) {
                 c->material_grid = m;
-                j.flags = 0; j.hist_begin = 0; j.hist_end = sample_histories;
-                cudaEventRecord(e0, st);
-                if ((rc = dose_run_batch(&j, 1, stream))) goto done;
-                cudaEventRecord(e1, st);
-                if ((rc = sync_stream(c, st))) goto done;
                 float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
+                if ((rc = timed(&ms))) goto done;
                 if (t_mat[m] < 0.0f || ms < t_mat[m]) t_mat[m] = ms;
             }
         }
@@ -1123,11 +1121,80 @@ done:
     c->chunk = rc ? keep_chunk : best_chunk;
     c->regs = rc ? keep_regs : best_regs;
     c->blocks_per_sm = keep_per_sm;
-    c->ph[phase].has_dose = false;
     if (!rc && best_ms < 0.0f) rc = fail(c, DOSE_ECUDA, "autotune: no launch shape could be timed");
     if (!rc && best) {
         best[0] = best_regs; best[1] = best_block; best[2] = best_chunk;
         best[3] = (int64_t)(best_ms * 1000.0f);
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dose_autotune(dose_ctx *c, int phase, uint64_t n_histories, uint64_t sample_histories, uint64_t seed,
+                  void *stream, int64_t best[4])
+{
+    if (!c) return fail(nullptr, DOSE_EINVAL, "ctx is NULL");
+    if (sample_histories == 0 || sample_histories > n_histories)
+        return fail(c, DOSE_EINVAL, "sample must be in 1..n_histories");
+    cudaStream_t st = S(stream);
+    dose_job j;
+    j.ctx = c; j.phase = phase; j.n_histories = n_histories; j.seed = seed; j.spr_scale = 1.0f;
+    j.shift_mm[0] = j.shift_mm[1] = j.shift_mm[2] = 0.0f;
+    // allocate the phase's histories once; each trial then only transports
+    j.flags = DOSE_JOB_CLEAR; j.hist_begin = 0; j.hist_end = 0;
+    int rc = dose_run_batch(&j, 1, stream);
+    if (!rc) {
+        j.flags = 0; j.hist_begin = 0; j.hist_end = sample_histories;
+        rc = tune_shapes(c, st, true, [&] { return dose_run_batch(&j, 1, stream); }, best);
+    }
+    if (phase >= 0 && phase < c->g->n_phases) c->ph[phase].has_dose = false;
+    return rc;
+}
+
+int dose_autotune_batch(const dose_job *jobs, int n_jobs, uint64_t sample_histories, void *stream, int64_t best[4])
+{
+    if (!jobs || n_jobs <= 0 || !jobs[0].ctx) return fail(nullptr, DOSE_EINVAL, "no jobs");
+    dose_ctx *c0 = jobs[0].ctx;
+    if (sample_histories == 0) return fail(c0, DOSE_EINVAL, "sample_histories must be positive");
+    unsigned long long total = 0;
+    for (int k = 0; k < n_jobs; ++k) {
+        if (!jobs[k].ctx) return fail(c0, DOSE_EINVAL, "job %d has no context", k);
+        if (jobs[k].hist_end < jobs[k].hist_begin) return fail(c0, DOSE_EINVAL, "job %d: empty history range", k);
+        total += jobs[k].hist_end - jobs[k].hist_begin;
+    }
+    if (total == 0) return fail(c0, DOSE_EINVAL, "the batch has no histories");
+    // allocate each (context, phase) once, then time samples of every job:
+    // job k transports the first ceil(sample x its share) histories of its range
+    std::vector<dose_job> clear, sample;
+    for (int k = 0; k < n_jobs; ++k) {
+        bool seen = false;
+        for (const auto &q : clear) seen |= q.ctx == jobs[k].ctx && q.phase == jobs[k].phase;
+        if (!seen) {
+            dose_job q = jobs[k];
+            q.flags = DOSE_JOB_CLEAR; q.hist_begin = 0; q.hist_end = 0;
+            clear.push_back(q);
+        }
+        const unsigned long long cnt = jobs[k].hist_end - jobs[k].hist_begin;
+        if (!cnt) continue;
+        dose_job q = jobs[k];
+        q.flags = 0;
+        const long double share = (long double)sample_histories * cnt / total;
+        q.hist_end = q.hist_begin + std::min<unsigned long long>(cnt, (unsigned long long)std::ceil(share));
+        sample.push_back(q);
+    }
+    int rc = dose_run_batch(clear.data(), (int)clear.size(), stream);
+    if (rc) return rc;
+    const bool single = sample.size() == 1;
+    rc = tune_shapes(c0, S(stream), single,
+                     [&] { return dose_run_batch(sample.data(), (int)sample.size(), stream); }, best);
+    for (const auto &q : clear) {
+        q.ctx->ph[q.phase].has_dose = false;
+        if (rc) continue;
+        q.ctx->regs = c0->regs; q.ctx->block = c0->block; q.ctx->chunk = c0->chunk;
+        q.ctx->material_grid = c0->material_grid;
     }
     return rc;
 }

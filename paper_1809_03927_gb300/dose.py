@@ -123,6 +123,7 @@ def _load():
         "dose_set_field_beam": ([P, I, P], I),
         "dose_get_option": ([P, I, C.POINTER(I64)], I),
         "dose_measure_peaks": ([P, P], I),
+        "dose_autotune_batch": ([P, I, U64, P, P], I),
         "dose_server_timing": ([P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -329,6 +330,15 @@ def dose_autotune(ctx, phase, n_histories, sample_histories, seed, stream=None):
     best = (C.c_int64 * 4)()
     _check(_lib.dose_autotune(ctx, int(phase), int(n_histories), int(sample_histories), int(seed),
                               _stream(stream), best), ctx)
+    return tuple(int(v) for v in best)
+
+
+def dose_autotune_batch(jobs, sample_histories, stream=None):
+    """Tune the launch shape of a batch (``make_jobs`` array) on a sample of
+    its histories; returns (register option, block, chunk, microseconds).
+    The batch's phases are cleared: run the batch afterwards."""
+    best = (C.c_int64 * 4)()
+    _check(_lib.dose_autotune_batch(jobs, len(jobs), int(sample_histories), _stream(stream), best), None)
     return tuple(int(v) for v in best)
 
 

@@ -582,6 +582,40 @@ def test_autotune_keeps_results(gpu):
     np.testing.assert_array_equal(t, ref)
 
 
+def test_autotune_batch_keeps_results(gpu):
+    """The batch autotuner times a sample of a ragged batch (two grids, two
+    seeds: the job-table kernel) and only picks its launch shape: the
+    batch's tallies are bit-identical before and after tuning, and every
+    context of the batch gets the picked shape."""
+    ph, pl = W.slab_phantom(n=48), W.slab_plan(n_layers=3, nx=3, ny=2)
+    ph2, pl2 = W.water_phantom(32, 32, 60), W.pencil_plan(120.0, 3.0)
+    ctxs = [H.make_ctx(gpu, ph), H.make_ctx(gpu, ph2)]
+    try:
+        gpu.dose_add_spots(ctxs[0], gpu.spots_array(pl), None)
+        gpu.dose_add_spots(ctxs[1], gpu.spots_array(pl2), None)
+        jobs = gpu.make_jobs([dict(ctx=ctxs[0], phase=0, n_histories=200_000, seed=3),
+                              dict(ctx=ctxs[1], phase=0, n_histories=100_000, seed=4)])
+
+        def tallies():
+            gpu.dose_run_batch(jobs)
+            return [gpu.dose_read(c, gpu.DOSE_TALLY_I64, 0, np.zeros(p.hu.shape, np.uint64))
+                    for c, p in zip(ctxs, (ph, ph2))]
+
+        ref = tallies()
+        regs, block, chunk, us = gpu.dose_autotune_batch(jobs, 60_000)
+        assert regs in (0, 1) and block in (128, 256, 512, 1024) and chunk in (32, 64, 128, 256) and us > 0
+        for c in ctxs:
+            assert gpu.dose_get_option(c, gpu.DOSE_OPT_BLOCK) == block
+            assert gpu.dose_get_option(c, gpu.DOSE_OPT_CHUNK) == chunk
+        got = tallies()
+    finally:
+        for c in ctxs:
+            gpu.dose_destroy(c)
+    for a, b in zip(ref, got):
+        assert a.sum() > 0
+        np.testing.assert_array_equal(a, b)
+
+
 def test_material_grid_gives_the_same_tallies(gpu):
     """The per-voxel (density, SPR) grid holds the table's values, so the
     transport's results do not depend on DOSE_OPT_MATERIAL_GRID (checked on
