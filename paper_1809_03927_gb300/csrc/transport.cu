@@ -423,14 +423,6 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
         // ---------------- one condensed-history step
         const TJob &J = job_of(job);
         const TJob &Jo = own_of(job);
-        if (step >= J.max_steps) {
-            led_add(job, 0, __float2ull_rn(E * wq));
-            led_add(job, 2, step);
-            if (staged) atomicOr(s_led + 4 * job + 3, (unsigned long long)FLAG_STEPLIMIT);
-            else atomicOr(jobs[job].ledger + LED_FLAGS, (unsigned long long)FLAG_STEPLIMIT);
-            alive = false;
-            continue;
-        }
         const int nx = J.nx, ny = J.ny;
         const int vox = (iz * ny + iy) * nx + ix;
         float2 m;
@@ -590,9 +582,17 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
             const float2 ext = __fmul2_rn(make_float2((float)iz, (float)(iz + 1)), make_float2(dz, dz));
             if (!(pz >= ext.x && pz <= ext.y)) iz = (int)floorf(pz * J.idz);
         }
-        if ((unsigned)ix >= (unsigned)nx || (unsigned)iy >= (unsigned)ny || (unsigned)iz >= (unsigned)J.nz) {
+        // leaving the grid, or the step limit reached (checked with the exit
+        // so that a step pays one rare branch): the energy escapes
+        const bool outside = (unsigned)ix >= (unsigned)nx || (unsigned)iy >= (unsigned)ny ||
+                             (unsigned)iz >= (unsigned)J.nz;
+        if (outside || step >= J.max_steps) {
             led_add(job, 0, __float2ull_rn(E * wq));
             led_add(job, 2, step);
+            if (!outside) {
+                if (staged) atomicOr(s_led + 4 * job + 3, (unsigned long long)FLAG_STEPLIMIT);
+                else atomicOr(jobs[job].ledger + LED_FLAGS, (unsigned long long)FLAG_STEPLIMIT);
+            }
             alive = false;
         }
     }

@@ -421,7 +421,11 @@ def test_view_shares_grid(gpu):
 
 
 # ---------------------------------------------------------- failure paths
-def test_step_limit_reported(gpu):
+def test_step_limit_reported(gpu, orc):
+    """A history that reaches the step limit stops after that many steps with
+    its energy counted as escaped, and the run reports DOSE_ESTEPLIMIT; with
+    matched streams (no scattering) the deposits of the first steps are the
+    oracle's, whose histories stop at the same step."""
     ph, pl = _config1(n=16, nz=100)
     g = H.gpu_run(gpu, ph, pl, 1000, 1, options={gpu.DOSE_OPT_MAX_STEPS: 5})
     assert g["status"] == gpu.DOSE_ESTEPLIMIT
@@ -429,6 +433,12 @@ def test_step_limit_reported(gpu):
     assert abs(dep + esc + rem - inc) <= 6000
     ok = H.gpu_run(gpu, ph, pl, 1000, 1)
     assert ok["status"] == gpu.DOSE_OK
+    phys = orc.PHYS_STRAGGLING | orc.PHYS_NUCLEAR
+    m = H.gpu_run(gpu, ph, pl, 20_000, 3, physics=phys, options={gpu.DOSE_OPT_MAX_STEPS: 7})
+    o = orc.dose(ph, pl, 20_000, 3, physics=phys, max_steps=7)
+    assert o["status"] == orc.ESTEP and m["status"] == gpu.DOSE_ESTEPLIMIT
+    assert np.max(np.abs(m["dose"] - o["dose"])) <= 0.002 * o["dose"].max()
+    assert int(m["ledger"][4]) == o["steps"]
 
 
 def test_errors_leave_context_usable(gpu):
