@@ -259,10 +259,10 @@ def test_full_size_4dct_phase(gpu, orc):
     3000-spot plan (20 layers, 70-180 MeV) along +y: 1e9 histories (100
     independent runs of 1e7) against the 1e8-history oracle reference, inside
     the body contour.  Every voxel above 10 % of Dmax: within 3 combined
-    standard errors (>= 99.5 %).  The depth-dose along the beam and the two
-    lateral profiles (dose summed over the other axes, where the noise of
-    single voxels averages out): within 1 % of their maxima wherever they
-    exceed 10 % of it.  The 1 %-of-Dmax and gamma(1 %/1 mm) criteria per
+    standard errors (>= 99.5 %).  The deposited energy along the beam and
+    across it (dose x density summed over the other two axes, where the noise
+    of single voxels averages out to ~0.03 % of the maximum): within 1 % of
+    the profile's maximum wherever it exceeds 10 % of it.  The 1 %-of-Dmax and gamma(1 %/1 mm) criteria per
     voxel are decided on the voxels whose combined standard error is at most
     a third of 1 % of Dmax: in these 2.5 mm^3 voxels the oracle's standard
     error at 1e8 histories is ~1.3 % of the dose in water and ~2.4 % in lung
@@ -275,21 +275,22 @@ def test_full_size_4dct_phase(gpu, orc):
     ph = W.Phantom(np.ascontiguousarray(ph.hu[0]), ph.d, ph.origin, ph.beam_axis, ph.beam_sign)
     plan = W.tumour_plan(geo, ph.origin)
     g, sg = H.gpu_batches_on_device(gpu, ph, plan, 1_000_000_000, 101, 100)
-    body = H.body_mask(orc, ph)[box]
+    rho = orc.density(ph)[box]
+    body = rho >= 0.1
     g, sg = np.where(body, g[box], 0.0), np.where(body, sg[box], 0.0)
     mean, sem = np.where(body, mean, 0.0), np.where(body, sem, 0.0)
     comb = _comb(sg, sem)
     frac, nsel = H.sigma_pass(g, mean, comb, dmax)
     profiles = []
     for axes in ((0, 2), (0, 1), (1, 2)):                 # along y (the beam), along z, along x
-        pg, po = g.sum(axis=axes), mean.sum(axis=axes)
+        pg, po = (g * rho).sum(axis=axes), (mean * rho).sum(axis=axes)
         keep = po >= 0.1 * po.max()
         profiles.append(float(np.max(np.abs(pg - po)[keep]) / po.max()))
     sel = mean >= 0.1 * dmax
     resolved = sel & (comb <= dmax * 0.01 / 3.0)
     one = float((np.abs(g - mean) <= 0.01 * dmax)[resolved].mean())
     gam = H.gamma_pass(mean, g, ph.d, dmax=dmax, select=resolved)
-    print(f"4DCT phase 1e9 vs oracle 1e8: {nsel} voxels, 3 sigma {frac:.4f}; profiles (y, z, x) max "
+    print(f"4DCT phase 1e9 vs oracle 1e8: {nsel} voxels, 3 sigma {frac:.4f}; energy profiles (y, z, x) max "
           f"|diff| {profiles[0]:.4f} {profiles[1]:.4f} {profiles[2]:.4f} of their maxima; resolved "
           f"{int(resolved.sum())} ({resolved.sum() / sel.sum():.3f}): 1 % Dmax {one:.4f}, gamma {gam:.4f}")
     assert nsel > 100_000 and frac >= 0.995, frac
