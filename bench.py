@@ -71,12 +71,12 @@ def _args():
     p.add_argument("--serve-budget-gb", type=float, default=150.0, help="device memory for request slots")
     p.add_argument("--serve-low-rate", type=float, default=8.0,
                    help="mean arrivals per second of the second serving point (below capacity)")
-    p.add_argument("--serve-low-window", type=float, default=40.0,
+    p.add_argument("--serve-low-window", type=float, default=30.0,
                    help="seconds of arrivals of the second serving point (0: skip it)")
     p.add_argument("--histories-4d", type=int, default=100_000_000, help="histories per phase of the 4D plan")
     p.add_argument("--small-4d", action="store_true",
                    help="4D leg on a 128x128x80 grid at 2x2x5 mm (profiler captures), not the 4DCT workload")
-    p.add_argument("--reference-seconds", type=float, default=10.0,
+    p.add_argument("--reference-seconds", type=float, default=5.0,
                    help="CPU seconds of each timed oracle step of the reference arm")
     p.add_argument("--launch", default=None,
                    help="transport launch shape 'registers,block,chunk,material' instead of the autotuner's")
