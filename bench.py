@@ -819,6 +819,11 @@ def run_engine(args):
                      "peak_basis": f"measured: mixed FP32/INT32 instruction stream (dose_measure_peaks), "
                                    f"{peak_ops:.2f} Top/s; nominal {sms} SMs x 128 lanes x {sm_mhz:.0f} MHz = "
                                    f"{nominal:.2f} Top/s; FFMA alone {measured['issue_ffma'] / 1e12:.2f} Top/s",
+                     # the bound in histories/s: the slower of issue (300 slots per
+                     # step) and the tally atomics (one per step), per history
+                     "histories_per_s_bound": min(measured["issue_mixed"] / (steps_per_hist * OPS_PER_STEP),
+                                                  measured["atomic_u64"] / steps_per_hist),
+                     "histories_per_s_kernel": n_hist / (t_kernel / 1e3),
                      "atomic": {"achieved": steps_per_s, "peak": measured["atomic_u64"], "unit": "atomics/s",
                                 "frac": steps_per_s / measured["atomic_u64"],
                                 "basis": "one 64-bit tally atomic per step against measured u64 atomic additions "
