@@ -68,6 +68,8 @@ def _args():
                    help="histories per phase of each uncertainty trial")
     p.add_argument("--serve-window", type=float, default=5.0, help="seconds of Poisson arrivals")
     p.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
+    p.add_argument("--serve-policies", default="fair,shortest_first",
+                   help="server sharing policies to measure: fair (equal shares) and/or shortest_first")
     p.add_argument("--serve-budget-gb", type=float, default=150.0, help="device memory for request slots")
     p.add_argument("--serve-low-rate", type=float, default=8.0,
                    help="mean arrivals per second of the second serving point (below capacity)")
@@ -567,7 +569,48 @@ def _requests(window_s, rate, seed=5):
         out.append(dict(t=t, n=n, seed=int(rng.integers(1, 2 ** 62)), spr=spr, shift=sh))
 
 
-def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
+def _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hist, policy):
+    """Replay the arrival schedule through a server with the given sharing
+    policy; latency percentiles, throughput and where the makespan went."""
+    srv = D.dose_server_create(base, budget_bytes, 40_000_000, spots, dlv, min_slice=20_000,
+                               nsub=(2, 2, 5), dvf=dvf_dev, policy=policy)
+    done_at, k, t0, ids, max_active = {}, 0, time.perf_counter(), {}, 0
+    try:
+        while len(done_at) < len(reqs):
+            now = time.perf_counter() - t0
+            while k < len(reqs) and reqs[k]["t"] <= now:
+                r = reqs[k]
+                ids[D.dose_server_submit(srv, r["n"], r["seed"], r["spr"], r["shift"])] = k
+                k += 1
+            st = D.dose_server_stats(srv)
+            max_active = max(max_active, st["active"] + st["queued"])
+            if st["queued"] + st["active"] == 0:
+                time.sleep(max(0.0, min(0.005, reqs[k]["t"] - now)) if k < len(reqs) else 0.0)
+                continue
+            for rid in D.dose_server_step(srv, stream):
+                done_at[ids[rid]] = time.perf_counter() - t0
+                D.dose_server_release(srv, rid)
+        total_s = time.perf_counter() - t0
+        st = D.dose_server_stats(srv)
+        tm = D.dose_server_timing(srv)
+    finally:
+        D.dose_server_destroy(srv)
+    lat = [done_at[i] - reqs[i]["t"] for i in range(len(reqs))]
+    busy = tm["step_wall_s"]
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(np.mean(lat)), "histories_per_s": hist / total_s, "makespan_s": total_s,
+            "steps": st["steps"], "slots": st["slots"], "max_in_system": max_active,
+            "slot_gb": st["slot_bytes"] / 1e9,
+            # where the makespan went: steps (device batch, device
+            # accumulation, host remainder of the step) and idle time
+            # waiting for arrivals
+            "breakdown_s": {"transport_batches": tm["batch_s"], "accumulations": tm["accumulate_s"],
+                            "host_step_overhead": max(busy - tm["batch_s"] - tm["accumulate_s"], 0.0),
+                            "idle_between_steps": max(total_s - busy, 0.0)},
+            "histories_per_device_batch_s": hist / tm["batch_s"] if tm["batch_s"] > 0 else None}
+
+
+def _bench_serving(D, torch, stream, window_s, rate, budget_bytes, policies):
     """p50/p99 latency (arrival -> dose ready) and histories/s of the
     continuous-batching server against the plain engine (each request alone,
     one phase job per launch, first come first served) on the same arrival
@@ -606,44 +649,12 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes):
             D.dose_set_option(base, opt, v)
         tune1 = D.dose_autotune(probe, int(np.argmax(pp)), 10_000_000, 2_000_000, 1, stream)
 
-        # ---- served: continuous batching
-        srv = D.dose_server_create(base, budget_bytes, 40_000_000, spots, dlv, min_slice=20_000,
-                                   nsub=(2, 2, 5), dvf=dvf_dev)
-        lat, done_at, k, t0 = [], {}, 0, time.perf_counter()
-        ids = {}
-        max_active = 0
-        while len(done_at) < len(reqs):
-            now = time.perf_counter() - t0
-            while k < len(reqs) and reqs[k]["t"] <= now:
-                r = reqs[k]
-                ids[D.dose_server_submit(srv, r["n"], r["seed"], r["spr"], r["shift"])] = k
-                k += 1
-            st = D.dose_server_stats(srv)
-            max_active = max(max_active, st["active"] + st["queued"])
-            if st["queued"] + st["active"] == 0:
-                time.sleep(max(0.0, min(0.005, reqs[k]["t"] - now)) if k < len(reqs) else 0.0)
-                continue
-            for rid in D.dose_server_step(srv, stream):
-                done_at[ids[rid]] = time.perf_counter() - t0
-                D.dose_server_release(srv, rid)
-        total_s = time.perf_counter() - t0
-        st = D.dose_server_stats(srv)
-        tm = D.dose_server_timing(srv)
-        D.dose_server_destroy(srv)
-        lat = [done_at[i] - reqs[i]["t"] for i in range(len(reqs))]
+        # ---- served: continuous batching, under each sharing policy
         hist = sum(r["n"] // len(phases) * len(phases) for r in reqs)
-        busy = tm["step_wall_s"]
-        out["served"] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                         "mean_s": float(np.mean(lat)), "histories_per_s": hist / total_s, "makespan_s": total_s,
-                         "steps": st["steps"], "slots": st["slots"], "max_in_system": max_active,
-                         "slot_gb": st["slot_bytes"] / 1e9,
-                         # where the makespan went: steps (device batch, device
-                         # accumulation, host remainder of the step) and idle
-                         # time waiting for arrivals
-                         "breakdown_s": {"transport_batches": tm["batch_s"], "accumulations": tm["accumulate_s"],
-                                         "host_step_overhead": max(busy - tm["batch_s"] - tm["accumulate_s"], 0.0),
-                                         "idle_between_steps": max(total_s - busy, 0.0)},
-                         "histories_per_device_batch_s": hist / tm["batch_s"] if tm["batch_s"] > 0 else None}
+        for key, policy in (("served", D.DOSE_SERVE_FAIR), ("served_shortest_first", D.DOSE_SERVE_SHORTEST_FIRST)):
+            if key in policies:
+                out[key] = _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hist, policy)
+                out[key]["policy"] = policies[key]
 
         # ---- plain: one request at a time, one phase job per launch
         done_at, t0, k = {}, time.perf_counter(), 0
@@ -841,11 +852,14 @@ def run_engine(args):
     if not args.no_trials:
         line["uncertainty_trials"] = _bench_trials(D, torch, stream, args.histories_trial)
     if not args.no_serve:
+        pol = {"fair": "served", "shortest_first": "served_shortest_first"}
+        policies = {pol[v.strip()]: v.strip() for v in args.serve_policies.split(",") if v.strip()}
         line["serving"] = _bench_serving(D, torch, stream, args.serve_window, args.serve_rate,
-                                         int(args.serve_budget_gb * 1e9))
+                                         int(args.serve_budget_gb * 1e9), policies)
         if args.serve_low_window > 0:
             line["serving_below_capacity"] = _bench_serving(D, torch, stream, args.serve_low_window,
-                                                            args.serve_low_rate, int(args.serve_budget_gb * 1e9))
+                                                            args.serve_low_rate, int(args.serve_budget_gb * 1e9),
+                                                            policies)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _oracle_sample(phantom, plan)
         line["cpu_baseline"].update(_oracle_extra(phantom, plan))

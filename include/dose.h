@@ -292,7 +292,15 @@ typedef struct dose_server_config {
     int32_t nsub[3];
     int32_t accumulate;
     const float *dvf;          /* device, n_phases x 3 x nvox mm, or NULL = identity */
+    int32_t policy;            /* DOSE_SERVE_FAIR or DOSE_SERVE_SHORTEST_FIRST */
+    int32_t reserved;          /* 0 */
 } dose_server_config;
+/* How a step's histories are shared among the active requests: equally
+ * (each at least min_slice per phase), or to the requests with the fewest
+ * histories left first (the step's budget handed out in that order; a
+ * request without a slice waits), which shortens the small requests'
+ * latency without stretching the large ones as much as equal shares do.  */
+enum { DOSE_SERVE_FAIR = 0, DOSE_SERVE_SHORTEST_FIRST = 1 };
 typedef struct dose_request {
     uint64_t n_histories;
     uint64_t seed;

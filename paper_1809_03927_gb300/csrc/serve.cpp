@@ -26,6 +26,8 @@
 #include "dose.h"
 #include "kernels.h"
 
+static_assert(sizeof(dose_server_config) == 64, "ABI layout");
+
 struct dose_server {
     struct Queued {
         int64_t id;
@@ -104,6 +106,8 @@ int dose_server_create(dose_ctx *base, const dose_server_config *cfg, const dose
     if (cfg->step_histories == 0) return sfail(nullptr, DOSE_EINVAL, "step_histories must be positive");
     if (cfg->accumulate && (cfg->nsub[0] < 1 || cfg->nsub[1] < 1 || cfg->nsub[2] < 1))
         return sfail(nullptr, DOSE_EINVAL, "nsub must be positive");
+    if (cfg->policy != DOSE_SERVE_FAIR && cfg->policy != DOSE_SERVE_SHORTEST_FIRST)
+        return sfail(nullptr, DOSE_EINVAL, "policy must be DOSE_SERVE_FAIR or DOSE_SERVE_SHORTEST_FIRST");
     dose_server *s = new dose_server;
     s->base = base;
     s->cfg = *cfg;
@@ -228,12 +232,37 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
     if (!s->ev[0])
         for (auto &e : s->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return sfail(s, DOSE_ECUDA, "cudaEventCreate failed");
-    // every active request gets an equal share of the step's histories
+    // the step's histories: an equal share for every active request, or
+    // (DOSE_SERVE_SHORTEST_FIRST) the budget handed out in order of the
+    // histories each request has left, fewest first; a request left
+    // without a slice waits for the next step.  At least min_slice
+    // histories per phase, so every slice makes progress.
     size_t phase_jobs = 0;
     for (const auto &a : s->active) phase_jobs += a.phases.size();
-    const uint64_t share = std::max<uint64_t>(
-        s->cfg.min_slice ? s->cfg.min_slice : 1,
-        s->cfg.step_histories / std::max<size_t>(1, phase_jobs));
+    const uint64_t min_slice = s->cfg.min_slice ? s->cfg.min_slice : 1;
+    std::vector<uint64_t> take(s->active.size(), 0);           // histories per phase this step
+    if (s->cfg.policy == DOSE_SERVE_SHORTEST_FIRST) {
+        std::vector<size_t> order(s->active.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        auto left = [&](size_t i) {
+            const auto &a = s->active[i];
+            return (a.per_phase - a.next) * (uint64_t)a.phases.size();
+        };
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return left(x) < left(y); });
+        uint64_t budget = s->cfg.step_histories;
+        for (size_t i : order) {
+            const auto &a = s->active[i];
+            if (a.phases.empty() || budget == 0) continue;
+            const uint64_t nph = a.phases.size();
+            const uint64_t t = std::min(a.per_phase - a.next, std::max(min_slice, budget / nph));
+            take[i] = t;
+            budget = budget > t * nph ? budget - t * nph : 0;
+        }
+    } else {
+        const uint64_t share = std::max<uint64_t>(min_slice, s->cfg.step_histories / std::max<size_t>(1, phase_jobs));
+        for (size_t i = 0; i < s->active.size(); ++i)
+            take[i] = std::min(s->active[i].per_phase - s->active[i].next, share);
+    }
     std::vector<dose_job> jobs;
     std::vector<int> finishing;
     for (size_t i = 0; i < s->active.size(); ++i) {
@@ -242,7 +271,8 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
             finishing.push_back((int)i);
             continue;
         }
-        const uint64_t end = std::min(a.per_phase, a.next + share);
+        if (take[i] == 0) continue;                  // waits for a later step
+        const uint64_t end = a.next + take[i];
         for (int p : a.phases) {
             dose_job j;
             j.ctx = s->slots[a.slot].view;

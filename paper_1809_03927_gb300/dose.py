@@ -28,6 +28,7 @@ DOSE_PHYS_STRAGGLING, DOSE_PHYS_MCS, DOSE_PHYS_NUCLEAR, DOSE_PHYS_ALL = 1, 2, 4,
 (DOSE_OPT_PHYSICS, DOSE_OPT_MAX_STEPS, DOSE_OPT_BLOCK, DOSE_OPT_BLOCKS_PER_SM, DOSE_OPT_CHUNK,
  DOSE_OPT_TIMEOUT_MS, DOSE_OPT_FAIL_ALLOC_AFTER, DOSE_OPT_REGISTERS, DOSE_OPT_MATERIAL_GRID) = range(9)
 DOSE_JOB_CLEAR, DOSE_JOB_FINISH = 1, 2
+DOSE_SERVE_FAIR, DOSE_SERVE_SHORTEST_FIRST = 0, 1
 LEDGER = ("deposited", "escaped", "removed", "incident", "steps", "histories", "flags", "protons")
 
 
@@ -69,7 +70,8 @@ class dose_job(C.Structure):
 class dose_server_config(C.Structure):
     _fields_ = [("memory_budget_bytes", C.c_uint64), ("step_histories", C.c_uint64),
                 ("min_slice", C.c_uint64), ("max_active", C.c_int32), ("ref_phase", C.c_int32),
-                ("nsub", C.c_int32 * 3), ("accumulate", C.c_int32), ("dvf", C.c_void_p)]
+                ("nsub", C.c_int32 * 3), ("accumulate", C.c_int32), ("dvf", C.c_void_p),
+                ("policy", C.c_int32), ("reserved", C.c_int32)]
 
 
 class dose_request(C.Structure):
@@ -84,7 +86,7 @@ class dose_dvf_grid(C.Structure):
 
 
 assert C.sizeof(dose_spot) == 32 and C.sizeof(dose_job) == 64 and C.sizeof(dose_delivery) == 112
-assert C.sizeof(dose_server_config) == 56 and C.sizeof(dose_request) == 40
+assert C.sizeof(dose_server_config) == 64 and C.sizeof(dose_request) == 40
 
 
 def _load():
@@ -383,12 +385,14 @@ def dose_run_phase_noalloc(hu, nx, ny, nz, dx_mm, dy_mm, dz_mm, origin_mm, beam_
 
 def dose_server_create(base, memory_budget_bytes, step_histories, spots, delivery=None,
                        min_slice=0, max_active=0, ref_phase=0, nsub=(2, 2, 5), accumulate=1,
-                       dvf=None):
-    """``dvf``: device tensor (n_phases x 3 x nvox) or None (identity)."""
+                       dvf=None, policy=0):
+    """``dvf``: device tensor (n_phases x 3 x nvox) or None (identity);
+    ``policy``: DOSE_SERVE_FAIR (0) or DOSE_SERVE_SHORTEST_FIRST (1)."""
     cfg = dose_server_config()
     cfg.memory_budget_bytes, cfg.step_histories, cfg.min_slice = (
         int(memory_budget_bytes), int(step_histories), int(min_slice))
     cfg.max_active, cfg.ref_phase, cfg.accumulate = int(max_active), int(ref_phase), int(accumulate)
+    cfg.policy = int(policy)
     cfg.nsub[:] = [int(v) for v in nsub]
     if dvf is not None:
         p, dev = _ptr(dvf)

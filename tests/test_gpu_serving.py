@@ -35,8 +35,9 @@ REQUESTS = [  # (histories, seed, spr scale, shift)
 def _serve(D, base, spots, dlv, dvf, arrivals, shape, **kw):
     """Serve REQUESTS; request k is submitted before step arrivals[k]."""
     srv = D.dose_server_create(base, 1 << 34, kw.get("step", 30_000), spots, dlv, min_slice=kw.get("min_slice", 50),
-                               max_active=kw.get("max_active", 0), nsub=NSUB, dvf=dvf)
-    out, ids, step, pending = {}, {}, 0, list(range(len(REQUESTS)))
+                               max_active=kw.get("max_active", 0), nsub=NSUB, dvf=dvf,
+                               policy=kw.get("policy", D.DOSE_SERVE_FAIR))
+    out, ids, done_step, step, pending = {}, {}, {}, 0, list(range(len(REQUESTS)))
     try:
         while len(out) < len(REQUESTS):
             for k in list(pending):
@@ -48,21 +49,28 @@ def _serve(D, base, spots, dlv, dvf, arrivals, shape, **kw):
                 acc = D.dose_server_result(srv, rid, D.DOSE_ACCUM, 0, np.zeros(shape, np.float32))
                 ph2 = D.dose_server_result(srv, rid, D.DOSE_PHASE_DOSE, 2, np.zeros(shape, np.float32))
                 out[ids[rid]] = (acc, ph2)
+                done_step[ids[rid]] = step
                 D.dose_server_release(srv, rid)
             step += 1
             assert step < 10_000
         stats = D.dose_server_stats(srv)
+        stats["done_step"] = done_step
     finally:
         D.dose_server_destroy(srv)
     return out, stats
 
 
-def test_served_results_equal_alone(gpu):
+@pytest.mark.parametrize("policy", ["fair", "shortest_first"])
+def test_served_results_equal_alone(gpu, policy):
+    """Under either sharing policy (equal shares, or the step's budget to
+    the requests with the fewest histories left) the slices differ but the
+    results are the bits of each request alone."""
     D = gpu
     ph, dvf, spots, dlv, base = _setup(D)
     shape = ph.hu.shape[1:]
+    pol = D.DOSE_SERVE_FAIR if policy == "fair" else D.DOSE_SERVE_SHORTEST_FIRST
     try:
-        mixed, stats = _serve(D, base, spots, dlv, dvf, [0, 1, 1, 3, 6], shape)
+        mixed, stats = _serve(D, base, spots, dlv, dvf, [0, 1, 1, 3, 6], shape, policy=pol)
         assert stats["completed"] == len(REQUESTS) and stats["queued"] == 0 and stats["active"] == 0
         assert stats["steps"] > 3 and stats["slots"] >= 2
         # each request alone: dose_run_4d with the server's even split over the phases
@@ -77,6 +85,29 @@ def test_served_results_equal_alone(gpu):
                 np.testing.assert_array_equal(mixed[k][1], ph2)
         finally:
             D.dose_destroy(view)
+    finally:
+        D.dose_destroy(base)
+
+
+def test_shortest_first_finishes_small_requests_first(gpu):
+    """All requests submitted together: with the budget going to the fewest
+    histories left, requests complete in order of size and the two smallest
+    in the first step, while the whole batch takes no more steps than equal
+    shares (the same histories go through each step)."""
+    D = gpu
+    ph, dvf, spots, dlv, base = _setup(D)
+    shape = ph.hu.shape[1:]
+    try:
+        _, fair = _serve(D, base, spots, dlv, dvf, [0] * len(REQUESTS), shape, policy=D.DOSE_SERVE_FAIR)
+        _, srpt = _serve(D, base, spots, dlv, dvf, [0] * len(REQUESTS), shape,
+                         policy=D.DOSE_SERVE_SHORTEST_FIRST)
+        by_size = sorted(range(len(REQUESTS)), key=lambda k: REQUESTS[k][0])
+        steps = [srpt["done_step"][k] for k in by_size]
+        assert steps == sorted(steps)
+        assert srpt["done_step"][by_size[0]] == 0 and srpt["done_step"][by_size[1]] == 0
+        assert max(srpt["done_step"].values()) <= max(fair["done_step"].values())
+        for k in by_size[:-1]:
+            assert srpt["done_step"][k] <= fair["done_step"][k]
     finally:
         D.dose_destroy(base)
 
@@ -151,6 +182,8 @@ def test_server_rejects_bad_input(gpu):
     try:
         with pytest.raises(D.DoseError):
             D.dose_server_create(base, 1000, 30_000, spots, dlv, dvf=dvf)       # budget below one slot
+        with pytest.raises(D.DoseError):
+            D.dose_server_create(base, 1 << 34, 30_000, spots, dlv, dvf=dvf, policy=2)   # no such policy
         srv = D.dose_server_create(base, 1 << 34, 30_000, spots, dlv, dvf=dvf)
         try:
             with pytest.raises(D.DoseError):
