@@ -575,6 +575,8 @@ def _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hi
     srv = D.dose_server_create(base, budget_bytes, 40_000_000, spots, dlv, min_slice=20_000,
                                nsub=(2, 2, 5), dvf=dvf_dev, policy=policy)
     done_at, k, t0, ids, max_active = {}, 0, time.perf_counter(), {}, 0
+    window_s = reqs[-1]["t"] if reqs else 0.0
+    at_window_end = None                      # requests in the system when the last one arrives
     try:
         while len(done_at) < len(reqs):
             now = time.perf_counter() - t0
@@ -584,6 +586,8 @@ def _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hi
                 k += 1
             st = D.dose_server_stats(srv)
             max_active = max(max_active, st["active"] + st["queued"])
+            if at_window_end is None and k == len(reqs):
+                at_window_end = st["active"] + st["queued"]
             if st["queued"] + st["active"] == 0:
                 time.sleep(max(0.0, min(0.005, reqs[k]["t"] - now)) if k < len(reqs) else 0.0)
                 continue
@@ -600,6 +604,7 @@ def _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hi
     return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(np.mean(lat)), "histories_per_s": hist / total_s, "makespan_s": total_s,
             "steps": st["steps"], "slots": st["slots"], "max_in_system": max_active,
+            "in_system_at_last_arrival": at_window_end,
             "slot_gb": st["slot_bytes"] / 1e9,
             # where the makespan went: steps (device batch, device
             # accumulation, host remainder of the step) and idle time
@@ -655,6 +660,17 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes, policies):
             if key in policies:
                 out[key] = _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hist, policy)
                 out[key]["policy"] = policies[key]
+
+        # capacity: the served rate while the device is busy (histories per
+        # second of transport batches); an offered load above it grows the
+        # queue, which the records show as requests in the system when the
+        # last request arrives
+        rates = [out[k]["histories_per_device_batch_s"] for k in ("served", "served_shortest_first")
+                 if k in out and out[k]["histories_per_device_batch_s"]]
+        if rates:
+            out["capacity_histories_per_s"] = max(rates)
+            out["offered_over_capacity"] = out["offered_histories_per_s"] / max(rates)
+            out["above_capacity"] = out["offered_over_capacity"] > 1.0
 
         # ---- plain: one request at a time, one phase job per launch
         done_at, t0, k = {}, time.perf_counter(), 0
