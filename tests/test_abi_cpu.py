@@ -46,6 +46,15 @@ def test_argument_validation_without_device(libdose):
         assert D.dose_last_error(None)
     lib = D.lib()
     assert lib.dose_create_grid(None, 4, 4, 4, 1.0, 1.0, 1.0, None, 1, None, 0, None, None) == D.DOSE_EINVAL
+    # voxel indices are 32-bit: a grid of 2^31 voxels is refused before any
+    # pointer is read or any device memory is touched
+    import ctypes as C
+    out = C.c_void_p()
+    f3 = (C.c_float * 3)
+    rc = lib.dose_create_grid(C.byref(out), 2048, 1024, 1024, 1.0, 1.0, 1.0, f3(0, 0, 0), 1, None, 0,
+                              f3(0, 0, 1), None)
+    assert rc == D.DOSE_EINVAL and out.value is None
+    assert b"2^31" in lib.dose_last_error(None)
     assert lib.dose_run_batch(None, 0, None) == D.DOSE_EINVAL
     assert lib.dose_read(None, 0, 0, None, 0, 0, None) == D.DOSE_EINVAL
     assert lib.dose_set_option(None, 0, 0) == D.DOSE_EINVAL
