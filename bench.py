@@ -48,8 +48,7 @@ OPS_PER_STEP_RANGE = (230, 300, 450)
 # block, chunk, material grid), from ncu --metrics dram__bytes_read.sum,
 # dram__bytes_write.sum on the full-size launch of the current kernel
 # (bench.py --launch R,B,C,M; the single-job kernel with subnormals flushed).
-TRANSPORT_DRAM = {(1, 1024, 32, 1): 3.73e6, (1, 1024, 64, 1): 3.80e6, (1, 1024, 128, 1): 3.92e6,
-                  (1, 1024, 64, 0): 2.73e6}
+TRANSPORT_DRAM = {}
 
 
 def _args():
@@ -840,7 +839,10 @@ def run_engine(args):
                    "parallelism": f"{ws} independent replica(s), one per GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "k_transport1_r64" if tune[0] else "k_transport1", "kernel_ms": t_kernel,
+                     # the single-job kernel built for all physics on and
+                     # the material source in use (<7, 1>: grid, <7, 2>: HU)
+                     "kernel": ("k_transport1_r64" if tune[0] else "k_transport1") + ("<7, 1>" if material else "<7, 2>"),
+                     "kernel_ms": t_kernel,
                      "ops_per_step": OPS_PER_STEP,
                      "frac_by_ops_per_step": {str(k): steps_per_s * k / 1e12 / peak_ops for k in OPS_PER_STEP_RANGE},
                      "peak_basis": f"measured: mixed FP32/INT32 instruction stream (dose_measure_peaks), "

@@ -962,9 +962,9 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         if (!single)
             CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
         CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
-        const void *kern = single ? (c0->regs ? (const void *)k_transport1_r64 : (const void *)k_transport1)
-                         : shared ? (c0->regs ? (const void *)k_transportS_r64 : (const void *)k_transportS)
-                                  : (c0->regs ? (const void *)k_transport_r64 : (const void *)k_transport);
+        const int mode = single ? kLaunchSingle : shared ? kLaunchShared : kLaunchTable;
+        const int spec = transport_spec(tj.data(), (int)tj.size());
+        const void *kern = transport_kernel(mode, c0->regs, spec);
         if (!c0->regs && c0->block > 512)
             return fail(c0, DOSE_EINVAL, "block %d needs the 64-register variant (DOSE_OPT_REGISTERS 1)", c0->block);
         CK(c0, transport_allow_smem());
@@ -997,23 +997,13 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         // keep at least ~4 pulls per warp so the tail stays short
         while (chunk > 32 && (unsigned long long)chunk * warps * 4 > work) chunk >>= 1;
         const unsigned grid = (unsigned)(sms * per_sm);
-        if (single && c0->regs)
-            k_transport1_r64<<<grid, c0->block, smem, st>>>(tj[0], work, c0->d_counter, tab.dev, tab.inv_ds, chunk);
-        else if (single)
-            k_transport1<<<grid, c0->block, smem, st>>>(tj[0], work, c0->d_counter, tab.dev, tab.inv_ds, chunk);
-        else if (shared && c0->regs)
-            k_transportS_r64<<<grid, c0->block, smem, st>>>(tj[0], c0->d_jobs, (int)tj.size(), work, c0->d_counter,
-                                                            tab.dev, tab.inv_ds, chunk, stage);
-        else if (shared)
-            k_transportS<<<grid, c0->block, smem, st>>>(tj[0], c0->d_jobs, (int)tj.size(), work, c0->d_counter,
-                                                        tab.dev, tab.inv_ds, chunk, stage);
-        else if (c0->regs)
-            k_transport_r64<<<grid, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
-                                                           tab.dev, tab.inv_ds, chunk, stage);
-        else
-            k_transport<<<grid, c0->block, smem, st>>>(c0->d_jobs, (int)tj.size(), work, c0->d_counter,
-                                                       tab.dev, tab.inv_ds, chunk, stage);
-        CK(c0, cudaGetLastError());
+        TransportLaunch L;
+        L.mode = mode; L.regs = c0->regs; L.spec = spec;
+        L.grid = grid; L.block = (unsigned)c0->block; L.smem = smem; L.stream = st;
+        L.job0 = &tj[0]; L.d_jobs = c0->d_jobs; L.n_jobs = (int)tj.size();
+        L.total = work; L.counter = c0->d_counter; L.tab = tab.dev; L.inv_ds = tab.inv_ds;
+        L.chunk = chunk; L.stage = stage;
+        CK(c0, transport_launch(L));
     }
     if (!nj.empty()) {
         CK(c0, cudaMemcpyAsync(c0->d_norm, nj.data(), nj.size() * sizeof(NormJob), cudaMemcpyHostToDevice, st));
@@ -1078,8 +1068,7 @@ int tune_shapes(dose_ctx *c, cudaStream_t st, bool single, Run run, int64_t best
         for (int b : blocks) {
             if (!regs && b > 512) continue;
             int fits = 0;
-            const void *k = single ? (regs ? (const void *)k_transport1_r64 : (const void *)k_transport1)
-                                   : (regs ? (const void *)k_transport_r64 : (const void *)k_transport);
+            const void *k = transport_kernel(single ? kLaunchSingle : kLaunchTable, regs, kSpecGeneric);
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fits, k, b, transport_smem(1) + birth_smem(b)) != cudaSuccess ||
                 fits <= 0) {
                 cudaGetLastError();

@@ -25,29 +25,42 @@ int copy_plan(dose_ctx *dst, const dose_ctx *src, void *stream);
 __global__ void k_density(const int16_t *hu, float *rho, long long n, const Tables *tab);
 __global__ void k_material(const int16_t *hu, float2 *m, long long n, const Tables *tab);
 __global__ void k_alloc(const AllocJob *jobs);
-// stage != 0: the launch gives transport_smem(n_jobs) bytes and the job
-// table is staged in shared memory; 0: transport_smem(kMaxStagedJobs + 1)
-// (tables only) and the jobs are read from global memory.
-__global__ void k_transport(const TJob *jobs, int n_jobs, unsigned long long total,
-                            unsigned long long *counter, const Tables *gtab, float inv_ds,
-                            unsigned chunk, int stage);
-__global__ void k_transport_r64(const TJob *jobs, int n_jobs, unsigned long long total,
-                                unsigned long long *counter, const Tables *gtab, float inv_ds,
-                                unsigned chunk, int stage);
-// One job, passed by value (kernel-parameter memory); the launch gives
-// transport_smem(1) + birth_smem(block) bytes of shared memory.
-__global__ void k_transport1(const __grid_constant__ TJob job, unsigned long long total, unsigned long long *counter,
-                             const Tables *gtab, float inv_ds, unsigned chunk);
-__global__ void k_transport1_r64(const __grid_constant__ TJob job, unsigned long long total, unsigned long long *counter,
-                                 const Tables *gtab, float inv_ds, unsigned chunk);
-// Several jobs that agree on every field before TJob::hu (see
-// jobs_share_step_fields): those fields from `common`, the rest per job.
-__global__ void k_transportS(const __grid_constant__ TJob common, const TJob *jobs, int n_jobs,
-                             unsigned long long total, unsigned long long *counter, const Tables *gtab,
-                             float inv_ds, unsigned chunk, int stage);
-__global__ void k_transportS_r64(const __grid_constant__ TJob common, const TJob *jobs, int n_jobs,
-                                 unsigned long long total, unsigned long long *counter, const Tables *gtab,
-                                 float inv_ds, unsigned chunk, int stage);
+// The transport kernels (csrc/transport.cu), reached through
+// transport_kernel() and transport_launch().  mode: one job as a kernel
+// parameter (kLaunchSingle; the launch gives transport_smem(1) +
+// birth_smem(block) bytes of shared memory), a table of jobs whose
+// per-step fields (see jobs_share_step_fields) come from the parameter
+// `job0` (kLaunchShared), or a general table (kLaunchTable).  For the two
+// table modes, stage != 0: the launch gives transport_smem(n_jobs) +
+// birth_smem(block) bytes and the job table is staged in shared memory;
+// 0: transport_smem(kMaxStagedJobs + 1) + birth_smem(block) (tables only)
+// and the jobs are read from global memory.  regs: 1 = the 64-register
+// build (blocks up to 1024 threads), 0 = up to 128 registers (blocks up to
+// 512).  spec: kSpecGeneric reads each job's physics mask and material
+// source; kSpecFullGrid and kSpecFullHu are built for jobs that all have
+// every physics process on and, respectively, all have a per-voxel (rho,
+// SPR) grid or all read HU + table (transport_spec() says which applies).
+enum { kLaunchTable = 0, kLaunchSingle = 1, kLaunchShared = 2 };
+enum { kSpecGeneric = 0, kSpecFullGrid = 1, kSpecFullHu = 2 };
+struct TransportLaunch {
+    int mode, regs, spec;
+    unsigned grid, block;
+    size_t smem;
+    cudaStream_t stream;
+    const TJob *job0;                   // host: the job (single) or the shared fields (shared)
+    const TJob *d_jobs;                 // device table (table and shared modes)
+    int n_jobs;
+    unsigned long long total;           // work items
+    unsigned long long *counter;        // device work counter, zero at launch
+    const Tables *tab;
+    float inv_ds;
+    unsigned chunk;
+    int stage;
+};
+// The most specialised kernel every job of the launch satisfies.
+int transport_spec(const TJob *jobs, int n);
+const void *transport_kernel(int mode, int regs, int spec);
+cudaError_t transport_launch(const TransportLaunch &L);
 // True when every job agrees with the first on the per-step fields (the
 // first kStepFieldBytes bytes of a TJob).
 inline bool jobs_share_step_fields(const TJob *jobs, int n)
@@ -56,7 +69,7 @@ inline bool jobs_share_step_fields(const TJob *jobs, int n)
         if (std::memcmp(&jobs[j], &jobs[0], kStepFieldBytes) != 0) return false;
     return true;
 }
-// The six transport kernels accept up to kSmemTransportMax + birth_smem(1024)
+// Every transport kernel accepts up to kSmemTransportMax + birth_smem(1024)
 // bytes of dynamic shared memory (set once per device before a launch).
 cudaError_t transport_allow_smem();
 __global__ void k_normalise(const NormJob *jobs);

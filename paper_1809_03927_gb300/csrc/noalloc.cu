@@ -223,10 +223,18 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
     const size_t smem = transport_smem(1) + birth_smem(1024);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transport1_r64, 1024, smem);
+    const int spec = transport_spec(&t, 1);      // all physics, HU + table
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, transport_kernel(kLaunchSingle, 1, spec), 1024, smem);
     if (e != cudaSuccess || per_sm <= 0) return fail(DOSE_ECUDA, "transport launch set-up", e);
-    const unsigned chunk = 32;                    // the default launch shape: 1024 threads, chunk 32
-    k_transport1_r64<<<sms * per_sm, 1024, smem, st>>>(t, n_histories, d_counter, d_tab, g_inv_ds, chunk);
+    TransportLaunch L;                            // the default launch shape: 64 registers, 1024 threads, chunk 32
+    L.mode = kLaunchSingle; L.regs = 1; L.spec = spec;
+    L.grid = (unsigned)(sms * per_sm); L.block = 1024; L.smem = smem; L.stream = st;
+    L.job0 = &t; L.d_jobs = nullptr; L.n_jobs = 1;
+    L.total = n_histories; L.counter = d_counter; L.tab = d_tab; L.inv_ds = g_inv_ds;
+    L.chunk = 32; L.stage = 0;
+    e = transport_launch(L);
+    if (e != cudaSuccess) return fail(DOSE_ECUDA, "launch", e);
     k_normalise_hu<<<304, 256, 0, st>>>(tally, d_ledger, hu, d_tab, dose, nvox, n_histories,
                                         (double)dx_mm * dy_mm * dz_mm / 1000.0);
     e = cudaGetLastError();

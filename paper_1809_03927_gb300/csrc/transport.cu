@@ -234,8 +234,15 @@ __device__ __forceinline__ float2 box_muller2(float ua, float ub)
 // size, voxel size, SPR scale, physics, step limit, Philox round keys),
 // which come from P; each step reads only its job's grid, tally and stream
 // from the table.
+//
+// kPhys >= 0 fixes the physics mask at compile time (the job's mask must
+// equal it) and kMat fixes the material source (1: every job has a (rho,
+// SPR) grid; 2: every job reads HU + table); -1 reads them from the job.
+// A fixed value drops the per-step branches on it; the arithmetic, and so
+// every result, is the same.
 enum { kTable = 0, kSingle = 1, kShared = 2 };
-template <int kMode>
+static_assert(kTable == kLaunchTable && kSingle == kLaunchSingle && kShared == kLaunchShared, "launch modes");
+template <int kMode, int kPhys, int kMat>
 __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, const TJob &P, int n_jobs,
                                                unsigned long long total,
                                                unsigned long long *__restrict__ counter,
@@ -428,7 +435,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
         float2 m;
         // the grid is read at random voxels (few L1 hits): through L2 only,
         // so L1 keeps the job descriptors and the HU table
-        if (Jo.matg) {
+        if (kMat == 1 || (kMat < 0 && Jo.matg)) {
             m = __ldcg(Jo.matg + vox);
         } else {
             const int hv = min(max((int)__ldcg(Jo.hu + vox), kHuMin), kHuMax);
@@ -478,7 +485,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
         float E1c = energy_at_range_in(T.er, R0 - sw, inv_ds);
         float Emean = 0.5f * (E + E1c);
         float2 hs = lerp_e_in(T.hs, Emean);
-        const unsigned physics = J.physics;
+        const unsigned physics = kPhys >= 0 ? (unsigned)kPhys : J.physics;
         bool nuclear = false;
         if (physics & 4u) {
             const float tau = hs.y * sw;
@@ -612,63 +619,139 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
 // Two register budgets of the same kernel: up to 128 registers per thread
 // (blocks of at most 512 threads) or 64 (blocks up to 1024 threads, more
 // resident warps).  The autotuner picks; results are equal.  k_transport1*
-// run one job given as a parameter; k_transport* a table of jobs.
+// run one job given as a parameter; k_transportS* a table of jobs whose
+// per-step fields come from the parameter `common`; k_transport* a table.
+// Each comes in the specialisations of transport_spec().
+template <int P, int M>
 __global__ void __launch_bounds__(512, 1)
 k_transport(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
             unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
             unsigned chunk, int stage)
 {
-    transport_body<kTable>(jobs, *jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+    transport_body<kTable, P, M>(jobs, *jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
 }
 
+template <int P, int M>
 __global__ void __launch_bounds__(1024, 1)
 k_transport_r64(const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
                 unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab,
                 float inv_ds, unsigned chunk, int stage)
 {
-    transport_body<kTable>(jobs, *jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+    transport_body<kTable, P, M>(jobs, *jobs, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
 }
 
+template <int P, int M>
 __global__ void __launch_bounds__(512, 1)
 k_transport1(const __grid_constant__ TJob job, unsigned long long total, unsigned long long *__restrict__ counter,
              const Tables *__restrict__ gtab, float inv_ds, unsigned chunk)
 {
-    transport_body<kSingle>(nullptr, job, 1, total, counter, gtab, inv_ds, chunk, 0);
+    transport_body<kSingle, P, M>(nullptr, job, 1, total, counter, gtab, inv_ds, chunk, 0);
 }
 
+template <int P, int M>
 __global__ void __launch_bounds__(1024, 1)
 k_transport1_r64(const __grid_constant__ TJob job, unsigned long long total,
                  unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
                  unsigned chunk)
 {
-    transport_body<kSingle>(nullptr, job, 1, total, counter, gtab, inv_ds, chunk, 0);
+    transport_body<kSingle, P, M>(nullptr, job, 1, total, counter, gtab, inv_ds, chunk, 0);
 }
 
+template <int P, int M>
 __global__ void __launch_bounds__(512, 1)
 k_transportS(const __grid_constant__ TJob common, const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
              unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
              unsigned chunk, int stage)
 {
-    transport_body<kShared>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+    transport_body<kShared, P, M>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
 }
 
+template <int P, int M>
 __global__ void __launch_bounds__(1024, 1)
 k_transportS_r64(const __grid_constant__ TJob common, const TJob *__restrict__ jobs, int n_jobs,
                  unsigned long long total, unsigned long long *__restrict__ counter,
                  const Tables *__restrict__ gtab, float inv_ds, unsigned chunk, int stage)
 {
-    transport_body<kShared>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+    transport_body<kShared, P, M>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+}
+
+namespace {
+// (kPhys, kMat) of each specialisation
+template <int S> struct SpecArgs;
+template <> struct SpecArgs<kSpecGeneric> { static constexpr int P = -1, M = -1; };
+template <> struct SpecArgs<kSpecFullGrid> { static constexpr int P = 7, M = 1; };
+template <> struct SpecArgs<kSpecFullHu> { static constexpr int P = 7, M = 2; };
+
+template <int S>
+const void *kernel_of(int mode, int regs)
+{
+    constexpr int P = SpecArgs<S>::P, M = SpecArgs<S>::M;
+    if (mode == kSingle) return regs ? (const void *)k_transport1_r64<P, M> : (const void *)k_transport1<P, M>;
+    if (mode == kShared) return regs ? (const void *)k_transportS_r64<P, M> : (const void *)k_transportS<P, M>;
+    return regs ? (const void *)k_transport_r64<P, M> : (const void *)k_transport<P, M>;
+}
+
+template <int S>
+void launch_spec(const TransportLaunch &L)
+{
+    constexpr int P = SpecArgs<S>::P, M = SpecArgs<S>::M;
+    const dim3 g(L.grid), b(L.block);
+    if (L.mode == kSingle && L.regs)
+        k_transport1_r64<P, M><<<g, b, L.smem, L.stream>>>(*L.job0, L.total, L.counter, L.tab, L.inv_ds, L.chunk);
+    else if (L.mode == kSingle)
+        k_transport1<P, M><<<g, b, L.smem, L.stream>>>(*L.job0, L.total, L.counter, L.tab, L.inv_ds, L.chunk);
+    else if (L.mode == kShared && L.regs)
+        k_transportS_r64<P, M><<<g, b, L.smem, L.stream>>>(*L.job0, L.d_jobs, L.n_jobs, L.total, L.counter, L.tab,
+                                                            L.inv_ds, L.chunk, L.stage);
+    else if (L.mode == kShared)
+        k_transportS<P, M><<<g, b, L.smem, L.stream>>>(*L.job0, L.d_jobs, L.n_jobs, L.total, L.counter, L.tab,
+                                                        L.inv_ds, L.chunk, L.stage);
+    else if (L.regs)
+        k_transport_r64<P, M><<<g, b, L.smem, L.stream>>>(L.d_jobs, L.n_jobs, L.total, L.counter, L.tab, L.inv_ds,
+                                                           L.chunk, L.stage);
+    else
+        k_transport<P, M><<<g, b, L.smem, L.stream>>>(L.d_jobs, L.n_jobs, L.total, L.counter, L.tab, L.inv_ds,
+                                                       L.chunk, L.stage);
+}
+}  // namespace
+
+int transport_spec(const TJob *jobs, int n)
+{
+    bool full = n > 0, grid = true, hu = true;
+    for (int j = 0; j < n; ++j) {
+        full = full && jobs[j].physics == 7u;
+        grid = grid && jobs[j].matg != nullptr;
+        hu = hu && jobs[j].matg == nullptr;
+    }
+    if (!full) return kSpecGeneric;
+    return grid ? kSpecFullGrid : hu ? kSpecFullHu : kSpecGeneric;
+}
+
+const void *transport_kernel(int mode, int regs, int spec)
+{
+    if (spec == kSpecFullGrid) return kernel_of<kSpecFullGrid>(mode, regs);
+    if (spec == kSpecFullHu) return kernel_of<kSpecFullHu>(mode, regs);
+    return kernel_of<kSpecGeneric>(mode, regs);
+}
+
+cudaError_t transport_launch(const TransportLaunch &L)
+{
+    if (L.spec == kSpecFullGrid) launch_spec<kSpecFullGrid>(L);
+    else if (L.spec == kSpecFullHu) launch_spec<kSpecFullHu>(L);
+    else launch_spec<kSpecGeneric>(L);
+    return cudaGetLastError();
 }
 
 cudaError_t transport_allow_smem()
 {
     const int bytes = (int)(kSmemTransportMax + birth_smem(1024));
-    const void *k[6] = {(const void *)k_transport, (const void *)k_transport_r64, (const void *)k_transport1,
-                        (const void *)k_transport1_r64, (const void *)k_transportS, (const void *)k_transportS_r64};
-    for (const void *f : k) {
-        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-    }
+    for (int spec = 0; spec < 3; ++spec)
+        for (int mode = 0; mode < 3; ++mode)
+            for (int regs = 0; regs < 2; ++regs) {
+                const cudaError_t e = cudaFuncSetAttribute(transport_kernel(mode, regs, spec),
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 
