@@ -427,6 +427,41 @@ def test_ragged_batch_equals_jobs_alone(gpu):
             gpu.dose_destroy(c)
 
 
+def test_specialised_and_generic_builds_agree(gpu):
+    """The transport is built generic and for all-physics jobs with either
+    material source; the launcher picks the build from the jobs.  A job run
+    alone (its specialised build) and the same job in a batch whose jobs
+    mix physics masks and material sources (the generic build) give the
+    same tally bits, as does a batch of only all-physics grid jobs."""
+    rng = np.random.default_rng(17)
+    specs = []   # (phantom, plan, histories, physics, material grid)
+    for side, n, phys, grid in ((32, 60_000, 7, 1), (40, 80_000, 7, 0), (36, 50_000, 3, 1), (32, 40_000, 6, 0)):
+        specs.append((W.random_phantom(rng, side), W.random_plan(rng, int(rng.integers(20, 50)), side * 0.6),
+                      n, phys, grid))
+    alone = [H.gpu_run(gpu, ph, pl, n, 40 + i, physics=phys, options={gpu.DOSE_OPT_MATERIAL_GRID: grid})["tally"]
+             for i, (ph, pl, n, phys, grid) in enumerate(specs)]
+
+    def batch(idx):
+        ctxs = [H.make_ctx(gpu, specs[i][0]) for i in idx]
+        try:
+            for c, i in zip(ctxs, idx):
+                gpu.dose_set_option(c, gpu.DOSE_OPT_PHYSICS, specs[i][3])
+                gpu.dose_set_option(c, gpu.DOSE_OPT_MATERIAL_GRID, specs[i][4])
+                gpu.dose_add_spots(c, gpu.spots_array(specs[i][1]), None)
+            gpu.dose_run_batch(gpu.make_jobs([dict(ctx=c, phase=0, n_histories=specs[i][2], seed=40 + i)
+                                              for c, i in zip(ctxs, idx)]))
+            for c, i in zip(ctxs, idx):
+                t = gpu.dose_read(c, gpu.DOSE_TALLY_I64, 0, np.zeros(specs[i][0].hu.shape, np.uint64))
+                np.testing.assert_array_equal(t, alone[i])
+        finally:
+            for c in ctxs:
+                gpu.dose_destroy(c)
+
+    batch([0, 1, 2, 3])      # mixed masks and sources: the generic build
+    batch([2, 0])            # a partial mask first
+    batch([0, 0])            # all physics, all grids: the specialised table build
+
+
 def test_view_shares_grid(gpu):
     ph = W.slab_phantom(n=32)
     pl = W.slab_plan(n_layers=2, nx=2, ny=2)
