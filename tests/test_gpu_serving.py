@@ -196,7 +196,8 @@ def test_server_rejects_bad_input(gpu):
         D.dose_destroy(base)
 
 
-def test_requests_with_their_own_delivery(gpu):
+@pytest.mark.parametrize("policy", ["fair", "shortest_first"])
+def test_requests_with_their_own_delivery(gpu, policy):
     """Gating and repainting variants served next to nominal requests: each
     request's result equals that request computed alone with its delivery
     (the even split over the phases its delivery reaches)."""
@@ -210,7 +211,8 @@ def test_requests_with_their_own_delivery(gpu):
     late = D.delivery_struct(W.Delivery(**dict(common, gated=1, gate_first=3, gate_last=3, start_phase=0)))
     reqs = [(30_000, 11, None), (20_000, 12, gated), (24_000, 13, repaint), (10_000, 14, None),
             (16_000, 15, gated), (8_000, 16, late)]
-    srv = D.dose_server_create(base, 1 << 34, 25_000, spots, dlv, min_slice=50, max_active=3, nsub=NSUB, dvf=dvf)
+    srv = D.dose_server_create(base, 1 << 34, 25_000, spots, dlv, min_slice=50, max_active=3, nsub=NSUB, dvf=dvf,
+                               policy=D.DOSE_SERVE_FAIR if policy == "fair" else D.DOSE_SERVE_SHORTEST_FIRST)
     out, ids = {}, {}
     try:
         for k, (n, seed, d) in enumerate(reqs):
