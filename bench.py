@@ -70,7 +70,10 @@ def _args():
     p.add_argument("--serve-window", type=float, default=5.0, help="seconds of Poisson arrivals")
     p.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
     p.add_argument("--serve-policies", default="fair,shortest_first",
-                   help="server sharing policies to measure: fair (equal shares) and/or shortest_first")
+                   help="server sharing policies to measure: fair (equal shares), shortest_first, "
+                        "shortest_first_bounded (with --serve-max-wait)")
+    p.add_argument("--serve-max-wait", type=int, default=8,
+                   help="max_wait_steps of the shortest_first_bounded policy")
     p.add_argument("--serve-budget-gb", type=float, default=150.0, help="device memory for request slots")
     p.add_argument("--serve-low-rate", type=float, default=8.0,
                    help="mean arrivals per second of the second serving point (below capacity)")
@@ -570,11 +573,11 @@ def _requests(window_s, rate, seed=5):
         out.append(dict(t=t, n=n, seed=int(rng.integers(1, 2 ** 62)), spr=spr, shift=sh))
 
 
-def _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hist, policy):
+def _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hist, policy, max_wait=0):
     """Replay the arrival schedule through a server with the given sharing
     policy; latency percentiles, throughput and where the makespan went."""
     srv = D.dose_server_create(base, budget_bytes, 40_000_000, spots, dlv, min_slice=20_000,
-                               nsub=(2, 2, 5), dvf=dvf_dev, policy=policy)
+                               nsub=(2, 2, 5), dvf=dvf_dev, policy=policy, max_wait_steps=max_wait)
     done_at, k, t0, ids, max_active = {}, 0, time.perf_counter(), {}, 0
     window_s = reqs[-1]["t"] if reqs else 0.0
     at_window_end = None                      # requests in the system when the last one arrives
@@ -616,7 +619,7 @@ def _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hi
             "histories_per_device_batch_s": hist / tm["batch_s"] if tm["batch_s"] > 0 else None}
 
 
-def _bench_serving(D, torch, stream, window_s, rate, budget_bytes, policies):
+def _bench_serving(D, torch, stream, window_s, rate, budget_bytes, policies, max_wait=8):
     """p50/p99 latency (arrival -> dose ready) and histories/s of the
     continuous-batching server against the plain engine (each request alone,
     one phase job per launch, first come first served) on the same arrival
@@ -657,16 +660,22 @@ def _bench_serving(D, torch, stream, window_s, rate, budget_bytes, policies):
 
         # ---- served: continuous batching, under each sharing policy
         hist = sum(r["n"] // len(phases) * len(phases) for r in reqs)
-        for key, policy in (("served", D.DOSE_SERVE_FAIR), ("served_shortest_first", D.DOSE_SERVE_SHORTEST_FIRST)):
+        for key, policy, wait in (("served", D.DOSE_SERVE_FAIR, 0),
+                                  ("served_shortest_first", D.DOSE_SERVE_SHORTEST_FIRST, 0),
+                                  ("served_shortest_first_bounded", D.DOSE_SERVE_SHORTEST_FIRST, max_wait)):
             if key in policies:
-                out[key] = _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hist, policy)
+                out[key] = _serve_schedule(D, base, spots, dlv, dvf_dev, budget_bytes, reqs, stream, hist, policy,
+                                           wait)
                 out[key]["policy"] = policies[key]
+                if wait:
+                    out[key]["max_wait_steps"] = wait
 
         # capacity: the served rate while the device is busy (histories per
         # second of transport batches); an offered load above it grows the
         # queue, which the records show as requests in the system when the
         # last request arrives
-        rates = [out[k]["histories_per_device_batch_s"] for k in ("served", "served_shortest_first")
+        rates = [out[k]["histories_per_device_batch_s"]
+                 for k in ("served", "served_shortest_first", "served_shortest_first_bounded")
                  if k in out and out[k]["histories_per_device_batch_s"]]
         if rates:
             out["capacity_histories_per_s"] = max(rates)
@@ -872,14 +881,15 @@ def run_engine(args):
     if not args.no_trials:
         line["uncertainty_trials"] = _bench_trials(D, torch, stream, args.histories_trial)
     if not args.no_serve:
-        pol = {"fair": "served", "shortest_first": "served_shortest_first"}
+        pol = {"fair": "served", "shortest_first": "served_shortest_first",
+               "shortest_first_bounded": "served_shortest_first_bounded"}
         policies = {pol[v.strip()]: v.strip() for v in args.serve_policies.split(",") if v.strip()}
         line["serving"] = _bench_serving(D, torch, stream, args.serve_window, args.serve_rate,
-                                         int(args.serve_budget_gb * 1e9), policies)
+                                         int(args.serve_budget_gb * 1e9), policies, args.serve_max_wait)
         if args.serve_low_window > 0:
             line["serving_below_capacity"] = _bench_serving(D, torch, stream, args.serve_low_window,
                                                             args.serve_low_rate, int(args.serve_budget_gb * 1e9),
-                                                            policies)
+                                                            policies, args.serve_max_wait)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _oracle_sample(phantom, plan)
         line["cpu_baseline"].update(_oracle_extra(phantom, plan))

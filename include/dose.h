@@ -293,13 +293,19 @@ typedef struct dose_server_config {
     int32_t accumulate;
     const float *dvf;          /* device, n_phases x 3 x nvox mm, or NULL = identity */
     int32_t policy;            /* DOSE_SERVE_FAIR or DOSE_SERVE_SHORTEST_FIRST */
-    int32_t reserved;          /* 0 */
+    int32_t max_wait_steps;    /* shortest-first: bound on the steps in a row a request goes
+                                  without a slice (0: none) */
 } dose_server_config;
 /* How a step's histories are shared among the active requests: equally
  * (each at least min_slice per phase), or to the requests with the fewest
  * histories left first (the step's budget handed out in that order; a
  * request without a slice waits), which shortens the small requests'
- * latency without stretching the large ones as much as equal shares do.  */
+ * latency without stretching the large ones as much as equal shares do.
+ * Under a sustained overload shortest-first alone can hold a large request
+ * back indefinitely; with max_wait_steps = k > 0 a request that has gone k
+ * steps in a row without a slice is served first at the next step, with
+ * at least min_slice histories per phase even when the step's budget is
+ * spent, so no request waits more than k steps in a row.                  */
 enum { DOSE_SERVE_FAIR = 0, DOSE_SERVE_SHORTEST_FIRST = 1 };
 typedef struct dose_request {
     uint64_t n_histories;

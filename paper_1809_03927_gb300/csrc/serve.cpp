@@ -48,6 +48,7 @@ struct dose_server {
         std::vector<int> phases;       // phases the request's delivery reaches
         uint64_t per_phase;            // histories per phase with protons
         uint64_t next;                 // next history index (same for every phase)
+        uint32_t waited = 0;           // steps in a row without a slice
     };
     dose_ctx *base = nullptr;
     dose_ctx *tmpl = nullptr;          // a view with the plan and the server's delivery loaded
@@ -108,6 +109,7 @@ int dose_server_create(dose_ctx *base, const dose_server_config *cfg, const dose
         return sfail(nullptr, DOSE_EINVAL, "nsub must be positive");
     if (cfg->policy != DOSE_SERVE_FAIR && cfg->policy != DOSE_SERVE_SHORTEST_FIRST)
         return sfail(nullptr, DOSE_EINVAL, "policy must be DOSE_SERVE_FAIR or DOSE_SERVE_SHORTEST_FIRST");
+    if (cfg->max_wait_steps < 0) return sfail(nullptr, DOSE_EINVAL, "max_wait_steps must be 0 or positive");
     dose_server *s = new dose_server;
     s->base = base;
     s->cfg = *cfg;
@@ -234,8 +236,9 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
             if (cudaEventCreate(&e) != cudaSuccess) return sfail(s, DOSE_ECUDA, "cudaEventCreate failed");
     // the step's histories: an equal share for every active request, or
     // (DOSE_SERVE_SHORTEST_FIRST) the budget handed out in order of the
-    // histories each request has left, fewest first; a request left
-    // without a slice waits for the next step.  At least min_slice
+    // histories each request has left, fewest first, after the requests
+    // that have waited max_wait_steps; a request left without a slice
+    // waits for the next step.  At least min_slice
     // histories per phase, so every slice makes progress.
     size_t phase_jobs = 0;
     for (const auto &a : s->active) phase_jobs += a.phases.size();
@@ -248,11 +251,18 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
             const auto &a = s->active[i];
             return (a.per_phase - a.next) * (uint64_t)a.phases.size();
         };
-        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return left(x) < left(y); });
+        // a request that has waited max_wait_steps steps goes first and
+        // gets at least min_slice even when the budget is spent
+        const uint32_t bound = (uint32_t)s->cfg.max_wait_steps;
+        auto overdue = [&](size_t i) { return bound > 0 && s->active[i].waited >= bound; };
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+            const bool ox = overdue(x), oy = overdue(y);
+            return ox != oy ? ox : left(x) < left(y);
+        });
         uint64_t budget = s->cfg.step_histories;
         for (size_t i : order) {
             const auto &a = s->active[i];
-            if (a.phases.empty() || budget == 0) continue;
+            if (a.phases.empty() || (budget == 0 && !overdue(i))) continue;
             const uint64_t nph = a.phases.size();
             const uint64_t t = std::min(a.per_phase - a.next, std::max(min_slice, budget / nph));
             take[i] = t;
@@ -271,7 +281,11 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
             finishing.push_back((int)i);
             continue;
         }
-        if (take[i] == 0) continue;                  // waits for a later step
+        if (take[i] == 0) {                          // waits for a later step
+            ++a.waited;
+            continue;
+        }
+        a.waited = 0;
         const uint64_t end = a.next + take[i];
         for (int p : a.phases) {
             dose_job j;

@@ -71,7 +71,7 @@ class dose_server_config(C.Structure):
     _fields_ = [("memory_budget_bytes", C.c_uint64), ("step_histories", C.c_uint64),
                 ("min_slice", C.c_uint64), ("max_active", C.c_int32), ("ref_phase", C.c_int32),
                 ("nsub", C.c_int32 * 3), ("accumulate", C.c_int32), ("dvf", C.c_void_p),
-                ("policy", C.c_int32), ("reserved", C.c_int32)]
+                ("policy", C.c_int32), ("max_wait_steps", C.c_int32)]
 
 
 class dose_request(C.Structure):
@@ -385,14 +385,16 @@ def dose_run_phase_noalloc(hu, nx, ny, nz, dx_mm, dy_mm, dz_mm, origin_mm, beam_
 
 def dose_server_create(base, memory_budget_bytes, step_histories, spots, delivery=None,
                        min_slice=0, max_active=0, ref_phase=0, nsub=(2, 2, 5), accumulate=1,
-                       dvf=None, policy=0):
+                       dvf=None, policy=0, max_wait_steps=0):
     """``dvf``: device tensor (n_phases x 3 x nvox) or None (identity);
-    ``policy``: DOSE_SERVE_FAIR (0) or DOSE_SERVE_SHORTEST_FIRST (1)."""
+    ``policy``: DOSE_SERVE_FAIR (0) or DOSE_SERVE_SHORTEST_FIRST (1);
+    ``max_wait_steps``: shortest-first's bound on steps in a row without a
+    slice (0: none)."""
     cfg = dose_server_config()
     cfg.memory_budget_bytes, cfg.step_histories, cfg.min_slice = (
         int(memory_budget_bytes), int(step_histories), int(min_slice))
     cfg.max_active, cfg.ref_phase, cfg.accumulate = int(max_active), int(ref_phase), int(accumulate)
-    cfg.policy = int(policy)
+    cfg.policy, cfg.max_wait_steps = int(policy), int(max_wait_steps)
     cfg.nsub[:] = [int(v) for v in nsub]
     if dvf is not None:
         p, dev = _ptr(dvf)

@@ -76,4 +76,8 @@ def test_structs_match_the_header(libdose):
     assert C.sizeof(D.dose_delivery_spread) == 9 * 8
     assert C.sizeof(D.dose_dvf_grid) == 3 * 4 + 4 * 3 * 4 + 2 * 16 * 4
     assert C.sizeof(D.dose_job) == 64
+    assert C.sizeof(D.dose_server_config) == 64
+    assert D.dose_server_config.dvf.offset == 48 and D.dose_server_config.policy.offset == 56
+    assert D.dose_server_config.max_wait_steps.offset == 60
+    assert (D.DOSE_SERVE_FAIR, D.DOSE_SERVE_SHORTEST_FIRST) == (0, 1)
     assert D.dose_job.shift_mm.offset == 52

@@ -36,7 +36,7 @@ def _serve(D, base, spots, dlv, dvf, arrivals, shape, **kw):
     """Serve REQUESTS; request k is submitted before step arrivals[k]."""
     srv = D.dose_server_create(base, 1 << 34, kw.get("step", 30_000), spots, dlv, min_slice=kw.get("min_slice", 50),
                                max_active=kw.get("max_active", 0), nsub=NSUB, dvf=dvf,
-                               policy=kw.get("policy", D.DOSE_SERVE_FAIR))
+                               policy=kw.get("policy", D.DOSE_SERVE_FAIR), max_wait_steps=kw.get("max_wait", 0))
     out, ids, done_step, step, pending = {}, {}, {}, 0, list(range(len(REQUESTS)))
     try:
         while len(out) < len(REQUESTS):
@@ -108,6 +108,61 @@ def test_shortest_first_finishes_small_requests_first(gpu):
         assert max(srpt["done_step"].values()) <= max(fair["done_step"].values())
         for k in by_size[:-1]:
             assert srpt["done_step"][k] <= fair["done_step"][k]
+    finally:
+        D.dose_destroy(base)
+
+
+def _completion_steps(sizes, nph, step, min_slice, bound):
+    """Completion step of each request (all submitted before step 0) under
+    shortest-first with a wait bound, from the policy's definition: requests
+    that have waited `bound` steps first, then fewest histories left (ties
+    in submission order); each takes min(left per phase, max(min_slice,
+    budget // nph)) per phase while budget remains, an overdue one at least
+    min(left, min_slice) after it is spent."""
+    per = [n // nph for n in sizes]
+    nxt, waited, done, st = [0] * len(sizes), [0] * len(sizes), {}, 0
+    while len(done) < len(sizes):
+        act = [i for i in range(len(sizes)) if i not in done]
+        over = {i: bound > 0 and waited[i] >= bound for i in act}
+        order = sorted(act, key=lambda i: (0 if over[i] else 1, (per[i] - nxt[i]) * nph))
+        budget, take = step, {}
+        for i in order:
+            if budget == 0 and not over[i]:
+                take[i] = 0
+                continue
+            take[i] = min(per[i] - nxt[i], max(min_slice, budget // nph))
+            budget = max(0, budget - take[i] * nph)
+        for i in act:
+            waited[i] = waited[i] + 1 if take[i] == 0 else 0
+            nxt[i] += take[i]
+            if nxt[i] == per[i]:
+                done[i] = st
+        st += 1
+    return done
+
+
+def test_shortest_first_wait_bound(gpu):
+    """With max_wait_steps the largest request is not held back until the
+    others finish: the completion steps follow the policy's definition for
+    the bound (computed here from it) and differ from those without one."""
+    D = gpu
+    ph, dvf, spots, dlv, base = _setup(D)
+    shape = ph.hu.shape[1:]
+    sizes = [r[0] for r in REQUESTS]
+    try:
+        got = {}
+        for bound in (0, 1):
+            _, st = _serve(D, base, spots, dlv, dvf, [0] * len(REQUESTS), shape,
+                           policy=D.DOSE_SERVE_SHORTEST_FIRST, max_wait=bound)
+            nph = [k for k in range(1, 5) if sum(n // k * k for n in sizes) == st["histories"]]
+            assert len(nph) >= 1
+            want = _completion_steps(sizes, nph[0], 30_000, 50, bound)
+            assert st["done_step"] == want, (bound, st["done_step"], want)
+            got[bound] = st["done_step"]
+        assert got[0] != got[1]
+        with pytest.raises(D.DoseError):
+            D.dose_server_create(base, 1 << 34, 30_000, spots, dlv, dvf=dvf,
+                                 policy=D.DOSE_SERVE_SHORTEST_FIRST, max_wait_steps=-1)
     finally:
         D.dose_destroy(base)
 
