@@ -335,6 +335,34 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed, small=False):
             torch.cuda.synchronize()
             walls.append(time.perf_counter() - t0)
             evs.append(e0.elapsed_time(e1) / 1e3)
+        acc_batched = D.dose_read(ctx, D.DOSE_ACCUM, 0, np.zeros((nz, ny, nx), np.float32))
+
+        # the plain engine: the same plan and histories, one phase job per
+        # launch (each phase's allocation, transport and normalisation), then
+        # the same accumulation; phase doses and the accumulated dose are the
+        # same bits as the batched plan's (histories are keyed by seed,
+        # history and phase)
+        zero = torch.zeros(nx * ny * nz, dtype=torch.float32, device="cuda")
+
+        def plan_plain():
+            D.dose_add_spots(ctx, spots, dlv, stream)
+            for p in range(ph.n_phases):
+                if phase_p[p] > 0:
+                    D.dose_run_phase(ctx, p, n_per_phase, seed, 1.0, None, stream)
+                else:
+                    D.dose_set_phase_dose(ctx, p, zero, stream)
+            D.dose_accumulate_subvoxel(ctx, 0, (2, 2, 5), dvf=dvf_dev, stream=stream)
+
+        plain_walls = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan_plain()
+            torch.cuda.synchronize()
+            plain_walls.append(time.perf_counter() - t0)
+        plain_same = bool(np.array_equal(D.dose_read(ctx, D.DOSE_ACCUM, 0, np.zeros((nz, ny, nx), np.float32)),
+                                         acc_batched))
+        del zero
         # the accumulation alone
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -383,6 +411,7 @@ def _bench_4d(D, torch, stream, n_per_phase, reps, seed, small=False):
         D.dose_destroy(ctx)
     s_plan = float(np.median(walls))
     return {"s_per_plan": s_plan, "s_per_plan_device": float(np.median(evs)), "reps": reps,
+            "plain_s_per_plan": float(np.median(plain_walls)), "plain_same_dose": plain_same,
             "histories_per_plan": n_run, "histories_per_s": n_run / s_plan,
             "steps_per_history": steps / n_run, "emtm_s": emtm_s,
             "emtm_subvoxels": int(stats[0]), "emtm_atomic_pairs": int(stats[2]),
