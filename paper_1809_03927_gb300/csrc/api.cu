@@ -957,7 +957,16 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         // table in device memory
         // a table whose jobs share their per-step fields (the phases of one
         // plan and seed) reads those from the launch's parameters too
-        const bool single = tj.size() == 1;
+        // jobs that each fill the GPU many times over (kSplitWork work items)
+        // run one after another as single-job launches, whose descriptor
+        // sits in the launch parameters (the cheapest step); the per-launch
+        // tail is a few tens of microseconds against their seconds
+        auto job_work = [&](size_t j) {
+            return (j + 1 < tj.size() ? tj[j + 1].work_begin : work) - tj[j].work_begin;
+        };
+        bool split = tj.size() > 1;
+        for (size_t j = 0; j < tj.size() && split; ++j) split = job_work(j) >= kSplitWork;
+        const bool single = tj.size() == 1 || split;
         const bool shared = !single && jobs_share_step_fields(tj.data(), (int)tj.size());
         if (!single)
             CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
@@ -993,17 +1002,31 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         if (per_sm <= 0) per_sm = fit;
         if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
         const unsigned long long warps = (unsigned long long)sms * per_sm * (c0->block / 32);
-        unsigned chunk = c0->chunk;
         // keep at least ~4 pulls per warp so the tail stays short
-        while (chunk > 32 && (unsigned long long)chunk * warps * 4 > work) chunk >>= 1;
-        const unsigned grid = (unsigned)(sms * per_sm);
+        auto chunk_for = [&](unsigned long long n) {
+            unsigned chunk = c0->chunk;
+            while (chunk > 32 && (unsigned long long)chunk * warps * 4 > n) chunk >>= 1;
+            return chunk;
+        };
         TransportLaunch L;
         L.mode = mode; L.regs = c0->regs; L.spec = spec;
-        L.grid = grid; L.block = (unsigned)c0->block; L.smem = smem; L.stream = st;
+        L.grid = (unsigned)(sms * per_sm); L.block = (unsigned)c0->block; L.smem = smem; L.stream = st;
         L.job0 = &tj[0]; L.d_jobs = c0->d_jobs; L.n_jobs = (int)tj.size();
         L.total = work; L.counter = c0->d_counter; L.tab = tab.dev; L.inv_ds = tab.inv_ds;
-        L.chunk = chunk; L.stage = stage;
-        CK(c0, transport_launch(L));
+        L.chunk = chunk_for(work); L.stage = stage;
+        if (!split) {
+            CK(c0, transport_launch(L));
+        } else {
+            for (size_t j = 0; j < tj.size(); ++j) {
+                TJob t = tj[j];                           // copied into the launch's parameters
+                const unsigned long long n = job_work(j);
+                t.work_begin = 0;
+                if (j) CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
+                L.job0 = &t; L.n_jobs = 1; L.total = n; L.chunk = chunk_for(n);
+                L.spec = transport_spec(&t, 1);
+                CK(c0, transport_launch(L));
+            }
+        }
     }
     if (!nj.empty()) {
         CK(c0, cudaMemcpyAsync(c0->d_norm, nj.data(), nj.size() * sizeof(NormJob), cudaMemcpyHostToDevice, st));

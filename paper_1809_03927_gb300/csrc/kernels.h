@@ -57,6 +57,9 @@ struct TransportLaunch {
     unsigned chunk;
     int stage;
 };
+// A batch whose jobs all have at least this many work items runs them as
+// consecutive single-job launches instead of one table launch.
+constexpr unsigned long long kSplitWork = 1ull << 22;
 // The most specialised kernel every job of the launch satisfies.
 int transport_spec(const TJob *jobs, int n);
 const void *transport_kernel(int mode, int regs, int spec);

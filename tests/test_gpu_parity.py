@@ -462,6 +462,38 @@ def test_specialised_and_generic_builds_agree(gpu):
     batch([0, 0])            # all physics, all grids: the specialised table build
 
 
+def test_batch_of_large_jobs_equals_jobs_alone(gpu):
+    """Jobs of at least 2^22 histories each run as consecutive single-job
+    launches within the batch (each with its own work counter); the tallies
+    are those of the jobs run alone, including a job that is a later slice
+    of a run (its history range starts past zero)."""
+    ph = W.water_phantom(24, 24, 60)
+    pl = W.pencil_plan(120.0, 3.0)
+    n = 1 << 22
+    alone = [H.gpu_run(gpu, ph, pl, n, 60 + i, physics=7 if i else 3)["tally"] for i in range(2)]
+    ctxs = [H.make_ctx(gpu, ph) for _ in range(3)]
+    try:
+        for i, c in enumerate(ctxs):
+            gpu.dose_set_option(c, gpu.DOSE_OPT_PHYSICS, 3 if i == 0 else 7)
+            gpu.dose_add_spots(c, gpu.spots_array(pl), None)
+        # ctx 2: the second run in two slices, the first alone, the second in the batch
+        gpu.dose_run_batch(gpu.make_jobs([dict(ctx=ctxs[2], phase=0, n_histories=2 * n, seed=61,
+                                               hist_begin=0, hist_end=n, flags=gpu.DOSE_JOB_CLEAR)]))
+        gpu.dose_run_batch(gpu.make_jobs([dict(ctx=ctxs[0], phase=0, n_histories=n, seed=60),
+                                          dict(ctx=ctxs[1], phase=0, n_histories=n, seed=61),
+                                          dict(ctx=ctxs[2], phase=0, n_histories=2 * n, seed=61,
+                                               hist_begin=n, hist_end=2 * n, flags=gpu.DOSE_JOB_FINISH)]))
+        for i in range(2):
+            t = gpu.dose_read(ctxs[i], gpu.DOSE_TALLY_I64, 0, np.zeros(ph.hu.shape, np.uint64))
+            np.testing.assert_array_equal(t, alone[i])
+        whole = H.gpu_run(gpu, ph, pl, 2 * n, 61)["tally"]
+        t = gpu.dose_read(ctxs[2], gpu.DOSE_TALLY_I64, 0, np.zeros(ph.hu.shape, np.uint64))
+        np.testing.assert_array_equal(t, whole)
+    finally:
+        for c in ctxs:
+            gpu.dose_destroy(c)
+
+
 def test_view_shares_grid(gpu):
     ph = W.slab_phantom(n=32)
     pl = W.slab_plan(n_layers=2, nx=2, ny=2)
