@@ -957,10 +957,10 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         // table in device memory
         // a table whose jobs share their per-step fields (the phases of one
         // plan and seed) reads those from the launch's parameters too
-        // jobs that each fill the GPU many times over (kSplitWork work items)
-        // run one after another as single-job launches, whose descriptor
-        // sits in the launch parameters (the cheapest step); the per-launch
-        // tail is a few tens of microseconds against their seconds
+        // jobs that each keep the GPU busy for tens of milliseconds or more
+        // (kSplitWork work items) run one after another as single-job
+        // launches, whose descriptor sits in the launch parameters (the
+        // cheapest step)
         auto job_work = [&](size_t j) {
             return (j + 1 < tj.size() ? tj[j + 1].work_begin : work) - tj[j].work_begin;
         };

@@ -58,8 +58,11 @@ struct TransportLaunch {
     int stage;
 };
 // A batch whose jobs all have at least this many work items runs them as
-// consecutive single-job launches instead of one table launch.
-constexpr unsigned long long kSplitWork = 1ull << 22;
+// consecutive single-job launches instead of one table launch: the
+// single-job step is a few per cent cheaper, and a launch's tail (its
+// longest histories finishing on a part-idle GPU) costs about 0.7 ms, so
+// the split pays only for jobs of tens of milliseconds and more.
+constexpr unsigned long long kSplitWork = 1ull << 25;
 // The most specialised kernel every job of the launch satisfies.
 int transport_spec(const TJob *jobs, int n);
 const void *transport_kernel(int mode, int regs, int spec);

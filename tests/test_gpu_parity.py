@@ -463,13 +463,13 @@ def test_specialised_and_generic_builds_agree(gpu):
 
 
 def test_batch_of_large_jobs_equals_jobs_alone(gpu):
-    """Jobs of at least 2^22 histories each run as consecutive single-job
+    """Jobs of at least 2^25 histories each run as consecutive single-job
     launches within the batch (each with its own work counter); the tallies
     are those of the jobs run alone, including a job that is a later slice
     of a run (its history range starts past zero)."""
     ph = W.water_phantom(24, 24, 60)
     pl = W.pencil_plan(120.0, 3.0)
-    n = 1 << 22
+    n = 1 << 25
     alone = [H.gpu_run(gpu, ph, pl, n, 60 + i, physics=7 if i else 3)["tally"] for i in range(2)]
     ctxs = [H.make_ctx(gpu, ph) for _ in range(3)]
     try:
