@@ -238,8 +238,8 @@ int dose_server_step(dose_server *s, void *stream, int64_t *completed, int max_c
     // (DOSE_SERVE_SHORTEST_FIRST) the budget handed out in order of the
     // histories each request has left, fewest first, after the requests
     // that have waited max_wait_steps; a request left without a slice
-    // waits for the next step.  At least min_slice
-    // histories per phase, so every slice makes progress.
+    // waits for the next step.  A slice has at least min_slice histories
+    // per phase, so every slice makes progress.
     size_t phase_jobs = 0;
     for (const auto &a : s->active) phase_jobs += a.phases.size();
     const uint64_t min_slice = s->cfg.min_slice ? s->cfg.min_slice : 1;
