@@ -637,7 +637,7 @@ int ensure_material(dose_ctx *c, cudaStream_t st)
     std::lock_guard<std::mutex> lock(g.mat_mutex);
     if (g.mat) return DOSE_OK;
     const size_t n_all = (size_t)g.nvox * g.n_phases;
-    cudaError_t e = cudaMalloc(&g.mat, n_all * sizeof(float2));
+    cudaError_t e = block_alloc(reinterpret_cast<void **>(&g.mat), n_all * sizeof(float2));
     if (e != cudaSuccess) {
         cudaGetLastError();
         g.mat = nullptr;
@@ -1566,7 +1566,7 @@ void dose_destroy(dose_ctx *c)
         const size_t n_all = (size_t)c->g->nvox * c->g->n_phases;
         block_release(c->g->hu, n_all * sizeof(int16_t));
         block_release(c->g->rho, n_all * sizeof(float));
-        if (c->g->mat) cudaFree(c->g->mat);
+        block_release(c->g->mat, n_all * sizeof(float2));
         delete c->g;
     }
     delete c;
