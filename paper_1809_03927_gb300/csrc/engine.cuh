@@ -76,9 +76,33 @@ struct alignas(16) TJob {
     float o[3];                         // patient->grid offsets per axis (origin + shift)
     int beam_axis, beam_sign;
     unsigned key0, key1, stream;
+    unsigned spread_log2;               // work items spread over 2^spread_log2 strides (see spread_history)
     unsigned long long hist_begin;      // first history of this slice
     unsigned long long work_begin;      // offset in the launch's work index
+    unsigned long long n_work;          // work items (histories) of this slice
 };
+static_assert(sizeof(TJob) == 256, "job descriptor: 256 bytes");
+
+// The order in which a job's histories are born: work item w of n goes to
+// history spread_history(w, n, s), a bijection of [0, n) that deals the
+// work items round-robin over 2^s contiguous strides of the history range
+// (stride k holds n / 2^s histories, one more for the first n mod 2^s).
+// Consecutive work items, and so the histories in flight at any moment,
+// then come from 2^s places of the plan instead of a few neighbouring
+// spots, whose tracks would overlap and pile their tally atomics onto the
+// same voxels.  A history's result depends only on its index, so the order
+// changes no tally bit.  s = 0 is the identity.
+__host__ __device__ inline unsigned long long spread_history(unsigned long long w, unsigned long long n, unsigned s)
+{
+    const unsigned long long m = (1ull << s) - 1, q = n >> s, r = n & m, k = w & m;
+    return k * q + (k < r ? k : r) + (w >> s);
+}
+// Grids whose tally and material grid (16 bytes a voxel) fit this budget
+// of the L2 take 64 strides; larger grids keep plan order, whose few
+// neighbouring spots keep the L2 working set small.
+constexpr unsigned kSpreadLog2 = 6;
+constexpr unsigned long long kSpreadGridBytes = 48ull << 20;
+inline unsigned spread_for(long long nvox) { return (unsigned long long)nvox * 16 <= kSpreadGridBytes ? kSpreadLog2 : 0; }
 
 // The fields every step reads that jobs of one context and seed share;
 // they precede the per-job pointers (no padding: all 4-byte scalars and

@@ -343,7 +343,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
                     }
                     const TJob &J = own_of(lo);
                     bjob = lo;
-                    bh = J.hist_begin + (w - J.work_begin);
+                    bh = J.hist_begin + spread_history(w - J.work_begin, J.n_work, J.spread_log2);
                     const int S = J.n_spots;
                     const unsigned long long *prefix = J.prefix;
                     if (bh < prefix[S]) {
