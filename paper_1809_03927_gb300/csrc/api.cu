@@ -953,80 +953,81 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
         CK(c0, cudaGetLastError());
     }
     if (work) {
-        // one job: its descriptor goes in the launch's parameters; several: a
-        // table in device memory
-        // a table whose jobs share their per-step fields (the phases of one
-        // plan and seed) reads those from the launch's parameters too
-        // jobs that each keep the GPU busy for tens of milliseconds or more
-        // (kSplitWork work items) run one after another as single-job
-        // launches, whose descriptor sits in the launch parameters (the
-        // cheapest step)
-        auto job_work = [&](size_t j) {
-            return (j + 1 < tj.size() ? tj[j + 1].work_begin : work) - tj[j].work_begin;
-        };
-        bool split = tj.size() > 1;
-        for (size_t j = 0; j < tj.size() && split; ++j) split = job_work(j) >= kSplitWork;
-        const bool single = tj.size() == 1 || split;
-        const bool shared = !single && jobs_share_step_fields(tj.data(), (int)tj.size());
-        if (!single)
-            CK(c0, cudaMemcpyAsync(c0->d_jobs, tj.data(), tj.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
-        CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
-        const int mode = single ? kLaunchSingle : shared ? kLaunchShared : kLaunchTable;
-        const int spec = transport_spec(tj.data(), (int)tj.size());
-        const void *kern = transport_kernel(mode, c0->regs, spec);
         if (!c0->regs && c0->block > 512)
             return fail(c0, DOSE_EINVAL, "block %d needs the 64-register variant (DOSE_OPT_REGISTERS 1)", c0->block);
         CK(c0, transport_allow_smem());
         int sms = 0;
         CK(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->g->device));
-        size_t smem;
-        int stage = 0, fit = 0;
-        if (single) {
-            smem = transport_smem(1) + birth_smem(c0->block);
-            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, c0->block, smem));
-        } else {
-            // stage the job table in shared memory unless that costs resident
-            // blocks or leaves too little L1 (kStageSmemCap)
-            const size_t smem_plain = transport_smem(kMaxStagedJobs + 1) + birth_smem(c0->block);
-            int fit_plain = 0, fit_staged = 0;
-            CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_plain, kern, c0->block, smem_plain));
-            if ((int)tj.size() <= kMaxStagedJobs)
-                CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_staged, kern, c0->block,
-                                                                     transport_smem((int)tj.size()) + birth_smem(c0->block)));
-            stage = fit_staged > 0 && fit_staged >= fit_plain &&
-                    transport_smem((int)tj.size()) + birth_smem(c0->block) <= kStageSmemCap ? 1 : 0;
-            smem = stage ? transport_smem((int)tj.size()) + birth_smem(c0->block) : smem_plain;
-            fit = stage ? fit_staged : fit_plain;
-        }
-        int per_sm = c0->blocks_per_sm;
-        if (per_sm <= 0) per_sm = fit;
-        if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
-        const unsigned long long warps = (unsigned long long)sms * per_sm * (c0->block / 32);
-        // keep at least ~4 pulls per warp so the tail stays short
-        auto chunk_for = [&](unsigned long long n) {
+        // One launch over a group of jobs whose work items are numbered
+        // contiguously from 0.  One job: its descriptor goes in the launch's
+        // parameters; several: a table in device memory; a table whose jobs
+        // share their per-step fields (the phases of one plan and seed) reads
+        // those from the launch's parameters too.
+        auto launch_group = [&](const std::vector<TJob> &grp, unsigned long long gwork) -> int {
+            const bool single = grp.size() == 1;
+            const bool shared = !single && jobs_share_step_fields(grp.data(), (int)grp.size());
+            if (!single)
+                CK(c0, cudaMemcpyAsync(c0->d_jobs, grp.data(), grp.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
+            CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
+            const int mode = single ? kLaunchSingle : shared ? kLaunchShared : kLaunchTable;
+            const int spec = transport_spec(grp.data(), (int)grp.size());
+            const void *kern = transport_kernel(mode, c0->regs, spec);
+            size_t smem;
+            int stage = 0, fit = 0;
+            if (single) {
+                smem = transport_smem(1) + birth_smem(c0->block);
+                CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, c0->block, smem));
+            } else {
+                // stage the job table in shared memory unless that costs
+                // resident blocks or leaves too little L1 (kStageSmemCap)
+                const int n = (int)grp.size();
+                const size_t smem_plain = transport_smem(kMaxStagedJobs + 1) + birth_smem(c0->block);
+                int fit_plain = 0, fit_staged = 0;
+                CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_plain, kern, c0->block, smem_plain));
+                if (n <= kMaxStagedJobs)
+                    CK(c0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_staged, kern, c0->block,
+                                                                         transport_smem(n) + birth_smem(c0->block)));
+                stage = fit_staged > 0 && fit_staged >= fit_plain &&
+                        transport_smem(n) + birth_smem(c0->block) <= kStageSmemCap ? 1 : 0;
+                smem = stage ? transport_smem(n) + birth_smem(c0->block) : smem_plain;
+                fit = stage ? fit_staged : fit_plain;
+            }
+            int per_sm = c0->blocks_per_sm;
+            if (per_sm <= 0) per_sm = fit;
+            if (per_sm <= 0) return fail(c0, DOSE_ECUDA, "transport kernel does not fit with block %d", c0->block);
+            const unsigned long long warps = (unsigned long long)sms * per_sm * (c0->block / 32);
+            // keep at least ~4 pulls per warp so the tail stays short
             unsigned chunk = c0->chunk;
-            while (chunk > 32 && (unsigned long long)chunk * warps * 4 > n) chunk >>= 1;
-            return chunk;
-        };
-        TransportLaunch L;
-        L.mode = mode; L.regs = c0->regs; L.spec = spec;
-        L.grid = (unsigned)(sms * per_sm); L.block = (unsigned)c0->block; L.smem = smem; L.stream = st;
-        L.job0 = &tj[0]; L.d_jobs = c0->d_jobs; L.n_jobs = (int)tj.size();
-        L.total = work; L.counter = c0->d_counter; L.tab = tab.dev; L.inv_ds = tab.inv_ds;
-        L.chunk = chunk_for(work); L.stage = stage;
-        if (!split) {
+            while (chunk > 32 && (unsigned long long)chunk * warps * 4 > gwork) chunk >>= 1;
+            TransportLaunch L;
+            L.mode = mode; L.regs = c0->regs; L.spec = spec;
+            L.grid = (unsigned)(sms * per_sm); L.block = (unsigned)c0->block; L.smem = smem; L.stream = st;
+            L.job0 = grp.data(); L.d_jobs = c0->d_jobs; L.n_jobs = (int)grp.size();
+            L.total = gwork; L.counter = c0->d_counter; L.tab = tab.dev; L.inv_ds = tab.inv_ds;
+            L.chunk = chunk; L.stage = stage;
             CK(c0, transport_launch(L));
-        } else {
-            for (size_t j = 0; j < tj.size(); ++j) {
-                TJob t = tj[j];                           // copied into the launch's parameters
-                const unsigned long long n = job_work(j);
+            return DOSE_OK;
+        };
+        // Jobs that each keep the GPU busy for tens of milliseconds or more
+        // (kSplitWork work items) run one after another as single-job
+        // launches, the cheapest step; the others share one launch, where
+        // the per-launch tail is paid once.
+        std::vector<TJob> rest, big;
+        unsigned long long rest_work = 0;
+        for (const TJob &t0 : tj) {
+            TJob t = t0;
+            if (tj.size() > 1 && t.n_work >= kSplitWork) {
                 t.work_begin = 0;
-                if (j) CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
-                L.job0 = &t; L.n_jobs = 1; L.total = n; L.chunk = chunk_for(n);
-                L.spec = transport_spec(&t, 1);
-                CK(c0, transport_launch(L));
+                big.push_back(t);
+            } else {
+                t.work_begin = rest_work;
+                rest_work += t.n_work;
+                rest.push_back(t);
             }
         }
+        if (!rest.empty() && (rc = launch_group(rest, rest_work))) return rc;
+        for (const TJob &t : big)
+            if ((rc = launch_group(std::vector<TJob>{t}, t.n_work))) return rc;
     }
     if (!nj.empty()) {
         CK(c0, cudaMemcpyAsync(c0->d_norm, nj.data(), nj.size() * sizeof(NormJob), cudaMemcpyHostToDevice, st));
