@@ -1556,6 +1556,13 @@ int dose_debug_tables(const float *E, int n, float *out, void *stream)
     return DOSE_OK;
 }
 
+int dose_debug_spread(uint64_t n, uint32_t log2_strides, uint64_t *out)
+{
+    if (!out || n > (1ull << 26) || log2_strides > 16) return fail(nullptr, DOSE_EINVAL, "bad arguments");
+    for (uint64_t w = 0; w < n; ++w) out[w] = spread_history(w, n, log2_strides);
+    return DOSE_OK;
+}
+
 void dose_destroy(dose_ctx *c)
 {
     if (!c) return;

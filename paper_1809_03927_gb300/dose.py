@@ -127,6 +127,7 @@ def _load():
         "dose_measure_peaks": ([P, P], I),
         "dose_autotune_batch": ([P, I, U64, P, P], I),
         "dose_server_timing": ([P, P], I),
+        "dose_debug_spread": ([U64, C.c_uint32, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -482,6 +483,14 @@ def dose_debug_tables(energies):
     e = np.ascontiguousarray(energies, np.float32)
     out = np.zeros((e.shape[0], 5), np.float32)
     _check(_lib.dose_debug_tables(e.ctypes.data, e.shape[0], out.ctypes.data, None))
+    return out
+
+
+def dose_debug_spread(n, log2_strides):
+    """History index of each of a job's n work items in the transport's
+    birth order over 2^log2_strides strides (host arithmetic only)."""
+    out = np.zeros(int(n), np.uint64)
+    _check(_lib.dose_debug_spread(int(n), int(log2_strides), out.ctypes.data), None)
     return out
 
 

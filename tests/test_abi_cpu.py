@@ -81,3 +81,31 @@ def test_structs_match_the_header(libdose):
     assert D.dose_server_config.max_wait_steps.offset == 60
     assert (D.DOSE_SERVE_FAIR, D.DOSE_SERVE_SHORTEST_FIRST) == (0, 1)
     assert D.dose_job.shift_mm.offset == 52
+
+
+def test_birth_order_is_a_round_robin_bijection(libdose):
+    """The order in which a job's histories are born (host arithmetic, no
+    device): every history exactly once; with 2^s strides, work item w goes
+    to stride w mod 2^s, and inside each stride the histories follow one
+    another; the strides tile the range in order, the first n mod 2^s one
+    history longer; s = 0 and n < 2^s are plan order."""
+    D = libdose
+    for n in (0, 1, 5, 63, 64, 65, 1000, 4097, 100_003):
+        for s in (0, 1, 4, 6):
+            h = D.dose_debug_spread(n, s)
+            assert np.array_equal(np.sort(h), np.arange(n, dtype=np.uint64))
+            K = 1 << s
+            if s == 0 or n <= K:
+                assert np.array_equal(h, np.arange(n, dtype=np.uint64))
+                continue
+            starts = []
+            for k in range(K):
+                mine = h[k::K].astype(np.int64)
+                assert np.all(np.diff(mine) == 1)              # consecutive inside a stride
+                assert len(mine) == n // K + (1 if k < n % K else 0)
+                starts.append(int(mine[0]))
+            lengths = [n // K + (1 if k < n % K else 0) for k in range(K)]
+            assert starts == list(np.cumsum([0] + lengths[:-1]))
+    with pytest.raises(D.DoseError):
+        D.dose_debug_spread(10, 17)
+
