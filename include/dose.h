@@ -238,8 +238,11 @@ int dose_run_phase(dose_ctx *c, int phase, uint64_t n_histories, uint64_t seed,
  * runs histories [hist_begin, hist_end) of an n_histories-history run of
  * (ctx, phase); DOSE_JOB_CLEAR zeroes the job's tally and allocates its
  * histories first, DOSE_JOB_FINISH normalises the tally to dose after the
- * launch.  Splitting a run into slices over several batches gives the same
- * bits as one call.  All contexts must live on the same GPU.              */
+ * launch.  Jobs of 2^25 histories or more run in single-job launches of
+ * their own, one after another on the stream, after the launch shared by
+ * the others.  Splitting a run into slices over several batches gives the
+ * same bits as one call, and so does any grouping of jobs into launches.
+ * All contexts must live on the same GPU.                                 */
 enum { DOSE_JOB_CLEAR = 1, DOSE_JOB_FINISH = 2 };
 typedef struct dose_job {
     dose_ctx *ctx;
