@@ -258,8 +258,10 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream);
 
 /* The whole 4D dose (Sec. 2.A): the Monte Carlo of every phase's subplan
  * (from the delivery given to dose_add_spots; Sec. 2.B-2.C) with
- * n_histories_per_phase histories each, all phases in one persistent launch
- * (phases without protons get zero dose), then the accumulation onto
+ * n_histories_per_phase histories each, all phases as one batch
+ * (dose_run_batch: one persistent launch, or one launch per phase from
+ * 2^25 histories; phases without protons get zero dose), then the
+ * accumulation onto
  * ref_phase as in dose_accumulate_subvoxel (method 0, Eqs. 2, 4-6).  Phase p
  * uses Philox stream p under `seed`.  Reads the per-phase proton totals back
  * to the host (a short wait on the stream) to skip empty phases.           */
