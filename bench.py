@@ -491,11 +491,33 @@ def _bench_trials(D, torch, stream, n_per_phase, n_trials=25, seed=SEED):
         n_jobs, mc_s = study()
         wall = time.perf_counter() - t0
         periods = sorted({int(D.read_delivery(v)["period_ns"]) // S_ for v in views})
+        acc = [D.dose_read(v, D.DOSE_ACCUM, 0, np.zeros((nz, ny, nx), np.float32)) for v in views[:3]]
+
+        # the plain engine: the same trials, one dose_run_phase per phase
+        # job, then the same accumulations; the same bits as the batch
+        zero = torch.zeros(nx * ny * nz, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D.dose_add_spots_trials(views, spots, D.delivery_struct(mean), D.spread_struct(spread), 0, stream)
+        for k, v in enumerate(views):
+            pp = D.dose_read(v, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64))
+            for p in range(ph.n_phases):
+                if pp[p].sum():
+                    D.dose_run_phase(v, p, n_per_phase, seed + k, 1.0, None, stream)
+                else:
+                    D.dose_set_phase_dose(v, p, zero, stream)
+        for v in views:
+            D.dose_accumulate_subvoxel(v, 0, (2, 2, 5), dvf=dvf_dev, stream=stream)
+        torch.cuda.synchronize()
+        plain_wall = time.perf_counter() - t0
+        plain_same = all(np.array_equal(D.dose_read(v, D.DOSE_ACCUM, 0, np.zeros((nz, ny, nx), np.float32)), a)
+                         for v, a in zip(views[:3], acc))
     finally:
         for v in views:
             D.dose_destroy(v)
         D.dose_destroy(base)
     return {"s_per_study": wall, "trials": n_trials, "phase_jobs": n_jobs, "transport_s": mc_s,
+            "plain_s_per_study": plain_wall, "plain_same_dose": plain_same,
             "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]},
             "transport_histories_per_s": n_jobs * n_per_phase / mc_s, "periods_s_drawn": periods,
             "workload": f"{n_trials} uncertainty trials of the synthetic 4DCT plan (synchrotron fills, "
