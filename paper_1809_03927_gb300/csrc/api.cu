@@ -969,7 +969,10 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
             if (!single)
                 CK(c0, cudaMemcpyAsync(c0->d_jobs, grp.data(), grp.size() * sizeof(TJob), cudaMemcpyHostToDevice, st));
             CK(c0, cudaMemsetAsync(c0->d_counter, 0, sizeof(unsigned long long), st));
-            const int mode = single ? kLaunchSingle : shared ? kLaunchShared : kLaunchTable;
+            // a table whose jobs differ only in seed and SPR scale (views of
+            // one grid: trials, serving steps) reads the rest from there too
+            const bool geom = !single && !shared && jobs_share_geometry(grp.data(), (int)grp.size());
+            const int mode = single ? kLaunchSingle : shared ? kLaunchShared : geom ? kLaunchGeom : kLaunchTable;
             const int spec = transport_spec(grp.data(), (int)grp.size());
             const void *kern = transport_kernel(mode, c0->regs, spec);
             size_t smem;

@@ -40,7 +40,7 @@ __global__ void k_alloc(const AllocJob *jobs);
 // source; kSpecFullGrid and kSpecFullHu are built for jobs that all have
 // every physics process on and, respectively, all have a per-voxel (rho,
 // SPR) grid or all read HU + table (transport_spec() says which applies).
-enum { kLaunchTable = 0, kLaunchSingle = 1, kLaunchShared = 2 };
+enum { kLaunchTable = 0, kLaunchSingle = 1, kLaunchShared = 2, kLaunchGeom = 3 };
 enum { kSpecGeneric = 0, kSpecFullGrid = 1, kSpecFullHu = 2 };
 struct TransportLaunch {
     int mode, regs, spec;
@@ -67,6 +67,19 @@ constexpr unsigned long long kSplitWork = 1ull << 25;
 int transport_spec(const TJob *jobs, int n);
 const void *transport_kernel(int mode, int regs, int spec);
 cudaError_t transport_launch(const TransportLaunch &L);
+// True when every job agrees with the first on the per-step fields other
+// than the SPR scale and the round keys: grid and voxel sizes, physics,
+// step limit (kLaunchGeom).
+inline bool jobs_share_geometry(const TJob *jobs, int n)
+{
+    constexpr size_t a = offsetof(TJob, spr_scale), b = offsetof(TJob, idx), e = offsetof(TJob, rk);
+    for (int j = 1; j < n; ++j)
+        if (std::memcmp(&jobs[j], &jobs[0], a) != 0 ||
+            std::memcmp(reinterpret_cast<const char *>(&jobs[j]) + b, reinterpret_cast<const char *>(&jobs[0]) + b,
+                        e - b) != 0)
+            return false;
+    return true;
+}
 // True when every job agrees with the first on the per-step fields (the
 // first kStepFieldBytes bytes of a TJob).
 inline bool jobs_share_step_fields(const TJob *jobs, int n)

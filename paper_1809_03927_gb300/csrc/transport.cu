@@ -240,8 +240,13 @@ __device__ __forceinline__ float2 box_muller2(float ua, float ub)
 // SPR) grid; 2: every job reads HU + table); -1 reads them from the job.
 // A fixed value drops the per-step branches on it; the arithmetic, and so
 // every result, is the same.
-enum { kTable = 0, kSingle = 1, kShared = 2 };
-static_assert(kTable == kLaunchTable && kSingle == kLaunchSingle && kShared == kLaunchShared, "launch modes");
+// kGeom: a table of jobs that agree on the grid, physics and step limit
+// (views of one grid under different seeds or SPR scales: trials, serving
+// steps), which come from P; the round keys and SPR scale come from the
+// job's entry with its grid, tally and stream.
+enum { kTable = 0, kSingle = 1, kShared = 2, kGeom = 3 };
+static_assert(kTable == kLaunchTable && kSingle == kLaunchSingle && kShared == kLaunchShared &&
+              kGeom == kLaunchGeom, "launch modes");
 template <int kMode, int kPhys, int kMat>
 __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, const TJob &P, int n_jobs,
                                                unsigned long long total,
@@ -280,6 +285,8 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
     // job_of: the per-step fields shared by the launch's jobs (and everything
     // a birth reads); own_of: the job's grid, tally, stream and ledger
     auto job_of = [&](int j) -> const TJob & { return kMode == kTable ? jt[j] : P; };
+    // the per-step fields that kGeom takes from the job: round keys, SPR scale
+    auto key_of = [&](int j) -> const TJob & { return kMode == kTable || kMode == kGeom ? jt[j] : P; };
     auto own_of = [&](int j) -> const TJob & { return kMode == kSingle ? P : jt[j]; };
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -442,7 +449,8 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
             m = __ldg(mat + (hv - kHuMin));
         }
         const float rho = m.x;
-        const float spr = m.y * J.spr_scale;
+        const TJob &Jk = key_of(job);
+        const float spr = m.y * Jk.spr_scale;
         const float inv_spr = __fdividef(1.0f, spr);
         const float2 re0 = lerp_e_in(T.re, E);
         const float R0 = re0.x;
@@ -450,7 +458,7 @@ __device__ __forceinline__ void transport_body(const TJob *__restrict__ jobs, co
         // this step's random numbers: independent of the geometry below, so
         // the generator's rounds can interleave with the table lookups
         const U6 u = uniforms6(philox_rk(
-            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), Jo.stream), J.rk));
+            make_uint4(step, (unsigned)h, (unsigned)(h >> 32), Jo.stream), Jk.rk));
         const float q = R0 * inv_spr;                  // residual range in the medium
         if (q <= kSmin) {                              // residual range below s_min
             atomicAdd(Jo.tally + vox, __float2ull_rn(E * wq));
@@ -675,6 +683,24 @@ k_transportS_r64(const __grid_constant__ TJob common, const TJob *__restrict__ j
     transport_body<kShared, P, M>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
 }
 
+template <int P, int M>
+__global__ void __launch_bounds__(512, 1)
+k_transportG(const __grid_constant__ TJob common, const TJob *__restrict__ jobs, int n_jobs, unsigned long long total,
+             unsigned long long *__restrict__ counter, const Tables *__restrict__ gtab, float inv_ds,
+             unsigned chunk, int stage)
+{
+    transport_body<kGeom, P, M>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+}
+
+template <int P, int M>
+__global__ void __launch_bounds__(1024, 1)
+k_transportG_r64(const __grid_constant__ TJob common, const TJob *__restrict__ jobs, int n_jobs,
+                 unsigned long long total, unsigned long long *__restrict__ counter,
+                 const Tables *__restrict__ gtab, float inv_ds, unsigned chunk, int stage)
+{
+    transport_body<kGeom, P, M>(jobs, common, n_jobs, total, counter, gtab, inv_ds, chunk, stage);
+}
+
 namespace {
 // (kPhys, kMat) of each specialisation
 template <int S> struct SpecArgs;
@@ -688,6 +714,7 @@ const void *kernel_of(int mode, int regs)
     constexpr int P = SpecArgs<S>::P, M = SpecArgs<S>::M;
     if (mode == kSingle) return regs ? (const void *)k_transport1_r64<P, M> : (const void *)k_transport1<P, M>;
     if (mode == kShared) return regs ? (const void *)k_transportS_r64<P, M> : (const void *)k_transportS<P, M>;
+    if (mode == kGeom) return regs ? (const void *)k_transportG_r64<P, M> : (const void *)k_transportG<P, M>;
     return regs ? (const void *)k_transport_r64<P, M> : (const void *)k_transport<P, M>;
 }
 
@@ -705,6 +732,12 @@ void launch_spec(const TransportLaunch &L)
                                                             L.inv_ds, L.chunk, L.stage);
     else if (L.mode == kShared)
         k_transportS<P, M><<<g, b, L.smem, L.stream>>>(*L.job0, L.d_jobs, L.n_jobs, L.total, L.counter, L.tab,
+                                                        L.inv_ds, L.chunk, L.stage);
+    else if (L.mode == kGeom && L.regs)
+        k_transportG_r64<P, M><<<g, b, L.smem, L.stream>>>(*L.job0, L.d_jobs, L.n_jobs, L.total, L.counter, L.tab,
+                                                            L.inv_ds, L.chunk, L.stage);
+    else if (L.mode == kGeom)
+        k_transportG<P, M><<<g, b, L.smem, L.stream>>>(*L.job0, L.d_jobs, L.n_jobs, L.total, L.counter, L.tab,
                                                         L.inv_ds, L.chunk, L.stage);
     else if (L.regs)
         k_transport_r64<P, M><<<g, b, L.smem, L.stream>>>(L.d_jobs, L.n_jobs, L.total, L.counter, L.tab, L.inv_ds,
@@ -746,7 +779,7 @@ cudaError_t transport_allow_smem()
 {
     const int bytes = (int)(kSmemTransportMax + birth_smem(1024));
     for (int spec = 0; spec < 3; ++spec)
-        for (int mode = 0; mode < 3; ++mode)
+        for (int mode = 0; mode < 4; ++mode)
             for (int regs = 0; regs < 2; ++regs) {
                 const cudaError_t e = cudaFuncSetAttribute(transport_kernel(mode, regs, spec),
                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
