@@ -492,6 +492,11 @@ def _bench_trials(D, torch, stream, n_per_phase, n_trials=25, seed=SEED):
         wall = time.perf_counter() - t0
         periods = sorted({int(D.read_delivery(v)["period_ns"]) // S_ for v in views})
         acc = [D.dose_read(v, D.DOSE_ACCUM, 0, np.zeros((nz, ny, nx), np.float32)) for v in views[:3]]
+        steps = 0
+        for v in views:
+            pp = D.dose_read(v, D.DOSE_SUBPLAN, 0, np.zeros((ph.n_phases, len(plan)), np.uint64)).sum(axis=1)
+            steps += sum(int(D.dose_read(v, D.DOSE_ENERGY_LEDGER, p, np.zeros(8, np.uint64))[4])
+                         for p in range(ph.n_phases) if pp[p] > 0)
 
         # the plain engine: the same trials, one dose_run_phase per phase
         # job, then the same accumulations; the same bits as the batch
@@ -520,6 +525,10 @@ def _bench_trials(D, torch, stream, n_per_phase, n_trials=25, seed=SEED):
             "plain_s_per_study": plain_wall, "plain_same_dose": plain_same,
             "launch": {"registers": "64" if tune[0] else "<=128", "block": tune[1], "chunk": tune[2]},
             "transport_histories_per_s": n_jobs * n_per_phase / mc_s, "periods_s_drawn": periods,
+            "steps_per_history": steps / (n_jobs * n_per_phase),
+            # the transport launch against the measured issue peak at the
+            # headline 300 issue slots per step
+            "transport_steps_per_s": steps / mc_s,
             "workload": f"{n_trials} uncertainty trials of the synthetic 4DCT plan (synchrotron fills, "
                         f"period U{{3..7}} s, Gaussian machine parameters), {n_per_phase:.0e} histories per "
                         "phase with protons, all trials' phases in one ragged launch, EMTM 2x2x5 per trial"}
