@@ -931,7 +931,7 @@ int dose_run_batch(const dose_job *jobs, int n_jobs, void *stream)
                 t.rk[r >> 1] = make_uint4(t.key0 + (unsigned)r * 0x9E3779B9u, t.key1 + (unsigned)r * 0xBB67AE85u,
                                           t.key0 + (unsigned)(r + 1) * 0x9E3779B9u, t.key1 + (unsigned)(r + 1) * 0xBB67AE85u);
             t.stream = (unsigned)J.phase;
-            t.hist_begin = J.hist_begin; t.work_begin = work; t.n_work = cnt; t.spread_log2 = spread_for(g.nvox);
+            t.hist_begin = J.hist_begin; t.work_begin = work; t.n_work = cnt; t.spread_log2 = spread_for(g.nvox, cnt);
             tj.push_back(t);
             work += cnt;
         }

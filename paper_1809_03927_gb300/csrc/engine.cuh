@@ -97,12 +97,19 @@ __host__ __device__ inline unsigned long long spread_history(unsigned long long 
     const unsigned long long m = (1ull << s) - 1, q = n >> s, r = n & m, k = w & m;
     return k * q + (k < r ? k : r) + (w >> s);
 }
-// Grids whose tally and material grid (16 bytes a voxel) fit this budget
-// of the L2 take 64 strides; larger grids keep plan order, whose few
-// neighbouring spots keep the L2 working set small.
+// Jobs of at least kSpreadMinWork histories on grids whose tally and
+// material grid (16 bytes a voxel) fit kSpreadGridBytes of the L2 take 64
+// strides.  Larger grids keep plan order, whose few neighbouring spots keep
+// the L2 working set small; so do smaller jobs, whose launch tail grows
+// when the last histories in flight mix all energies instead of ending on
+// the plan's last, lowest-energy spots.
 constexpr unsigned kSpreadLog2 = 6;
 constexpr unsigned long long kSpreadGridBytes = 48ull << 20;
-inline unsigned spread_for(long long nvox) { return (unsigned long long)nvox * 16 <= kSpreadGridBytes ? kSpreadLog2 : 0; }
+constexpr unsigned long long kSpreadMinWork = 1ull << 23;
+inline unsigned spread_for(long long nvox, unsigned long long n_work)
+{
+    return (unsigned long long)nvox * 16 <= kSpreadGridBytes && n_work >= kSpreadMinWork ? kSpreadLog2 : 0;
+}
 
 // The fields every step reads that jobs of one context and seed share;
 // they precede the per-job pointers (no padding: all 4-byte scalars and

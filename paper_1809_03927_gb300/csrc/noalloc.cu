@@ -212,7 +212,7 @@ int dose_run_phase_noalloc(const int16_t *hu, int nx, int ny, int nz, float dx_m
         t.rk[r >> 1] = make_uint4(t.key0 + (unsigned)r * 0x9E3779B9u, t.key1 + (unsigned)r * 0xBB67AE85u,
                                   t.key0 + (unsigned)(r + 1) * 0x9E3779B9u, t.key1 + (unsigned)(r + 1) * 0xBB67AE85u);
     t.stream = 0;
-    t.hist_begin = 0; t.work_begin = 0; t.n_work = n_histories; t.spread_log2 = spread_for(nvox);
+    t.hist_begin = 0; t.work_begin = 0; t.n_work = n_histories; t.spread_log2 = spread_for(nvox, n_histories);
     AllocJob *d_a = reinterpret_cast<AllocJob *>(base + kOffAlloc);
     e = cudaMemcpyAsync(d_a, &a, sizeof a, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);                   // a lives on this stack
