@@ -536,11 +536,13 @@ int dose_debug_tables(const float *E, int n, float *out, void *stream);
 
 /* Self-test of the birth order of a job's histories (no device work): for
  * work items w = 0 .. n-1 writes out[w] = the history index (from the
- * job's first) that work item w transports, with the work dealt
- * round-robin over 2^log2_strides contiguous strides of the history range
- * (the order the transport uses on grids small enough for the L2; 0 is
- * plan order).  A history's result depends only on its index, so the
- * order changes no tally.  n <= 2^26, log2_strides <= 16; host memory.     */
+ * job's first) that work item w transports: the last t = min(n/8, 2^18)
+ * work items take the last t histories in order, the others are dealt
+ * round-robin over 2^log2_strides contiguous strides of the first n - t
+ * histories (the order the transport uses for large jobs on grids small
+ * enough for the L2; 0 is plan order).  A history's result depends only on
+ * its index, so the order changes no tally.  n <= 2^26, log2_strides <= 16;
+ * host memory.                                                            */
 int dose_debug_spread(uint64_t n, uint32_t log2_strides, uint64_t *out);
 
 #ifdef __cplusplus

@@ -84,17 +84,23 @@ struct alignas(16) TJob {
 static_assert(sizeof(TJob) == 256, "job descriptor: 256 bytes");
 
 // The order in which a job's histories are born: work item w of n goes to
-// history spread_history(w, n, s), a bijection of [0, n) that deals the
-// work items round-robin over 2^s contiguous strides of the history range
-// (stride k holds n / 2^s histories, one more for the first n mod 2^s).
-// Consecutive work items, and so the histories in flight at any moment,
-// then come from 2^s places of the plan instead of a few neighbouring
-// spots, whose tracks would overlap and pile their tally atomics onto the
-// same voxels.  A history's result depends only on its index, so the order
-// changes no tally bit.  s = 0 is the identity.
+// history spread_history(w, n, s), a bijection of [0, n).  The last
+// t = min(n / 8, 2^18) work items take the last t histories in plan order;
+// the others are dealt round-robin over 2^s contiguous strides of the first
+// n - t histories (stride k holds (n - t) / 2^s of them, one more for the
+// first (n - t) mod 2^s).  Consecutive work items, and so the histories in
+// flight, then come from 2^s places of the plan instead of a few
+// neighbouring spots, whose tracks would overlap and pile their tally
+// atomics onto the same voxels; the launch still ends on the plan's last
+// (lowest-energy, shortest) spots, which keeps its tail short.  A
+// history's result depends only on its index, so the order changes no
+// tally bit.  s = 0 is the identity.
+constexpr unsigned kSpreadTailLog2 = 18;
 __host__ __device__ inline unsigned long long spread_history(unsigned long long w, unsigned long long n, unsigned s)
 {
-    const unsigned long long m = (1ull << s) - 1, q = n >> s, r = n & m, k = w & m;
+    const unsigned long long t = (n >> 3) < (1ull << kSpreadTailLog2) ? (n >> 3) : (1ull << kSpreadTailLog2);
+    if (s == 0 || w >= n - t) return w;
+    const unsigned long long ns = n - t, m = (1ull << s) - 1, q = ns >> s, r = ns & m, k = w & m;
     return k * q + (k < r ? k : r) + (w >> s);
 }
 // Jobs of at least kSpreadMinWork histories on grids whose tally and

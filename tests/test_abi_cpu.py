@@ -85,27 +85,34 @@ def test_structs_match_the_header(libdose):
 
 def test_birth_order_is_a_round_robin_bijection(libdose):
     """The order in which a job's histories are born (host arithmetic, no
-    device): every history exactly once; with 2^s strides, work item w goes
-    to stride w mod 2^s, and inside each stride the histories follow one
-    another; the strides tile the range in order, the first n mod 2^s one
-    history longer; s = 0 and n < 2^s are plan order."""
+    device): every history exactly once; the last t = min(n/8, 2^18) work
+    items take the last t histories in order; before them, with 2^s
+    strides, work item w goes to stride w mod 2^s of the first n - t
+    histories, inside each stride the histories follow one another, and
+    the strides tile that range in order, the first (n - t) mod 2^s one
+    history longer; s = 0 and short ranges are plan order."""
     D = libdose
-    for n in (0, 1, 5, 63, 64, 65, 1000, 4097, 100_003):
+    for n in (0, 1, 5, 63, 64, 65, 1000, 4097, 100_003, 3_000_001):
         for s in (0, 1, 4, 6):
-            h = D.dose_debug_spread(n, s)
-            assert np.array_equal(np.sort(h), np.arange(n, dtype=np.uint64))
-            K = 1 << s
-            if s == 0 or n <= K:
-                assert np.array_equal(h, np.arange(n, dtype=np.uint64))
+            h = D.dose_debug_spread(n, s).astype(np.int64)
+            assert np.array_equal(np.sort(h), np.arange(n))
+            if s == 0:
+                assert np.array_equal(h, np.arange(n))
+                continue
+            t = min(n // 8, 1 << 18)
+            assert np.array_equal(h[n - t:], np.arange(n - t, n))
+            ns, K = n - t, 1 << s
+            head = h[:ns]
+            if ns <= K:
+                assert np.array_equal(head, np.arange(ns))
                 continue
             starts = []
             for k in range(K):
-                mine = h[k::K].astype(np.int64)
+                mine = head[k::K]
                 assert np.all(np.diff(mine) == 1)              # consecutive inside a stride
-                assert len(mine) == n // K + (1 if k < n % K else 0)
+                assert len(mine) == ns // K + (1 if k < ns % K else 0)
                 starts.append(int(mine[0]))
-            lengths = [n // K + (1 if k < n % K else 0) for k in range(K)]
+            lengths = [ns // K + (1 if k < ns % K else 0) for k in range(K)]
             assert starts == list(np.cumsum([0] + lengths[:-1]))
     with pytest.raises(D.DoseError):
         D.dose_debug_spread(10, 17)
-
