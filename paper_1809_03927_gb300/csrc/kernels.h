@@ -30,8 +30,11 @@ __global__ void k_alloc(const AllocJob *jobs);
 // parameter (kLaunchSingle; the launch gives transport_smem(1) +
 // birth_smem(block) bytes of shared memory), a table of jobs whose
 // per-step fields (see jobs_share_step_fields) come from the parameter
-// `job0` (kLaunchShared), or a general table (kLaunchTable).  For the two
-// table modes, stage != 0: the launch gives transport_smem(n_jobs) +
+// `job0` (kLaunchShared), a table of jobs that share only the grid,
+// physics and step limit (see jobs_share_geometry), which come from `job0`
+// while round keys and SPR scale come from each job (kLaunchGeom), or a
+// general table (kLaunchTable).  For the table modes, stage != 0: the
+// launch gives transport_smem(n_jobs) +
 // birth_smem(block) bytes and the job table is staged in shared memory;
 // 0: transport_smem(kMaxStagedJobs + 1) + birth_smem(block) (tables only)
 // and the jobs are read from global memory.  regs: 1 = the 64-register
