@@ -50,8 +50,8 @@ struct TransportLaunch {
     unsigned grid, block;
     size_t smem;
     cudaStream_t stream;
-    const TJob *job0;                   // host: the job (single) or the shared fields (shared)
-    const TJob *d_jobs;                 // device table (table and shared modes)
+    const TJob *job0;                   // host: the job (single) or the shared fields (shared, geom)
+    const TJob *d_jobs;                 // device table (the table modes)
     int n_jobs;
     unsigned long long total;           // work items
     unsigned long long *counter;        // device work counter, zero at launch
@@ -60,11 +60,11 @@ struct TransportLaunch {
     unsigned chunk;
     int stage;
 };
-// A batch whose jobs all have at least this many work items runs them as
-// consecutive single-job launches instead of one table launch: the
+// The jobs of a batch with at least this many work items run in single-job
+// launches of their own, after one launch shared by the others: the
 // single-job step is a few per cent cheaper, and a launch's tail (its
 // longest histories finishing on a part-idle GPU) costs about 0.7 ms, so
-// the split pays only for jobs of tens of milliseconds and more.
+// a launch of its own pays only for jobs of tens of milliseconds and more.
 constexpr unsigned long long kSplitWork = 1ull << 25;
 // The most specialised kernel every job of the launch satisfies.
 int transport_spec(const TJob *jobs, int n);
