@@ -6,6 +6,7 @@
 //                transport with a 64-bit fixed-point energy tally
 //   k_normalise  tally -> dose in Gy
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include "engine.cuh"
 #include "kernels.h"
@@ -777,14 +778,23 @@ cudaError_t transport_launch(const TransportLaunch &L)
 
 cudaError_t transport_allow_smem()
 {
+    // the attribute is a per-device property of each kernel: set it once per
+    // device (24 calls), not on every launch
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
     const int bytes = (int)(kSmemTransportMax + birth_smem(1024));
     for (int spec = 0; spec < 3; ++spec)
         for (int mode = 0; mode < 4; ++mode)
             for (int regs = 0; regs < 2; ++regs) {
-                const cudaError_t e = cudaFuncSetAttribute(transport_kernel(mode, regs, spec),
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                e = cudaFuncSetAttribute(transport_kernel(mode, regs, spec),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
                 if (e != cudaSuccess) return e;
             }
+    done.fetch_or(bit, std::memory_order_release);
     return cudaSuccess;
 }
 
