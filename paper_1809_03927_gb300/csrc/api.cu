@@ -356,7 +356,9 @@ int wait_event(dose_ctx *c, cudaEvent_t ev)
         const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
             std::chrono::steady_clock::now() - t0).count();
         if (ms > c->timeout_ms) return fail(c, DOSE_ETIMEOUT, "device work did not finish within %lld ms", c->timeout_ms);
-        std::this_thread::sleep_for(std::chrono::microseconds(ms < 10 ? 20 : 500));
+        // short naps while the work is young (a dose run of ~10 ms should be
+        // noticed within tens of microseconds), longer ones for long runs
+        std::this_thread::sleep_for(std::chrono::microseconds(ms < 50 ? 10 : ms < 1000 ? 100 : 1000));
     }
 }
 
